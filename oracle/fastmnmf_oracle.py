@@ -1,0 +1,339 @@
+"""Float64 CPU oracle of FastMNMF (Sekiguchi et al., EUSIPCO 2019, arXiv 1903.03237).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module.
+The product path (the CUDA library and its Python binding) never calls it, and this
+module imports nothing from the product package: the two share no code.
+
+What it computes, step by step in the paper's order and notation (NumPy float64 /
+complex128; plain ``einsum`` sums and explicit Python loops for the iterative
+projection).  Each function cites the passage it follows:
+
+* source model        lambda_ftn = sum_k w_nkf h_nkt                      (Sec. II-B-2, Eq. 9)
+* diagonalised SCMs   Q_f G_nf Q_f^H = Diag(g~_nf),  Q_f = [q_f1..q_fM]^H   (Sec. III-A-1, Eq. 16)
+* model power         y~_ftm = sum_n lambda_ftn g~_nfm                     (Sec. III-A-2, below Eq. 17)
+* projected power     x~_ftm = |q_fm^H x_ft|^2                             (Sec. III-A-2, below Eq. 17)
+* log-likelihood      Eq. 17, with the dropped constant -FTM log(pi) restored
+* IP update of Q_f    V_fm, (Q_f V_fm)^-1 e_m, normalisation by q^H V q   (Eqs. 18-20)
+* MU of g~            Eq. 21;   MU of W and H   Eqs. 23-24
+* Wiener separation   x_ftn = Y_ftn Y_ft^-1 x_ft                          (Sec. II-A-1, Eq. 3)
+
+Readings of points where the paper is silent (block order, scale normalisation,
+initialisation, the log-likelihood constant) are fixed in ``iterate``,
+``normalise`` and ``init_state`` below.
+
+Pins (see tests/test_oracle_*.py): monotone log-likelihood per block (MM / IP
+guarantee), q^H V q = 1 and Q V q = e after each IP row update, decorrelated
+log-likelihood == full-rank complex-Gaussian log-density built from explicit
+covariances, MU numerator minus denominator == finite-difference gradient of the
+log-likelihood, IP row == brute-force row maximiser, M=1 reduction to textbook
+IS-NMF, Wiener outputs summing to the mixture and equal to the direct full-rank
+filter, LL invariance of the normalisation.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+UPDATE_W = 1
+UPDATE_H = 2
+UPDATE_G = 4
+UPDATE_Q = 8
+UPDATE_ALL = UPDATE_W | UPDATE_H | UPDATE_G | UPDATE_Q
+
+# ---------------------------------------------------------------------------
+# SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+# generators", OOPSLA 2014), counter form: output i (i = 0, 1, ...) of the
+# stream seeded with s is mix(s + (i + 1) * 0x9E3779B97F4A7C15 mod 2^64), where
+# mix(z) = z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+#          z *= 0x94D049BB133111EB; z ^= z >> 31.
+# The initial state of fmnmf_init draws its W, H from this stream; the library
+# implements the same published definition independently.
+# ---------------------------------------------------------------------------
+_MASK64 = (1 << 64) - 1
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+def _splitmix64_mix(z: int) -> int:
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def splitmix64_uniform(seed: int, start: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1): top 53 bits of SplitMix64 outputs start..start+count-1."""
+    out = np.empty(count, dtype=np.float64)
+    s = seed & _MASK64
+    for i in range(count):
+        z = _splitmix64_mix((s + (start + i + 1) * _GAMMA) & _MASK64)
+        out[i] = (z >> 11) * (1.0 / 9007199254740992.0)
+    return out
+
+
+def init_state(F: int, T: int, M: int, N: int, K: int, seed: int):
+    """Initial state of ``fmnmf_init`` (the paper fixes an initialisation only for its
+    DP experiments, Sec. IV-A; this is the library's documented one):
+
+    * W[n,k,f] = 0.1 + u_i, i = (n*K + k)*F + f        (u_i the SplitMix64 uniforms)
+    * H[n,k,t] = 0.1 + u_j, j = N*K*F + (n*K + k)*T + t
+    * g~[n,f,m] = 1 if m == n mod M else 1e-2, then divided by its sum over m
+    * Q_f = I (identity diagonaliser)
+
+    Values are rounded to float32, the library's state precision.
+    """
+    nw, nh = N * K * F, N * K * T
+    u = splitmix64_uniform(seed, 0, nw + nh)
+    W = (0.1 + u[:nw]).astype(np.float32).astype(np.float64).reshape(N, K, F)
+    H = (0.1 + u[nw:]).astype(np.float32).astype(np.float64).reshape(N, K, T)
+    G = np.full((N, F, M), 1e-2)
+    for n in range(N):
+        G[n, :, n % M] = 1.0
+    G = G / G.sum(axis=2, keepdims=True)
+    G = G.astype(np.float32).astype(np.float64)
+    Q = np.tile(np.eye(M, dtype=np.complex128), (F, 1, 1))
+    return W, H, G, Q
+
+
+# ---------------------------------------------------------------------------
+# Model quantities
+# ---------------------------------------------------------------------------
+def source_psd(W, H):
+    """lambda[f,t,n] = sum_k w_nkf h_nkt  (Sec. II-B-2, Eq. 9)."""
+    return np.einsum("nkf,nkt->ftn", W, H)
+
+
+def model_power(lam, G):
+    """y~[f,t,m] = sum_n lambda_ftn g~_nfm  (Sec. III-A-2, definition below Eq. 17)."""
+    return np.einsum("ftn,nfm->ftm", lam, G)
+
+
+def projected_power(Q, X):
+    """x~[f,t,m] = |q_fm^H x_ft|^2 = |(Q_f x_ft)_m|^2  (Sec. III-A-2, below Eq. 17;
+    row m of Q_f is q_fm^H, Eq. 16)."""
+    QX = np.einsum("fmj,ftj->ftm", Q, X)
+    return (QX.real ** 2) + (QX.imag ** 2)
+
+
+def log_det_QQH(Q):
+    """log |Q_f Q_f^H| = log |det Q_f|^2 per bin (the last term of Eq. 17)."""
+    _, logabs = np.linalg.slogdet(Q)
+    return 2.0 * logabs
+
+
+def loglik(X, W, H, G, Q):
+    """Decorrelated log-likelihood, Eq. 17:
+    sum_{f,t,m} ( -x~/y~ - log y~ ) + T sum_f log|Q_f Q_f^H|  - F T M log(pi).
+    The constant -FTM log(pi), dropped by the paper's "=c", is restored so that the
+    value is the true log-density of Eq. 2 under the constraint of Eq. 16."""
+    F, T, M = X.shape
+    xt = projected_power(Q, X)
+    yt = model_power(source_psd(W, H), G)
+    return (float(np.sum(-xt / yt - np.log(yt))) + T * float(np.sum(log_det_QQH(Q)))
+            - F * T * M * np.log(np.pi))
+
+
+def loglik_terms_abs(X, W, H, G, Q):
+    """Sum of the absolute values of the terms of Eq. 17 (scale for relative LL errors)."""
+    F, T, M = X.shape
+    xt = projected_power(Q, X)
+    yt = model_power(source_psd(W, H), G)
+    return (float(np.sum(np.abs(xt / yt)) + np.sum(np.abs(np.log(yt))))
+            + T * float(np.sum(np.abs(log_det_QQH(Q)))) + F * T * M * np.log(np.pi))
+
+
+def full_rank_covariances(W, H, G, Q):
+    """Y_ftn = lambda_ftn G_nf with G_nf = Q_f^-1 Diag(g~_nf) Q_f^-H (Eq. 16 solved for
+    G_nf), and Y_ft = sum_n Y_ftn (Eq. 2).  Returns (Ysrc[f,t,n,M,M], Y[f,t,M,M])."""
+    lam = source_psd(W, H)
+    Qi = np.linalg.inv(Q)                                            # [F,M,M]
+    Gfull = np.einsum("fij,nfj,fkj->nfik", Qi, G, Qi.conj())         # Q^-1 Diag(g) Q^-H
+    Ysrc = np.einsum("ftn,nfik->ftnik", lam, Gfull)
+    return Ysrc, Ysrc.sum(axis=2)
+
+
+def loglik_fullrank(X, W, H, G, Q):
+    """Log-density of Eq. 2 evaluated directly: sum_{f,t} log CN(x_ft | 0, Y_ft)
+    = -sum ( x^H Y^-1 x + log det(pi Y) )  (Eq. 4 with its constant), with Y_ft built
+    explicitly from the full-rank SCMs.  Used only as a pin of ``loglik``."""
+    _, Y = full_rank_covariances(W, H, G, Q)
+    M = X.shape[2]
+    sol = np.linalg.solve(Y, X[..., None])[..., 0]
+    quad = np.einsum("ftm,ftm->ft", X.conj(), sol).real
+    _, logabs = np.linalg.slogdet(Y)
+    return float(-np.sum(quad) - np.sum(logabs) - X.shape[0] * X.shape[1] * M * np.log(np.pi))
+
+
+# ---------------------------------------------------------------------------
+# Update rules
+# ---------------------------------------------------------------------------
+def _aux(xt, yt):
+    """The two ratios every MU rule is built from: A = y~^-1 x~ y~^-1 and B = y~^-1."""
+    return xt / yt ** 2, 1.0 / yt
+
+
+def mu_W_terms(xt, W, H, G):
+    """Numerator and denominator of the W rule (Sec. III-B-2, Eq. 23):
+    num[n,k,f] = sum_{t,m} h_nkt g~_nfm x~/y~^2,  den[n,k,f] = sum_{t,m} h_nkt g~_nfm / y~."""
+    A, B = _aux(xt, model_power(source_psd(W, H), G))
+    num = np.einsum("nkt,nfm,ftm->nkf", H, G, A)
+    den = np.einsum("nkt,nfm,ftm->nkf", H, G, B)
+    return num, den
+
+
+def update_W(xt, W, H, G):
+    """w_nkf <- w_nkf sqrt(num/den)  (Eq. 23)."""
+    num, den = mu_W_terms(xt, W, H, G)
+    return W * np.sqrt(num / den)
+
+
+def mu_H_terms(xt, W, H, G):
+    """Numerator and denominator of the H rule (Eq. 24): sums over f and m of
+    w_nkf g~_nfm x~/y~^2 and of w_nkf g~_nfm / y~."""
+    A, B = _aux(xt, model_power(source_psd(W, H), G))
+    num = np.einsum("nkf,nfm,ftm->nkt", W, G, A)
+    den = np.einsum("nkf,nfm,ftm->nkt", W, G, B)
+    return num, den
+
+
+def update_H(xt, W, H, G):
+    """h_nkt <- h_nkt sqrt(num/den)  (Eq. 24)."""
+    num, den = mu_H_terms(xt, W, H, G)
+    return H * np.sqrt(num / den)
+
+
+def mu_G_terms(xt, W, H, G):
+    """Numerator and denominator of the g~ rule (Sec. III-A-2, Eq. 21):
+    num[n,f,m] = sum_t lambda_ftn x~/y~^2,  den[n,f,m] = sum_t lambda_ftn / y~."""
+    lam = source_psd(W, H)
+    A, B = _aux(xt, model_power(lam, G))
+    num = np.einsum("ftn,ftm->nfm", lam, A)
+    den = np.einsum("ftn,ftm->nfm", lam, B)
+    return num, den
+
+
+def update_G(xt, W, H, G):
+    """g~_nfm <- g~_nfm sqrt(num/den)  (Eq. 21)."""
+    num, den = mu_G_terms(xt, W, H, G)
+    return G * np.sqrt(num / den)
+
+
+def weighted_scm(X, yt):
+    """V_fm = (1/T) sum_t x_ft x_ft^H / y~_ftm  (Sec. III-A-2, Eq. 18).  Returns V[f,m,i,j]."""
+    T = X.shape[1]
+    return np.einsum("fti,ftj,ftm->fmij", X, X.conj(), 1.0 / yt) / T
+
+
+def update_Q(X, W, H, G, Q, trace=None):
+    """Iterative projection (Eqs. 18-20), rows in order m = 1..M, each using the
+    current Q_f (Eq. 19 has Q_f on the right-hand side):
+
+        q_fm <- (Q_f V_fm)^-1 e_m ;  q_fm <- q_fm / sqrt(q_fm^H V_fm q_fm) ;
+        row m of Q_f <- q_fm^H.
+
+    V_fm depends on y~ only, which the Q update does not change, so all V_fm of a bin
+    are formed once before its row loop.  ``trace`` (a list) receives, after each row
+    update, (f, m, q^H V q, Q_f V_fm q_fm) for the pins."""
+    F, T, M = X.shape
+    yt = model_power(source_psd(W, H), G)
+    V = weighted_scm(X, yt)
+    Qn = Q.copy()
+    for f in range(F):
+        for m in range(M):
+            Vfm = V[f, m]
+            e = np.zeros(M, dtype=np.complex128)
+            e[m] = 1.0
+            q = np.linalg.solve(Qn[f] @ Vfm, e)                      # Eq. 19
+            s = float(np.real(q.conj() @ Vfm @ q))
+            q = q / np.sqrt(s)                                       # Eq. 20
+            Qn[f, m, :] = q.conj()                                   # Q_f = [q_f1 .. q_fM]^H
+            if trace is not None:
+                trace.append((f, m, float(np.real(q.conj() @ Vfm @ q)), Qn[f] @ Vfm @ q))
+    return Qn
+
+
+def normalise(W, H, G, Q):
+    """Scale normalisation (the paper is silent; this reading leaves every y~_ftm, every
+    x~/y~ and the log-likelihood unchanged in exact arithmetic):
+
+    1. phi_f = tr(Q_f Q_f^H)/M;  Q_f <- Q_f/sqrt(phi_f);  g~_nf <- g~_nf/phi_f
+       (x~_ft and y~_ft both scale by 1/phi_f; log|Q Q^H| drops by M log phi_f, which
+       the T*M log phi_f rise of -sum log y~ cancels).
+    2. nu_nf = sum_m g~_nfm;  g~_nf <- g~_nf/nu_nf;  w_nkf <- w_nkf nu_nf  (lambda g~ fixed).
+    3. mu_nk = sum_f w_nkf;   w_nkf <- w_nkf/mu_nk;  h_nkt <- h_nkt mu_nk  (lambda fixed).
+    """
+    M = Q.shape[1]
+    phi = np.einsum("fij,fij->f", Q, Q.conj()).real / M
+    Q = Q / np.sqrt(phi)[:, None, None]
+    G = G / phi[None, :, None]
+    nu = G.sum(axis=2)                                               # [N,F]
+    G = G / nu[:, :, None]
+    W = W * nu[:, None, :]
+    mu = W.sum(axis=2)                                               # [N,K]
+    W = W / mu[:, :, None]
+    H = H * mu[:, :, None]
+    return W, H, G, Q
+
+
+def iterate(X, W, H, G, Q, n_iter=1, mask=UPDATE_ALL, do_normalise=True, block_ll=None):
+    """n_iter FastMNMF iterations (Sec. III-C-2: the NMF source model of Sec. III-B-2
+    inside the jointly diagonalisable spatial model of Sec. III-A).  Block order
+    (the paper only says the method alternates NTF-style multiplicative updates and
+    IP): W (Eq. 23) -> H (Eq. 24) -> g~ (Eq. 21) -> Q (Eqs. 18-20) -> normalise.
+    y~ and x~ are recomputed from the current parameters before every block, so each
+    block is an exact MM / IP step and the log-likelihood never decreases.
+
+    Returns (W, H, G, Q, ll_trace) with ll_trace[i] the log-likelihood after
+    iteration i.  ``block_ll`` (a list), if given, receives the log-likelihood after
+    every block."""
+    W = np.array(W, dtype=np.float64)
+    H = np.array(H, dtype=np.float64)
+    G = np.array(G, dtype=np.float64)
+    Q = np.array(Q, dtype=np.complex128)
+    X = np.asarray(X, dtype=np.complex128)
+    trace = []
+    for _ in range(n_iter):
+        xt = projected_power(Q, X)
+        if mask & UPDATE_W:
+            W = update_W(xt, W, H, G)
+            if block_ll is not None:
+                block_ll.append(("W", loglik(X, W, H, G, Q)))
+        if mask & UPDATE_H:
+            H = update_H(xt, W, H, G)
+            if block_ll is not None:
+                block_ll.append(("H", loglik(X, W, H, G, Q)))
+        if mask & UPDATE_G:
+            G = update_G(xt, W, H, G)
+            if block_ll is not None:
+                block_ll.append(("G", loglik(X, W, H, G, Q)))
+        if mask & UPDATE_Q:
+            Q = update_Q(X, W, H, G, Q)
+            if block_ll is not None:
+                block_ll.append(("Q", loglik(X, W, H, G, Q)))
+        if do_normalise:
+            W, H, G, Q = normalise(W, H, G, Q)
+        trace.append(loglik(X, W, H, G, Q))
+    return W, H, G, Q, trace
+
+
+# ---------------------------------------------------------------------------
+# Separation
+# ---------------------------------------------------------------------------
+def separate(X, W, H, G, Q):
+    """Multichannel Wiener filter of Eq. 3 in the diagonalised form.  Substituting
+    G_nf = Q_f^-1 Diag(g~_nf) Q_f^-H (Eq. 16) into Y_ftn Y_ft^-1 gives
+    Q_f^-1 Diag(lambda_ftn g~_nf / y~_ft) Q_f, so
+        x_ftn = Q_f^-1 ( lambda_ftn g~_nf / y~_ft  (elementwise)  Q_f x_ft ).
+    Returns out[n,f,t,m] (every channel of every source image)."""
+    lam = source_psd(W, H)
+    yt = model_power(lam, G)
+    QX = np.einsum("fmj,ftj->ftm", Q, X)
+    Qi = np.linalg.inv(Q)
+    gain = np.einsum("ftn,nfm->nftm", lam, G) / yt[None]
+    return np.einsum("fij,nftj->nfti", Qi, gain * QX[None])
+
+
+def separate_direct(X, W, H, G, Q):
+    """Eq. 3 evaluated literally, x_ftn = Y_ftn Y_ft^-1 x_ft with explicit full-rank
+    matrices (pin of ``separate``)."""
+    Ysrc, Y = full_rank_covariances(W, H, G, Q)
+    sol = np.linalg.solve(Y, X[..., None])[..., 0]                   # Y_ft^-1 x_ft
+    return np.einsum("ftnij,ftj->nfti", Ysrc, sol)

@@ -1,0 +1,88 @@
+"""Seeded synthetic multichannel mixtures drawn from FastMNMF's own generative model.
+
+This module only draws data: it is the one piece that both the CUDA path's tests and
+the float64 oracle consume, and it contains none of the estimation updates.  A
+mixture is synthesised exactly as the generative model states it:
+
+* source model (Sec. II-B-2, Eq. 9): lambda_ftn = sum_k w_nkf h_nkt with
+  w, h ~ Gamma(1, 1) i.i.d.;
+* jointly diagonalisable spatial model (Sec. III-A-1, Eq. 16): per bin a
+  diagonaliser Q_f = I + 0.3 Z (Z_ij ~ CN(0, 1)) and per (n, f) a nonnegative
+  g~_nf ~ Dirichlet(1_M);
+* source images (Eq. 1): x_ftn = Q_f^-1 diag(sqrt(lambda_ftn g~_nf)) z_ftn with
+  z_ftn ~ CN(0, I), so x_ftn ~ CN(0, lambda_ftn Q_f^-1 Diag(g~_nf) Q_f^-H);
+* mixture (Eq. 2): x_ft = sum_n x_ftn;
+* optional diffuse noise on a seeded 10 % of the frequency bins: x_ft += CN(0, s I).
+
+Everything is drawn with NumPy's ``default_rng(seed)`` (PCG64) in a fixed order, and
+stored as complex64 ``X[F][T][M]`` (real/imag interleaved), the library's input
+layout.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Mixture:
+    X: np.ndarray          # complex64 [F, T, M]
+    W: np.ndarray          # float64 [N, K, F]   (truth used for the draw)
+    H: np.ndarray          # float64 [N, K, T]
+    G: np.ndarray          # float64 [N, F, M]
+    Q: np.ndarray          # complex128 [F, M, M]
+    noisy_bins: np.ndarray  # int64 indices of bins that received diffuse noise
+
+
+def _cn(rng, shape):
+    """Circularly-symmetric CN(0, 1): real and imaginary parts i.i.d. N(0, 1/2)."""
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * np.sqrt(0.5)
+
+
+def make_mixture(F: int, T: int, M: int, N: int, K: int, seed: int,
+                 diffuse_frac: float = 0.0, diffuse_var: float = 1e-3) -> Mixture:
+    rng = np.random.default_rng(seed)
+    W = rng.gamma(1.0, 1.0, size=(N, K, F))
+    H = rng.gamma(1.0, 1.0, size=(N, K, T))
+    G = rng.dirichlet(np.ones(M), size=(N, F))                      # [N, F, M]
+    Q = np.eye(M)[None] + 0.3 * _cn(rng, (F, M, M))
+    Z = _cn(rng, (N, F, T, M))
+    Qi = np.linalg.inv(Q)
+    X = np.zeros((F, T, M), dtype=np.complex128)
+    for n in range(N):
+        psd = W[n].T @ H[n]                                         # [F, T] source PSD
+        amp = np.sqrt(psd[:, :, None] * G[n][:, None, :])           # [F, T, M]
+        X += np.einsum("fij,ftj->fti", Qi, amp * Z[n])
+    noisy = np.zeros(0, dtype=np.int64)
+    if diffuse_frac > 0.0:
+        n_noisy = int(round(diffuse_frac * F))
+        noisy = np.sort(rng.choice(F, size=n_noisy, replace=False)).astype(np.int64)
+        X[noisy] += np.sqrt(diffuse_var) * _cn(rng, (n_noisy, T, M))
+    return Mixture(X=X.astype(np.complex64), W=W, H=H, G=G, Q=Q, noisy_bins=noisy)
+
+
+def make_state(F: int, T: int, M: int, N: int, K: int, seed: int):
+    """A random positive starting state (not the truth) for parity tests:
+    W, H ~ U(0.2, 1.2), g~ rows ~ Dirichlet(1) + 0.05 renormalised, Q_f = I + 0.2 Z.
+    Returned already rounded to the library's storage types (float32 / complex64)."""
+    rng = np.random.default_rng(seed + 7919)
+    W = rng.uniform(0.2, 1.2, size=(N, K, F)).astype(np.float32)
+    H = rng.uniform(0.2, 1.2, size=(N, K, T)).astype(np.float32)
+    G = rng.dirichlet(np.ones(M), size=(N, F)) + 0.05
+    G = (G / G.sum(axis=2, keepdims=True)).astype(np.float32)
+    Q = (np.eye(M)[None] + 0.2 * _cn(rng, (F, M, M))).astype(np.complex64)
+    return W, H, G, Q
+
+
+# Workload shapes (M channels, N sources, K bases, F bins, T frames, iterations).
+CONFIGS = {
+    "c0": dict(M=2, N=2, K=8, F=257, T=200, iters=20, diffuse=0.0),
+    "c1": dict(M=4, N=4, K=32, F=513, T=640, iters=100, diffuse=0.1),
+    "c2": dict(M=8, N=6, K=64, F=1025, T=4096, iters=1, diffuse=0.0),
+}
+
+
+def config_mixture(name: str, seed: int = 0) -> Mixture:
+    c = CONFIGS[name]
+    return make_mixture(c["F"], c["T"], c["M"], c["N"], c["K"], seed, diffuse_frac=c["diffuse"])
