@@ -1,0 +1,337 @@
+"""FastMNMF throughput on GB300: TF-bin*iterations per second.
+
+One step = one whole FastMNMF job on the paper-scale single mixture (M=4 channels, N=4
+sources, K=32 bases, F=513 bins, T=640 frames, 10 % of the bins with diffuse noise):
+restore the seeded initial state, 100 iterations (W, H, g~ MU, V + IP, x~, normalisation,
+log-likelihood), then the multichannel Wiener separation, all on device-resident data.  L2 is flushed (a 512 MB
+write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank runs its own mixture (seed + rank): the
+mixtures are independent problems, so the units shard with no collective ("weak").
+--impl reference times the float64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FastMNMF TF-bin·iters/s vs plain FP32 on 1 GB300; serving p50/p99 latency"
+UNIT = "TF-bin·iters/s"
+WORKLOAD = dict(M=4, N=4, K=32, F=513, T=640, iters=100, diffuse=0.1)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz = 80.5 TFLOP/s
+
+
+def kernel_flops(kind: str, F, T, M, N, K) -> float:
+    """Algorithmic FLOPs of one launch of a kernel class (per TF bin x F*T)."""
+    ft = F * T
+    mm = M * M
+    per_point = {
+        # A, B (M rcp + 3M mul), P, R (4NM), contraction over t (4NK)
+        "w_update": 4 * N * K + 4 * N * M + 4 * M,
+        # lambda (2NK), y~ (2NM), A, B, P, R as above, contraction over f (4NK)
+        "h_update": 6 * N * K + 6 * N * M + 4 * M,
+        # lambda (2NK), y~ (2NM), A, B (4M), num/den over t (4NM)
+        "g_update": 2 * N * K + 6 * N * M + 4 * M,
+        # lambda, y~, 1/y~, x x^H (3 M^2), V accumulation (2 M * M^2)
+        "scm_ip": 2 * N * K + 2 * N * M + M + 3 * mm + 2 * M * mm,
+        # Q x (8 M^2), |.|^2, LL term (4M)
+        "xt_loglik": 8 * mm + 7 * M,
+    }
+    return float(per_point.get(kind, 0)) * ft
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def read_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary (None if not captured)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == workload:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str | None):
+        self.dev_id = dev_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.dev_id:
+            cmd += ["-i", self.dev_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_iteration_rate(mix, W, H, G, Q, n_iter: int):
+    """Times the float64 oracle (as it stands) on the host; returns (rate, cores, seconds)."""
+    from oracle import fastmnmf_oracle as O
+    X = mix.X.astype(np.complex128)
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.iterate(X, W.astype(np.float64), H.astype(np.float64), G.astype(np.float64), Q.astype(np.complex128),
+              n_iter=n_iter)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    F, T = X.shape[0], X.shape[1]
+    return F * T * n_iter / wall, max(1, int(math.ceil(cpu / wall - 0.05))), wall
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1903_03237_gb300.synth import make_mixture, make_state
+    w = WORKLOAD
+    mix = make_mixture(w["F"], w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
+    W, H, G, Q = make_state(w["F"], w["T"], w["M"], w["N"], w["K"], 0)
+    for _ in range(args.warmup):
+        oracle_iteration_rate(mix, W, H, G, Q, 1)
+    rates, secs, cores = [], [], 1
+    for _ in range(args.steps):
+        r, c, s = oracle_iteration_rate(mix, W, H, G, Q, 1)
+        rates.append(r)
+        secs.append(s)
+        cores = max(cores, c)
+    value = w["F"] * w["T"] * args.steps / sum(secs)
+    sample = f"1 oracle iteration of the {w['F']}x{w['T']} M{w['M']} N{w['N']} K{w['K']} mixture per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def _config():
+    w = WORKLOAD
+    return {"workload": f"paper-scale single mixture M{w['M']} N{w['N']} K{w['K']} F{w['F']} T{w['T']}, "
+                        f"{w['iters']} iterations + Wiener separation per step",
+            "M": w["M"], "N": w["N"], "K": w["K"], "F": w["F"], "T": w["T"], "iters_per_step": w["iters"],
+            "l2": "flushed between timed steps (512 MB write)", "precision": "plain FP32 (float64 IP solve)"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1903_03237_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    from paper_1903_03237_gb300.synth import make_mixture, make_state
+
+    w = WORKLOAD
+    F, T, M, N, K, iters = w["F"], w["T"], w["M"], w["N"], w["K"], w["iters"]
+    mix = make_mixture(F, T, M, N, K, seed=rank, diffuse_frac=w["diffuse"])
+    stream = torch.cuda.Stream()
+    Xd = torch.from_numpy(mix.X).cuda()
+    torch.cuda.synchronize()
+    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream)
+    out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():  # one whole job: fresh initial state, 100 iterations, Wiener separation
+        ctx.restart()
+        ctx.iterate(iters)
+        ctx.separate(out)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    ctx.set_timing(True)
+    for _ in range(args.warmup):  # capture the timed graph variant before the timed region
+        step()
+    ctx.sync()
+    ctx.kernel_times()
+    dev_id = None
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = None
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_id) as clocks:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ctx.sync()
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    kt = ctx.kernel_times()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = F * T * iters * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    dom = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / kt[dom][1]
+    flops = kernel_flops(dom, F, T, M, N, K)
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = read_traffic(dom, "c1")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "avg_launch_us": avg_ms * 1e3,
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz"}
+    shares = {k: round(v[0] / max(1e-12, sum(x[0] for x in kt.values())), 4) for k, v in kt.items() if v[1]}
+
+    # end to end through the C ABI with host buffers: H2D mixture, 100 iterations, D2H images
+    ctx.set_timing(False)
+    Xh = np.ascontiguousarray(mix.X)
+    outh = np.empty((N, F, T, M), dtype=np.complex64)
+    ctx.reset(Xh, seed=rank)
+    ctx.iterate(iters)
+    ctx.separate(outh)
+    e2e_s = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.reset(Xh, seed=rank)
+        ctx.iterate(iters)
+        ctx.separate(outh)  # synchronises (host output)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_val = F * T * iters * len(e2e_s) * world / e2e_total
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        W0, H0, G0, Q0 = make_state(F, T, M, N, K, 0)
+        r, cores, secs = oracle_iteration_rate(mix, W0, H0, G0, Q0, 2)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"2 oracle iterations of the same {F}x{T} mixture ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config() | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": F * T * M * 8,
+                    "d2h_bytes_per_step": N * F * T * M * 8},
+            "gpu_launches": launches, "clocks": clocks.summary(),
+            "kernel_share": shares,
+            "kernel_avg_us": {k: round(1e3 * v[0] / v[1], 2) for k, v in kt.items() if v[1]},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * fastmnmf.h — C ABI of libfastmnmf.so, a GB300 (sm_103a) implementation of FastMNMF:
+ * Sekiguchi, Nugraha, Bando, Yoshii, "Fast Multichannel Source Separation Based on
+ * Jointly Diagonalizable Spatial Covariance Matrices", EUSIPCO 2019 (arXiv 1903.03237).
+ *
+ * Problem (Sec. II-A-1, Eqs. 1-2; Sec. III-A-1, Eq. 16): an observed multichannel STFT
+ * X in C^{F x T x M} is a sum of N source images x_ftn ~ CN(0, lambda_ftn G_nf) whose
+ * spatial covariances are jointly diagonalised per bin, Q_f G_nf Q_f^H = Diag(g~_nf),
+ * with NMF source PSDs lambda_ftn = sum_k w_nkf h_nkt (Sec. II-B-2, Eq. 9).  The library
+ * estimates W, H, g~ and Q by the convergence-guaranteed MM + iterative-projection
+ * algorithm of Sec. III (Eqs. 17-24) and separates the sources with the multichannel
+ * Wiener filter of Eq. 3.
+ *
+ * Conventions for every call:
+ *  - Layouts are row-major, last index fastest.  Complex numbers are (re, im) pairs of
+ *    the stated real type, interleaved.
+ *      X    complex64  [F][T][M]          observed mixture
+ *      W    float32    [N][K][F]          NMF bases        w_nkf >= 0
+ *      H    float32    [N][K][T]          NMF activations  h_nkt >= 0
+ *      G    float32    [N][F][M]          diagonal SCMs    g~_nfm >= 0
+ *      Q    complex64  [F][M][M]          diagonalisers; row m of Q_f is q_fm^H (Eq. 16)
+ *      out  complex64  [N][F][T][M]       separated source images (all M channels)
+ *  - Pointers marked "host" are ordinary host memory; "device" pointers are CUDA device
+ *    memory of the current device and must be 16-byte aligned.  Device inputs are read on
+ *    the context stream: the caller must have completed (or ordered before that stream)
+ *    whatever work produces them; device outputs are ready once the context stream has
+ *    passed the call.
+ *  - Ownership: the caller owns every buffer it passes; the library copies what it
+ *    needs during the call (device->device for device inputs) and never keeps a caller
+ *    pointer.  The context owns all device state until fmnmf_destroy.
+ *  - Errors: every call returns an fmnmf_status and never aborts.  Argument errors
+ *    (FMNMF_EINVAL) change no state.  Errors found on the device (non-finite values, a
+ *    singular IP system) are recorded in a device status word, reported by the next
+ *    synchronising call (fmnmf_sync, fmnmf_loglik, fmnmf_get_state, fmnmf_separate) and
+ *    stay sticky until fmnmf_set_state or fmnmf_reset.  fmnmf_last_error gives a
+ *    message.
+ *  - Threads: a context is used by one host thread at a time; separate contexts are
+ *    independent.  All device work is ordered on the context's stream.
+ */
+#ifndef FASTMNMF_H
+#define FASTMNMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmnmf_ctx fmnmf_ctx;
+
+typedef enum {
+  FMNMF_OK = 0,
+  FMNMF_EINVAL = 1,      /* bad argument (shape, pointer, option)                  */
+  FMNMF_ENOMEM = 2,      /* device allocation failed or over the HBM budget         */
+  FMNMF_ECUDA = 3,       /* a CUDA runtime call failed                              */
+  FMNMF_ENONFINITE = 4,  /* NaN/Inf in the input or produced by an update           */
+  FMNMF_ESINGULAR = 5,   /* an IP system (Q_f V_fm) had a vanishing pivot            */
+  FMNMF_ETIMEOUT = 6,    /* a bounded device wait expired                           */
+  FMNMF_EBUSY = 7        /* resource (server slot) not available now                */
+} fmnmf_status;
+
+/* Blocks of the update (Sec. III): W (Eq. 23), H (Eq. 24), g~ (Eq. 21), Q (Eqs. 18-20). */
+enum { FMNMF_UPDATE_W = 1, FMNMF_UPDATE_H = 2, FMNMF_UPDATE_G = 4, FMNMF_UPDATE_Q = 8,
+       FMNMF_UPDATE_ALL = 15 };
+
+/* Arithmetic of the contractions.  FP32: every sum in float32 on CUDA cores, the M x M
+ * IP solves and log|det Q_f|^2 in float64.  BF16 / TF32: the NMF and SCM contractions on
+ * the tensor cores with float32 accumulation (same float64 IP). */
+enum { FMNMF_PREC_FP32 = 0, FMNMF_PREC_BF16 = 1, FMNMF_PREC_TF32 = 2 };
+
+typedef struct {
+  int precision;          /* FMNMF_PREC_*                                      (default FP32) */
+  unsigned update_mask;   /* FMNMF_UPDATE_* bits applied by fmnmf_iterate      (default ALL)  */
+  int normalise;          /* 1: scale normalisation after each iteration       (default 1)    */
+  void* stream;           /* cudaStream_t for all device work; NULL = a private stream        */
+  size_t hbm_budget;      /* 0 = unlimited; else init fails with ENOMEM above it              */
+} fmnmf_opts;
+
+/* Fills *opts with the defaults above. */
+fmnmf_status fmnmf_default_opts(fmnmf_opts* opts);
+
+/*
+ * Creates a context for one mixture and sets the initial state.
+ *  X           complex64 [F][T][M], host (x_on_device = 0) or device (x_on_device = 1).
+ *              Must be finite (checked; FMNMF_ENONFINITE otherwise).
+ *  F, T        >= 1 bins and frames; M in [1, 8] channels; N >= 1 sources; K >= 1 bases.
+ *  seed        initial state (the paper fixes none for FastMNMF; Sec. IV-A only gives
+ *              one for its DP experiments):  with u_i the i-th output of the counter-based
+ *              SplitMix64 stream of `seed` (output i = mix(seed + (i+1)*0x9E3779B97F4A7C15),
+ *              top 53 bits / 2^53), W[n][k][f] = 0.1 + u_{(nK+k)F+f},
+ *              H[n][k][t] = 0.1 + u_{NKF+(nK+k)T+t}; g~[n][f][m] = (m == n mod M ? 1 : 0.01)
+ *              divided by its sum over m; Q_f = I.
+ *  opts        may be NULL (defaults).
+ * On success *out receives the context; x~, y~ and the log-likelihood of the initial state
+ * are computed.  Device memory: about (8 + 4 + 4) F T M + 4 N K (F + T) bytes + scratch.
+ */
+fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, int T, int M,
+                        int N, int K, uint64_t seed, const fmnmf_opts* opts);
+
+/* Replaces the mixture of an existing context (same F, T, M) and re-initialises the state
+ * from `seed` as fmnmf_init does, reusing the context's device memory. */
+fmnmf_status fmnmf_reset(fmnmf_ctx* ctx, const void* X, int x_on_device, uint64_t seed);
+
+/* Restores the state the context had right after its last fmnmf_init, fmnmf_reset or
+ * fmnmf_set_state (device-side copies, asynchronous on the context stream) and clears the
+ * error word: the next fmnmf_iterate starts a fresh estimation of the same mixture. */
+fmnmf_status fmnmf_restart(fmnmf_ctx* ctx);
+
+/*
+ * Runs n_iter >= 0 iterations of FastMNMF (Sec. III-C-2: NMF source model in the jointly
+ * diagonalisable spatial model).  One iteration, in this order, each block from the
+ * current parameters (so each is an exact MM / IP step and Eq. 17 never decreases):
+ *   W  <- W * sqrt(num/den)                                   (Eq. 23)
+ *   H  <- H * sqrt(num/den)                                   (Eq. 24)
+ *   g~ <- g~ * sqrt(num/den)                                  (Eq. 21)
+ *   for m = 1..M:  q_fm <- (Q_f V_fm)^-1 e_m,  q_fm /= sqrt(q^H V_fm q)   (Eqs. 18-20)
+ *   x~ <- |Q_f x_ft|^2; scale normalisation (if opts.normalise):
+ *     Q_f /= sqrt(tr(Q_f Q_f^H)/M), g~_nf scaled to match; g~_nf /= sum_m g~_nfm with
+ *     w_nkf scaled to match; w_nk /= sum_f w_nkf with h_nk scaled to match
+ *   (these leave every y~ and the log-likelihood unchanged);
+ *   log-likelihood of the new state (Eq. 17).
+ * Asynchronous: enqueued on the context stream; device errors surface at the next
+ * synchronising call.
+ */
+fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter);
+
+/* Waits for the context stream and reports any device-side error. */
+fmnmf_status fmnmf_sync(fmnmf_ctx* ctx);
+
+/* Synchronises and returns the log-likelihood of the current state: Eq. 17 including the
+ * constant -F T M log(pi) that the paper's "=c" drops (the true log-density of Eq. 2). */
+fmnmf_status fmnmf_loglik(fmnmf_ctx* ctx, double* ll);
+
+/*
+ * Multichannel Wiener filter, Eq. 3, in diagonalised form (Eq. 16 substituted):
+ *   x_ftn = Q_f^-1 ( (lambda_ftn g~_nf / y~_ft) (elementwise) Q_f x_ft )
+ * for every source n and every channel.  out: complex64 [N][F][T][M], host
+ * (out_on_device = 0; the call synchronises) or device (asynchronous).
+ */
+fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device);
+
+/* Copies the state to host buffers (any may be NULL).  Synchronises. */
+fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void* Q);
+
+/* Sets the state from host buffers (all four required, finite, W/H/G >= 0, Q_f
+ * non-singular), recomputes x~, y~ and the log-likelihood and clears the error word. */
+fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, const float* G,
+                             const void* Q);
+
+/* Shapes of a context (any pointer may be NULL). */
+fmnmf_status fmnmf_shape(const fmnmf_ctx* ctx, int* F, int* T, int* M, int* N, int* K);
+
+/* Frees the context and its device memory.  NULL is accepted. */
+fmnmf_status fmnmf_destroy(fmnmf_ctx* ctx);
+
+/* Message for the last error on ctx (or of the calling thread when ctx is NULL). */
+const char* fmnmf_last_error(const fmnmf_ctx* ctx);
+
+/*
+ * Kernel timing, for measurement only.  While enabled, every launch made by
+ * fmnmf_iterate / fmnmf_separate is bracketed by CUDA events on the context stream.
+ * fmnmf_kernel_times synchronises and returns, for each kernel class i < *n (names from
+ * fmnmf_kernel_name), the summed milliseconds and launch count since the last reset.
+ */
+fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int enable);
+fmnmf_status fmnmf_kernel_times(fmnmf_ctx* ctx, double* ms, long long* launches, int* n);
+const char* fmnmf_kernel_name(int i);
+
+/* Number of kernel launches this context has enqueued since creation. */
+long long fmnmf_launch_count(const fmnmf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTMNMF_H */

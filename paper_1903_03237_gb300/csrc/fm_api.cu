@@ -1,0 +1,664 @@
+// Host runtime of libfastmnmf.so: the C ABI declared in include/fastmnmf.h.
+//
+// A context owns one device arena (a single cudaMalloc) holding the mixture, the state
+// and the scratch of the split reductions, the tiling of every launch, and a cache of
+// CUDA graphs (one per chunk length of fmnmf_iterate) so that an iteration costs one
+// graph launch instead of five kernel launches from the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fastmnmf.h"
+#include "fm_kernels.cuh"
+#include "fm_launch.h"
+
+namespace {
+
+using namespace fm;
+
+thread_local std::string g_thread_err;
+
+constexpr int kMaxChunk = 100;          // iterations per captured graph
+constexpr int kSmemTarget = 100 * 1024;  // bytes per CTA aimed for (two CTAs per SM)
+constexpr int kSmemMax = 220 * 1024;     // hard ceiling (227 KB per CTA on sm_103a)
+
+const char* kKindNames[KK_COUNT] = {"w_update", "h_update", "g_update", "scm", "xt_loglik",
+                                    "prep_q", "wiener", "ip"};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;  // (kind, start/end)
+  int launches = 0;
+  bool unharvested = false;  // timing graphs: events hold a launch not yet accumulated
+};
+
+}  // namespace
+
+struct fmnmf_ctx {
+  int F = 0, T = 0, M = 0, N = 0, K = 0, maxm = 0;
+  fmnmf_opts opts{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  Prob p{};
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  Geom gW{}, gH{}, gG{}, gY{}, gS{};
+  size_t smW = 0, smH = 0, smG = 0, smY = 0, smS = 0;
+  int n_pt_blocks = 0, n_mu_blocks = 0;
+  unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
+  // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
+  float* W0 = nullptr;
+  float* H0 = nullptr;
+  float* G0 = nullptr;
+  double2* Q0 = nullptr;
+  std::map<std::pair<int, int>, GraphEntry> graphs;  // (chunk, timing) -> graph
+  std::string err;
+  bool timing = false;
+  double ms[KK_COUNT] = {0};
+  long long cnt[KK_COUNT] = {0};
+  long long launches = 0;
+  // events for timed direct launches (separate)
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+fmnmf_status set_err(fmnmf_ctx* c, fmnmf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_thread_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(ctx, FMNMF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
+int bucket(int M) { return M <= 2 ? 2 : (M <= 4 ? 4 : 8); }
+
+cudaError_t launch(fmnmf_ctx* c, KernelKind k, const LaunchArgs& a) {
+  c->launches++;
+  switch (c->maxm) {
+    case 2: return launch_m2(k, a);
+    case 4: return launch_m4(k, a);
+    default: return launch_m8(k, a);
+  }
+}
+
+cudaError_t configure(int maxm, int bytes) {
+  switch (maxm) {
+    case 2: return configure_m2(bytes);
+    case 4: return configure_m4(bytes);
+    default: return configure_m8(bytes);
+  }
+}
+
+// Tiling of a sweep over an own extent SO (tiles of kOT) and an inner extent SI split
+// S ways so that the grid has about `target` CTAs; sub-chunks of at most ic_cap.
+Geom make_geom(int SO, int SI, int ic_cap, int target) {
+  Geom g;
+  g.n_own_tiles = (SO + kOT - 1) / kOT;
+  int S = std::max(1, (target + g.n_own_tiles - 1) / g.n_own_tiles);
+  S = std::min(S, (SI + 3) / 4);
+  int span = (SI + S - 1) / S;
+  span = (span + 3) & ~3;
+  g.S = (SI + span - 1) / span;
+  g.span = span;
+  g.IC = std::min(ic_cap, span);
+  g.ICP = g.IC + 4;
+  return g;
+}
+
+// Largest sub-chunk (multiple of 4, <= 256) whose shared memory fits `limit` bytes.
+int ic_cap_for(int mode, int N, int K, int M, int maxm, int limit) {
+  for (int ic = 256; ic >= 4; ic -= 4) {
+    size_t bytes = (size_t)tile_smem(mode, N, K, M, maxm, ic).total * 4;
+    if (bytes <= (size_t)limit) return ic;
+  }
+  return 0;
+}
+
+size_t smem_bytes(int mode, int N, int K, int M, int maxm, int ic) {
+  size_t b = (size_t)tile_smem(mode, N, K, M, maxm, ic).total * 4;
+  return b;
+}
+
+size_t sep_smem_bytes(int N, int K, int M, int maxm, int ic) {
+  const int NK = N * K, ICP = ic + 4;
+  size_t fl = (size_t)NK * kOT + (size_t)NK * ICP + (((size_t)N * kOT * M + 3) & ~(size_t)3) +
+              (size_t)N * kOT * ICP;
+  return fl * 4 + 2 * (size_t)kOT * maxm * maxm * sizeof(float2);
+}
+
+fmnmf_status plan(fmnmf_ctx* ctx) {
+  const int F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K, mx = ctx->maxm;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int target = 2 * sms;
+  int caps[4];
+  for (int mode = 0; mode < 4; ++mode) {
+    int cap = ic_cap_for(mode, N, K, M, mx, kSmemTarget);
+    if (cap == 0) cap = ic_cap_for(mode, N, K, M, mx, kSmemMax);
+    if (cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K = %d too large for the shared-memory tiles", N * K);
+    caps[mode] = cap;
+  }
+  ctx->gW = make_geom(F, T, caps[MODE_W], target);
+  ctx->gH = make_geom(T, F, caps[MODE_H], target);
+  ctx->gG = make_geom(F, T, caps[MODE_G], target);
+  ctx->gY = make_geom(F, T, caps[MODE_Y], target);
+  ctx->smW = smem_bytes(MODE_W, N, K, M, mx, ctx->gW.IC);
+  ctx->smH = smem_bytes(MODE_H, N, K, M, mx, ctx->gH.IC);
+  ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC);
+  ctx->smY = smem_bytes(MODE_Y, N, K, M, mx, ctx->gY.IC);
+  int sep_cap = 0;
+  for (int ic = 256; ic >= 4; ic -= 4)
+    if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemTarget) { sep_cap = ic; break; }
+  if (sep_cap == 0)
+    for (int ic = 256; ic >= 4; ic -= 4)
+      if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemMax) { sep_cap = ic; break; }
+  if (sep_cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K too large for the Wiener tiles");
+  ctx->gS = make_geom(F, T, sep_cap, target);
+  ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC);
+  size_t mx_smem = std::max({ctx->smW, ctx->smH, ctx->smG, ctx->smY, ctx->smS});
+  CK(configure(mx, (int)std::max<size_t>(mx_smem, 48 * 1024)));
+  ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
+  ctx->n_mu_blocks = (N * K + (kThreads / 32) - 1) / (kThreads / 32);
+  return FMNMF_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+fmnmf_status allocate(fmnmf_ctx* ctx) {
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  const int mx = ctx->maxm;
+  size_t part = 0;
+  part = std::max(part, (size_t)ctx->gW.S * tile_part_floats(MODE_W, F, T, M, N, K, mx));
+  part = std::max(part, (size_t)ctx->gH.S * tile_part_floats(MODE_H, F, T, M, N, K, mx));
+  part = std::max(part, (size_t)ctx->gG.S * tile_part_floats(MODE_G, F, T, M, N, K, mx));
+  part = std::max(part, (size_t)ctx->gY.S * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
+  const unsigned nctr = ctx->gW.n_own_tiles + ctx->gH.n_own_tiles + ctx->gG.n_own_tiles +
+                        ctx->gY.n_own_tiles + 1;
+  ctx->ctrW = 0;
+  ctx->ctrH = ctx->ctrW + ctx->gW.n_own_tiles;
+  ctx->ctrG = ctx->ctrH + ctx->gH.n_own_tiles;
+  ctx->ctrY = ctx->ctrG + ctx->gG.n_own_tiles;
+  ctx->ctrLL = ctx->ctrY + ctx->gY.n_own_tiles;
+  struct Slot { void** dst; size_t bytes; };
+  Prob& p = ctx->p;
+  void* X = nullptr;
+  std::vector<Slot> slots = {
+      {&X, F * T * M * sizeof(float2)},
+      {(void**)&p.W, N * K * F * 4},
+      {(void**)&p.H, N * K * T * 4},
+      {(void**)&p.G, N * F * M * 4},
+      {(void**)&p.Qd, F * M * M * sizeof(double2)},
+      {(void**)&p.Qf, F * M * M * sizeof(float2)},
+      {(void**)&p.Qinv, F * M * M * sizeof(float2)},
+      {(void**)&p.xt, F * T * M * 4},
+      {(void**)&p.yt, F * T * M * 4},
+      {(void**)&p.logdet, F * 8},
+      {(void**)&p.phi, F * 4},
+      {(void**)&p.ll, 8},
+      {(void**)&p.status, 4},
+      {(void**)&p.part, part * 4},
+      {(void**)&p.llpart, (size_t)ctx->n_pt_blocks * 8},
+      {(void**)&p.counters, (size_t)nctr * 4},
+      {(void**)&ctx->W0, N * K * F * 4},
+      {(void**)&ctx->H0, N * K * T * 4},
+      {(void**)&ctx->G0, N * F * M * 4},
+      {(void**)&ctx->Q0, F * M * M * sizeof(double2)},
+  };
+  size_t total = 0;
+  for (auto& s : slots) total += align256(s.bytes);
+  if (ctx->opts.hbm_budget && total > ctx->opts.hbm_budget)
+    return set_err(ctx, FMNMF_ENOMEM, "needs %zu bytes of device memory, budget %zu", total,
+                   ctx->opts.hbm_budget);
+  cudaError_t e = cudaMalloc(&ctx->arena, total);
+  if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+  ctx->arena_bytes = total;
+  char* base = (char*)ctx->arena;
+  for (auto& s : slots) { *s.dst = base; base += align256(s.bytes); }
+  p.X = (const float2*)X;
+  p.F = ctx->F; p.T = ctx->T; p.M = ctx->M; p.N = ctx->N; p.K = ctx->K;
+  CK(cudaMemsetAsync(p.counters, 0, (size_t)nctr * 4, ctx->st));
+  CK(cudaMemsetAsync(p.status, 0, 4, ctx->st));
+  return FMNMF_OK;
+}
+
+// ---- launches ----------------------------------------------------------------------
+LaunchArgs tile_args(fmnmf_ctx* c, const Geom& g, size_t smem, int flags, unsigned ctr) {
+  LaunchArgs a;
+  a.p = c->p; a.g = g; a.smem = smem; a.st = c->st; a.flags = flags; a.ctr = ctr;
+  a.grid = dim3(g.n_own_tiles, g.S);
+  return a;
+}
+
+struct Recorder {  // brackets launches with events when timing is on (works under capture)
+  fmnmf_ctx* c;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* out;
+  cudaEvent_t take() {
+    cudaEvent_t e;
+    if (!c->evpool.empty()) { e = c->evpool.back(); c->evpool.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+  }
+  cudaError_t run(KernelKind k, const LaunchArgs& a) {
+    if (!out) return launch(c, k, a);
+    cudaEvent_t e0 = take(), e1 = take();
+    // under stream capture the records must be External to become event-record nodes
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(c->st, &cs);
+    if (r != cudaSuccess) return r;
+    const unsigned fl = (cs == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if ((r = cudaEventRecordWithFlags(e0, c->st, fl)) != cudaSuccess) return r;
+    if ((r = launch(c, k, a)) != cudaSuccess) return r;
+    if ((r = cudaEventRecordWithFlags(e1, c->st, fl)) != cudaSuccess) return r;
+    out->push_back({(int)k, {e0, e1}});
+    return cudaSuccess;
+  }
+};
+
+cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
+  const unsigned mask = c->opts.update_mask;
+  const int norm = c->opts.normalise ? FLAG_NORMALISE : 0;
+  cudaError_t e;
+  if (mask & FMNMF_UPDATE_W)
+    if ((e = rec.run(KK_W, tile_args(c, c->gW, c->smW, 0, c->ctrW))) != cudaSuccess) return e;
+  if (mask & FMNMF_UPDATE_H)
+    if ((e = rec.run(KK_H, tile_args(c, c->gH, c->smH, 0, c->ctrH))) != cudaSuccess) return e;
+  if (mask & FMNMF_UPDATE_G)
+    if ((e = rec.run(KK_G, tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG))) != cudaSuccess) return e;
+  const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
+  if ((e = rec.run(KK_Y, tile_args(c, c->gY, c->smY, yflags, c->ctrY))) != cudaSuccess) return e;
+  if (yflags) {
+    LaunchArgs a;
+    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
+    a.grid = dim3((c->F + kIpWarps - 1) / kIpWarps);
+    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
+  }
+  LaunchArgs x;
+  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+  x.n_pt_blocks = c->n_pt_blocks;
+  x.apply_phi = (yflags != 0);
+  x.do_mu = norm ? 1 : 0;
+  x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
+  return rec.run(KK_XT, x);
+}
+
+// x~, y~, log-det and log-likelihood of the state currently on the device.
+fmnmf_status refresh_state(fmnmf_ctx* ctx) {
+  LaunchArgs a;
+  a.p = ctx->p; a.st = ctx->st;
+  a.grid = dim3((ctx->F + 7) / 8);
+  a.prep_mode = 0;
+  CK(launch(ctx, KK_PREP, a));
+  CK(launch(ctx, KK_Y, tile_args(ctx, ctx->gY, ctx->smY, 0, ctx->ctrY)));
+  LaunchArgs x;
+  x.p = ctx->p; x.st = ctx->st; x.ctr = ctx->ctrLL; x.n_pt_blocks = ctx->n_pt_blocks;
+  x.apply_phi = 0; x.do_mu = 0; x.grid = dim3(ctx->n_pt_blocks);
+  CK(launch(ctx, KK_XT, x));
+  return FMNMF_OK;
+}
+
+// Copies the current state (W, H, G, Q) to the restart snapshot, or back from it.
+fmnmf_status snapshot(fmnmf_ctx* ctx, bool restore) {
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  struct { void* live; void* snap; size_t bytes; } c[4] = {
+      {ctx->p.W, ctx->W0, N * K * F * 4}, {ctx->p.H, ctx->H0, N * K * T * 4},
+      {ctx->p.G, ctx->G0, N * F * M * 4}, {ctx->p.Qd, ctx->Q0, F * M * M * sizeof(double2)}};
+  for (auto& e : c)
+    CK(cudaMemcpyAsync(restore ? e.live : e.snap, restore ? e.snap : e.live, e.bytes,
+                       cudaMemcpyDeviceToDevice, ctx->st));
+  return FMNMF_OK;
+}
+
+fmnmf_status check_status(fmnmf_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, ctx->p.status, 4, cudaMemcpyDeviceToHost));
+  if (st & ST_SINGULAR) return set_err(ctx, FMNMF_ESINGULAR, "singular IP system or diagonaliser (device status 0x%x)", st);
+  if (st & ST_NONFINITE) return set_err(ctx, FMNMF_ENONFINITE, "non-finite value produced on the device (status 0x%x)", st);
+  if (st & ST_TIMEOUT) return set_err(ctx, FMNMF_ETIMEOUT, "device wait timed out (status 0x%x)", st);
+  return FMNMF_OK;
+}
+
+void harvest(fmnmf_ctx* c, std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>& ev, bool release) {
+  for (auto& k : ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, k.second.first, k.second.second) == cudaSuccess) {
+      c->ms[k.first] += ms;
+      c->cnt[k.first] += 1;
+    }
+    if (release) { c->evpool.push_back(k.second.first); c->evpool.push_back(k.second.second); }
+  }
+  if (release) ev.clear();
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), counter form: output i of the stream seeded
+// with s is mix(s + (i + 1) * 0x9E3779B97F4A7C15).
+inline uint64_t sm64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+fmnmf_status load_x(fmnmf_ctx* ctx, const void* X, int x_on_device) {
+  const size_t nfl = (size_t)ctx->F * ctx->T * ctx->M * 2;
+  if (!X) return set_err(ctx, FMNMF_EINVAL, "X is NULL");
+  if (x_on_device) {
+    CK(cudaMemcpyAsync((void*)ctx->p.X, X, nfl * 4, cudaMemcpyDeviceToDevice, ctx->st));
+    // finiteness check on the device copy: reuse the host path on a staged copy
+    std::vector<float> h(nfl);
+    CK(cudaMemcpyAsync(h.data(), ctx->p.X, nfl * 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (size_t i = 0; i < nfl; ++i)
+      if (!std::isfinite(h[i])) return set_err(ctx, FMNMF_ENONFINITE, "X has a non-finite value at float %zu", i);
+  } else {
+    const float* h = (const float*)X;
+    for (size_t i = 0; i < nfl; ++i)
+      if (!std::isfinite(h[i])) return set_err(ctx, FMNMF_ENONFINITE, "X has a non-finite value at float %zu", i);
+    CK(cudaMemcpyAsync((void*)ctx->p.X, X, nfl * 4, cudaMemcpyHostToDevice, ctx->st));
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status seed_state(fmnmf_ctx* ctx, uint64_t seed) {
+  const int F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  const size_t nw = (size_t)N * K * F, nh = (size_t)N * K * T;
+  std::vector<float> W(nw), H(nh), G((size_t)N * F * M);
+  std::vector<double2> Q((size_t)F * M * M);
+  for (size_t i = 0; i < nw; ++i) W[i] = (float)(0.1 + (double)(sm64(seed, i) >> 11) * 0x1.0p-53);
+  for (size_t i = 0; i < nh; ++i) H[i] = (float)(0.1 + (double)(sm64(seed, nw + i) >> 11) * 0x1.0p-53);
+  for (int n = 0; n < N; ++n) {
+    double sum = 0.0;
+    for (int m = 0; m < M; ++m) sum += (m == n % M) ? 1.0 : 1e-2;
+    for (int f = 0; f < F; ++f)
+      for (int m = 0; m < M; ++m) G[((size_t)n * F + f) * M + m] = (float)(((m == n % M) ? 1.0 : 1e-2) / sum);
+  }
+  for (int f = 0; f < F; ++f)
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) Q[((size_t)f * M + i) * M + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  CK(cudaMemcpyAsync(ctx->p.W, W.data(), nw * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.H, H.data(), nh * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.G, G.data(), G.size() * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.Qd, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  // the host vectors die at return: wait for the copies
+  CK(cudaStreamSynchronize(ctx->st));
+  return FMNMF_OK;
+}
+
+void free_ctx(fmnmf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (auto& kv : ctx->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& e : kv.second.ev) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+  }
+  for (auto& e : ctx->pending) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+  for (auto e : ctx->evpool) cudaEventDestroy(e);
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+fmnmf_status fmnmf_default_opts(fmnmf_opts* opts) {
+  if (!opts) return set_err(nullptr, FMNMF_EINVAL, "opts is NULL");
+  opts->precision = FMNMF_PREC_FP32;
+  opts->update_mask = FMNMF_UPDATE_ALL;
+  opts->normalise = 1;
+  opts->stream = nullptr;
+  opts->hbm_budget = 0;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, int T, int M, int N,
+                        int K, uint64_t seed, const fmnmf_opts* opts) {
+  if (!out) return set_err(nullptr, FMNMF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (F < 1 || T < 1 || M < 1 || M > kMaxM || N < 1 || K < 1)
+    return set_err(nullptr, FMNMF_EINVAL, "bad shape F=%d T=%d M=%d N=%d K=%d (need F,T,N,K >= 1, 1 <= M <= 8)", F, T, M, N, K);
+  if ((double)F * T * M > 2.0e9) return set_err(nullptr, FMNMF_EINVAL, "F*T*M too large");
+  if (!X) return set_err(nullptr, FMNMF_EINVAL, "X is NULL");
+  if (opts && opts->precision != FMNMF_PREC_FP32)
+    return set_err(nullptr, FMNMF_EINVAL, "precision %d not available in this build", opts->precision);
+  fmnmf_ctx* ctx = new fmnmf_ctx();
+  ctx->F = F; ctx->T = T; ctx->M = M; ctx->N = N; ctx->K = K; ctx->maxm = bucket(M);
+  if (opts) ctx->opts = *opts; else fmnmf_default_opts(&ctx->opts);
+  if (ctx->opts.update_mask & ~(unsigned)FMNMF_UPDATE_ALL) {
+    const unsigned bad = ctx->opts.update_mask;
+    delete ctx;
+    return set_err(nullptr, FMNMF_EINVAL, "bad update_mask 0x%x", bad);
+  }
+  fmnmf_status s;
+  if (ctx->opts.stream) {
+    ctx->st = (cudaStream_t)ctx->opts.stream;
+  } else {
+    cudaError_t e = cudaStreamCreate(&ctx->st);
+    if (e != cudaSuccess) { delete ctx; return set_err(nullptr, FMNMF_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+    ctx->own_stream = true;
+  }
+  if ((s = plan(ctx)) != FMNMF_OK || (s = allocate(ctx)) != FMNMF_OK || (s = load_x(ctx, X, x_on_device)) != FMNMF_OK ||
+      (s = seed_state(ctx, seed)) != FMNMF_OK || (s = snapshot(ctx, false)) != FMNMF_OK ||
+      (s = refresh_state(ctx)) != FMNMF_OK || (s = check_status(ctx)) != FMNMF_OK) {
+    g_thread_err = ctx->err;
+    free_ctx(ctx);
+    return s;
+  }
+  *out = ctx;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_reset(fmnmf_ctx* ctx, const void* X, int x_on_device, uint64_t seed) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  fmnmf_status s;
+  if ((s = load_x(ctx, X, x_on_device)) != FMNMF_OK) return s;
+  if ((s = seed_state(ctx, seed)) != FMNMF_OK) return s;
+  if ((s = snapshot(ctx, false)) != FMNMF_OK) return s;
+  if ((s = refresh_state(ctx)) != FMNMF_OK) return s;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_restart(fmnmf_ctx* ctx) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  fmnmf_status s;
+  if ((s = snapshot(ctx, true)) != FMNMF_OK) return s;
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  return refresh_state(ctx);
+}
+
+fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (n_iter < 0) return set_err(ctx, FMNMF_EINVAL, "n_iter < 0");
+  while (n_iter > 0) {
+    const int chunk = std::min(n_iter, kMaxChunk);
+    auto key = std::make_pair(chunk, ctx->timing ? 1 : 0);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+      GraphEntry ge;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+      Recorder rec{ctx, ctx->timing ? &ge.ev : nullptr};
+      const long long before = ctx->launches;
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = enqueue_iteration(ctx, rec);
+      ge.launches = (int)(ctx->launches - before);
+      ctx->launches = before;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->st, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return set_err(ctx, FMNMF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      CK(cudaGraphInstantiate(&ge.exec, g, 0));
+      cudaGraphDestroy(g);
+      it = ctx->graphs.emplace(key, std::move(ge)).first;
+    }
+    GraphEntry& ge = it->second;
+    if (ctx->timing && ge.unharvested) {
+      // the events of this graph still hold its previous launch: wait for that launch
+      // only (work queued after it keeps the device busy) and accumulate it
+      CK(cudaEventSynchronize(ge.ev.back().second.second));
+      harvest(ctx, ge.ev, false);
+      ge.unharvested = false;
+    }
+    CK(cudaGraphLaunch(ge.exec, ctx->st));
+    ctx->launches += ge.launches;
+    if (ctx->timing) ge.unharvested = true;
+    n_iter -= chunk;
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_sync(fmnmf_ctx* ctx) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_loglik(fmnmf_ctx* ctx, double* ll) {
+  if (!ctx || !ll) return set_err(ctx, FMNMF_EINVAL, "NULL argument");
+  fmnmf_status s = check_status(ctx);
+  if (s != FMNMF_OK) return s;
+  CK(cudaMemcpy(ll, ctx->p.ll, 8, cudaMemcpyDeviceToHost));
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
+  if (!ctx || !out) return set_err(ctx, FMNMF_EINVAL, "NULL argument");
+  const size_t bytes = (size_t)ctx->N * ctx->F * ctx->T * ctx->M * sizeof(float2);
+  float2* dst = (float2*)out;
+  float2* tmp = nullptr;
+  if (!out_on_device) {
+    cudaError_t e = cudaMallocAsync((void**)&tmp, bytes, ctx->st);
+    if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    dst = tmp;
+  }
+  Recorder rec{ctx, ctx->timing ? &ctx->pending : nullptr};
+  LaunchArgs a;
+  a.p = ctx->p; a.st = ctx->st; a.grid = dim3((ctx->F + 7) / 8); a.prep_mode = 1;
+  cudaError_t e = rec.run(KK_PREP, a);
+  if (e == cudaSuccess) {
+    LaunchArgs s;
+    s.p = ctx->p; s.g = ctx->gS; s.smem = ctx->smS; s.st = ctx->st; s.out = dst;
+    s.grid = dim3(ctx->gS.n_own_tiles, ctx->gS.S);
+    e = rec.run(KK_SEP, s);
+  }
+  if (e != cudaSuccess) {
+    if (tmp) cudaFreeAsync(tmp, ctx->st);
+    return set_err(ctx, FMNMF_ECUDA, "separate launch: %s", cudaGetErrorString(e));
+  }
+  if (!out_on_device) {
+    CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaFreeAsync(tmp, ctx->st));
+    return check_status(ctx);
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void* Q) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->st));
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  if (W) CK(cudaMemcpy(W, ctx->p.W, N * K * F * 4, cudaMemcpyDeviceToHost));
+  if (H) CK(cudaMemcpy(H, ctx->p.H, N * K * T * 4, cudaMemcpyDeviceToHost));
+  if (G) CK(cudaMemcpy(G, ctx->p.G, N * F * M * 4, cudaMemcpyDeviceToHost));
+  if (Q) CK(cudaMemcpy(Q, ctx->p.Qf, F * M * M * sizeof(float2), cudaMemcpyDeviceToHost));
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, const float* G, const void* Q) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (!W || !H || !G || !Q) return set_err(ctx, FMNMF_EINVAL, "set_state needs W, H, G and Q");
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  auto nonneg = [](const float* a, size_t n) {
+    for (size_t i = 0; i < n; ++i) if (!(a[i] >= 0.f) || !std::isfinite(a[i])) return false;
+    return true;
+  };
+  if (!nonneg(W, N * K * F) || !nonneg(H, N * K * T) || !nonneg(G, N * F * M))
+    return set_err(ctx, FMNMF_EINVAL, "W, H and G must be finite and nonnegative");
+  const float* q = (const float*)Q;
+  std::vector<double2> Qd(F * M * M);
+  for (size_t i = 0; i < F * M * M; ++i) {
+    if (!std::isfinite(q[2 * i]) || !std::isfinite(q[2 * i + 1])) return set_err(ctx, FMNMF_EINVAL, "Q must be finite");
+    Qd[i] = make_double2(q[2 * i], q[2 * i + 1]);
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpy(ctx->p.W, W, N * K * F * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->p.H, H, N * K * T * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->p.G, G, N * F * M * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->p.Qd, Qd.data(), Qd.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemset(ctx->p.status, 0, 4));
+  fmnmf_status s = snapshot(ctx, false);
+  if (s != FMNMF_OK) return s;
+  s = refresh_state(ctx);
+  if (s != FMNMF_OK) return s;
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_shape(const fmnmf_ctx* ctx, int* F, int* T, int* M, int* N, int* K) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (F) *F = ctx->F;
+  if (T) *T = ctx->T;
+  if (M) *M = ctx->M;
+  if (N) *N = ctx->N;
+  if (K) *K = ctx->K;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_destroy(fmnmf_ctx* ctx) {
+  free_ctx(ctx);
+  return FMNMF_OK;
+}
+
+const char* fmnmf_last_error(const fmnmf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_thread_err.c_str(); }
+
+fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int enable) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  ctx->timing = enable != 0;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_kernel_times(fmnmf_ctx* ctx, double* ms, long long* launches, int* n) {
+  if (!ctx || !n) return set_err(ctx, FMNMF_EINVAL, "NULL argument");
+  CK(cudaStreamSynchronize(ctx->st));
+  harvest(ctx, ctx->pending, true);
+  for (auto& kv : ctx->graphs)
+    if (kv.second.unharvested) { harvest(ctx, kv.second.ev, false); kv.second.unharvested = false; }
+  const int cap = *n;
+  for (int i = 0; i < KK_COUNT && i < cap; ++i) {
+    if (ms) ms[i] = ctx->ms[i];
+    if (launches) launches[i] = ctx->cnt[i];
+    ctx->ms[i] = 0.0;
+    ctx->cnt[i] = 0;
+  }
+  *n = KK_COUNT;
+  return FMNMF_OK;
+}
+
+const char* fmnmf_kernel_name(int i) { return (i >= 0 && i < KK_COUNT) ? kKindNames[i] : ""; }
+
+long long fmnmf_launch_count(const fmnmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,915 @@
+// FastMNMF kernels, templated on MAXM (the channel bucket: 2, 4 or 8).  Included by
+// fm_kernels_m{2,4,8}.cu, each of which instantiates one bucket.
+//
+// One iteration (Sec. III, block order W -> H -> g~ -> Q -> normalise) is six launches:
+//   k_tile<MODE_W>   W update, Eq. 23:   num/den[n,k,f] = sum_t h_nkt sum_m g~_nfm {x~/y~^2, 1/y~}
+//   k_tile<MODE_H>   H update, Eq. 24:   num/den[n,k,t] = sum_f w_nkf sum_m g~_nfm {x~/y~^2, 1/y~}
+//   k_tile<MODE_G>   g~ update, Eq. 21:  num/den[n,f,m] = sum_t lambda_ftn {x~/y~^2, 1/y~}
+//   k_tile<MODE_Y>   y~ refresh; split sums of V_fm = (1/T) sum_t x x^H / y~_ftm (Eq. 18)
+//   k_ip             IP, Eqs. 19-20, float64, one warp per bin (+ phi and nu normalisation)
+//   k_xt_ll          x~ = |Q_f x_ft|^2 (below Eq. 17); log-likelihood, Eq. 17; mu normalisation
+// A k_tile CTA owns kOT consecutive "own" elements and one split of the summed "inner"
+// index; each split writes partial sums and the last CTA to arrive for an own tile sums
+// the splits in a fixed order and applies the update, so results do not depend on
+// scheduling.  lambda_ftn = sum_k w_nkf h_nkt (Eq. 9) is formed on chip from W and H
+// tiles staged in shared memory; it is never written to memory.
+#pragma once
+#include "fm_common.cuh"
+
+namespace fm {
+
+enum { MODE_W = 0, MODE_H = 1, MODE_G = 2, MODE_Y = 3 };
+// FLAG_DO_V (MODE_Y): form V_fm and run the IP update.  FLAG_UPDATE (MODE_G): apply the
+// g~ rule (without it the launch only normalises).  FLAG_NORMALISE: scale normalisation.
+enum { FLAG_DO_V = 1, FLAG_NORMALISE = 2, FLAG_UPDATE = 4 };
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float dot4acc(float4 a, float4 b, float c) {
+  c = fmaf(a.x, b.x, c); c = fmaf(a.y, b.y, c); c = fmaf(a.z, b.z, c); return fmaf(a.w, b.w, c);
+}
+__device__ __forceinline__ bool finitef(float v) { return isfinite(v); }
+
+// Shared-memory carve-up of k_tile (in floats; every region a multiple of 4 floats).
+struct TileSmem {
+  int own, oth, g, a, b, acc, total;
+};
+__host__ __device__ inline TileSmem tile_smem(int mode, int N, int K, int M, int MAXM, int IC) {
+  const int ICP = IC + 4, NK = N * K;
+  TileSmem s;
+  s.own = 0;
+  s.oth = s.own + NK * kOT;
+  s.g = s.oth + NK * ICP;
+  int gsz = (mode == MODE_H) ? N * IC * M : N * kOT * M;
+  gsz = (gsz + 3) & ~3;
+  s.a = s.g + gsz;
+  int asz = 0, bsz = 0, accsz = 0;
+  if (mode == MODE_W || mode == MODE_H) { asz = 2 * N * kOT * ICP; accsz = 2 * NK * kOT; }
+  if (mode == MODE_G) { asz = N * kOT * ICP; bsz = 2 * kOT * M * ICP; accsz = 2 * N * kOT * M; }
+  if (mode == MODE_Y) { asz = 0; bsz = kOT * M * ICP; accsz = kOT * M * MAXM * MAXM; }
+  s.b = s.a + asz;
+  s.acc = s.b + bsz;
+  s.total = s.acc + ((accsz + 3) & ~3);
+  return s;
+}
+
+// Partial-sum floats per split for each mode.
+__host__ __device__ inline size_t tile_part_floats(int mode, int F, int T, int M, int N, int K, int MAXM) {
+  switch (mode) {
+    case MODE_W: return (size_t)2 * N * K * F;
+    case MODE_H: return (size_t)2 * N * K * T;
+    case MODE_G: return (size_t)2 * N * F * M;
+    default: return (size_t)F * M * MAXM * MAXM;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Warp-level float64 linear algebra for the IP step (M <= 8).  A is row-major with
+// leading dimension LD; columns [0, M) hold the matrix, columns [M, M + R) right-hand
+// sides.  Gauss-Jordan with partial pivoting; returns false (all lanes) if a pivot is
+// below 1e-30 times the largest entry of the matrix.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double2 crecip(double2 b) {
+  const double d = 1.0 / cabs2(b);
+  return make_double2(b.x * d, -b.y * d);
+}
+
+// Lane-parallel partial pivot: the row r in [c, M) with the largest |A[r][c]|^2 (lowest
+// row on ties), identical in every lane.
+__device__ __forceinline__ int warp_pivot(int M, int LD, const double2* A, int c, double* best_out) {
+  const int lane = threadIdx.x & 31;
+  double v = (lane >= c && lane < M) ? cabs2(A[lane * LD + c]) : -1.0;
+  int idx = lane;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  *best_out = v;
+  return idx;
+}
+
+__device__ inline bool warp_gauss_jordan(int M, int R, int LD, double2* A, double2* fac) {
+  const int lane = threadIdx.x & 31;
+  // scale for the singularity test
+  double amax = 0.0;
+  for (int e = lane; e < M * M; e += 32) amax = fmax(amax, cabs2(A[(e / M) * LD + (e % M)]));
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  bool ok = amax > 0.0 && isfinite(amax);
+  const int C = M + R;
+  for (int c = 0; c < M; ++c) {
+    double bv;
+    const int pr = warp_pivot(M, LD, A, c, &bv);
+    ok = ok && (bv > 1e-60 * amax);
+    if (pr != c) {
+      for (int j = lane; j < C; j += 32) {
+        double2 t = A[c * LD + j];
+        A[c * LD + j] = A[pr * LD + j];
+        A[pr * LD + j] = t;
+      }
+    }
+    __syncwarp();
+    const double2 inv = crecip(A[c * LD + c]);
+    if (lane < M) fac[lane] = (lane == c) ? make_double2(0.0, 0.0) : cmul(A[lane * LD + c], inv);
+    __syncwarp();
+    for (int e = lane; e < M * C; e += 32) {
+      int r = e / C, j = e % C;
+      if (r != c && j >= c) A[r * LD + j] = csub(A[r * LD + j], cmul(fac[r], A[c * LD + j]));
+    }
+    __syncwarp();
+  }
+  // divide each row by its pivot
+  for (int e = lane; e < M * R; e += 32) {
+    int r = e / R, j = M + e % R;
+    A[r * LD + j] = cmul(A[r * LD + j], crecip(A[r * LD + r]));
+  }
+  __syncwarp();
+  return ok;
+}
+
+// log|det A|^2 by Gaussian elimination with partial pivoting (A is destroyed).
+__device__ inline double warp_logdet2(int M, int LD, double2* A, double2* fac) {
+  const int lane = threadIdx.x & 31;
+  double prod = 1.0;  // product of |pivot|^2, renormalised by powers of two
+  int ex = 0;
+  for (int c = 0; c < M; ++c) {
+    double bv;
+    const int pr = warp_pivot(M, LD, A, c, &bv);
+    if (pr != c) {
+      for (int j = lane; j < M; j += 32) {
+        double2 t = A[c * LD + j];
+        A[c * LD + j] = A[pr * LD + j];
+        A[pr * LD + j] = t;
+      }
+    }
+    __syncwarp();
+    const double2 pv = A[c * LD + c];
+    int e2;
+    prod = frexp(prod * cabs2(pv), &e2);
+    ex += e2;
+    const double2 inv = crecip(pv);
+    if (lane < M) fac[lane] = (lane > c) ? cmul(A[lane * LD + c], inv) : make_double2(0.0, 0.0);
+    __syncwarp();
+    for (int e = lane; e < M * M; e += 32) {
+      int r = e / M, j = e % M;
+      if (r > c && j >= c) A[r * LD + j] = csub(A[r * LD + j], cmul(fac[r], A[c * LD + j]));
+    }
+    __syncwarp();
+  }
+  return log(prod) + (double)ex * 0.69314718055994531;  // log 2
+}
+
+// V_fm entry (j, c) from the packed Hermitian sums: slot a*MAXM+b holds Re(V_ab) for
+// a <= b and Im(V_ba) for a > b.
+template <int MAXM>
+__device__ __forceinline__ double2 vget(const double* vs, int j, int c) {
+  if (j == c) return make_double2(vs[j * MAXM + j], 0.0);
+  if (j < c) return make_double2(vs[j * MAXM + c], vs[c * MAXM + j]);
+  return make_double2(vs[c * MAXM + j], -vs[j * MAXM + c]);
+}
+
+// IP update of one bin by one warp, float64 (Eqs. 18-20), rows in order m = 0..M-1:
+//   q <- (Q V_m)^-1 e_m ;  q <- q / sqrt(q^H V_m q) ;  row m of Q <- q^H
+// vs: [M][MAXM*MAXM] packed V_fm (already divided by T).  Q: [MAXM*MAXM] in/out.
+template <int MAXM>
+__device__ bool warp_ip_bin(int M, const double* vs, double2* Q, double2* A, double2* fac, double2* qv) {
+  const int lane = threadIdx.x & 31;
+  const int LD = MAXM + 1;
+  bool ok = true;
+  for (int m = 0; m < M; ++m) {
+    const double* v = vs + m * MAXM * MAXM;
+    for (int e = lane; e < M * M; e += 32) {
+      int r = e / M, c = e % M;
+      double2 s = make_double2(0.0, 0.0);
+      for (int j = 0; j < M; ++j) s = cadd(s, cmul(Q[r * MAXM + j], vget<MAXM>(v, j, c)));
+      A[r * LD + c] = s;
+    }
+    if (lane < M) A[lane * LD + M] = make_double2(lane == m ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    ok = warp_gauss_jordan(M, 1, LD, A, fac) && ok;
+    if (lane < M) qv[lane] = A[lane * LD + M];
+    __syncwarp();
+    // s = Re(q^H V q)
+    double s = 0.0;
+    for (int e = lane; e < M * M; e += 32) {
+      int i = e / M, j = e % M;
+      double2 t = cmul(cconj(qv[i]), cmul(vget<MAXM>(v, i, j), qv[j]));
+      s += t.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (!(s > 0.0) || !isfinite(s)) { ok = false; s = 1.0; }
+    const double inv = 1.0 / sqrt(s);
+    if (lane < M) Q[m * MAXM + lane] = make_double2(qv[lane].x * inv, -qv[lane].y * inv);
+    __syncwarp();
+  }
+  return ok;
+}
+
+// ---------------------------------------------------------------------------------
+// The tiled sweep.  grid = (n_own_tiles, S), block = 256, dynamic smem = tile_smem(...)
+// (or the IP scratch for MODE_Y, whichever is larger).
+// ---------------------------------------------------------------------------------
+template <int MAXM, int MODE>
+__global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, unsigned ctr_base) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr bool F_OWN = (MODE != MODE_H);
+  const int tid = threadIdx.x;
+  const int N = p.N, K = p.K, M = p.M, NK = N * K, F = p.F, T = p.T;
+  const int SO = F_OWN ? F : T;
+  const int SI = F_OWN ? T : F;
+  const int ot = blockIdx.x, s = blockIdx.y;
+  const int o_base = ot * kOT;
+  const int n_own = min(kOT, SO - o_base);
+  const int i_begin = s * g.span;
+  const int i_end = min(SI, i_begin + g.span);
+  const int IC = g.IC, ICP = g.ICP;
+  const TileSmem L = tile_smem(MODE, N, K, M, MAXM, IC);
+  float* own_s = sm + L.own;   // [NK][kOT]
+  float* oth_s = sm + L.oth;   // [NK][ICP]
+  float* g_s = sm + L.g;       // F_OWN: [N][kOT][M]   else [N][IC][M]
+  float* a_s = sm + L.a;
+  float* b_s = sm + L.b;
+  float* acc_s = sm + L.acc;
+
+  // factors: own = the factor indexed by the own index, oth = by the inner index
+  const float* ownF = F_OWN ? p.W : p.H;
+  const float* othF = F_OWN ? p.H : p.W;
+
+  for (int e = tid; e < NK * kOT; e += kThreads) {
+    int nk = e / kOT, o = e % kOT;
+    own_s[e] = (o < n_own) ? ownF[(size_t)nk * SO + o_base + o] : 0.f;
+  }
+  if (F_OWN) {
+    for (int e = tid; e < N * kOT * M; e += kThreads) {
+      int n = e / (kOT * M), o = (e / M) % kOT, m = e % M;
+      g_s[e] = (o < n_own) ? p.G[((size_t)n * F + o_base + o) * M + m] : 0.f;
+    }
+  }
+  {
+    int accsz = (MODE == MODE_W || MODE == MODE_H) ? 2 * NK * kOT
+              : (MODE == MODE_G) ? 2 * N * kOT * M : kOT * M * MAXM * MAXM;
+    for (int e = tid; e < accsz; e += kThreads) acc_s[e] = 0.f;
+  }
+
+  // MODE_G without FLAG_UPDATE only normalises (launched with S = 1): no sweep.
+  const bool sweep = !(MODE == MODE_G && !(flags & FLAG_UPDATE));
+  for (int i0 = i_begin; sweep && i0 < i_end; i0 += IC) {
+    const int icn = min(IC, i_end - i0);
+    __syncthreads();  // previous sub-chunk fully consumed
+    for (int e = tid; e < NK * IC; e += kThreads) {
+      int nk = e / IC, i = e % IC;
+      oth_s[nk * ICP + i] = (i < icn) ? othF[(size_t)nk * SI + i0 + i] : 0.f;
+    }
+    if (!F_OWN) {
+      for (int e = tid; e < N * IC * M; e += kThreads) {
+        int n = e / (IC * M), i = (e / M) % IC, m = e % M;
+        g_s[e] = (i < icn) ? p.G[((size_t)n * F + i0 + i) * M + m] : 0.f;
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase 1: per point quantities (2 own x 4 inner per item) -------
+    const int nq = IC / 4;
+    for (int it = tid; it < (kOT / 2) * nq; it += kThreads) {
+      const int o0 = (it / nq) * 2;
+      const int ii = (it % nq) * 4;
+      float y[2][4][MAXM];
+      // model power y~ (read for MODE_W, formed from lambda otherwise)
+      if (MODE == MODE_W) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const bool v = (o0 + a < n_own) && (ii + b < icn);
+            const size_t pt = (size_t)(o_base + o0 + a) * T + (i0 + ii + b);
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) y[a][b][m] = (v && m < M) ? p.yt[pt * M + m] : 1.f;
+          }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) y[a][b][m] = 0.f;
+        for (int n = 0; n < N; ++n) {
+          float lam[2][4];
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) lam[a][b] = 0.f;
+          for (int k = 0; k < K; ++k) {
+            const int nk = n * K + k;
+            const float2 w = *reinterpret_cast<const float2*>(own_s + nk * kOT + o0);
+            const float4 h = ld4(oth_s + nk * ICP + ii);
+            lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);
+            lam[0][2] = fmaf(w.x, h.z, lam[0][2]); lam[0][3] = fmaf(w.x, h.w, lam[0][3]);
+            lam[1][0] = fmaf(w.y, h.x, lam[1][0]); lam[1][1] = fmaf(w.y, h.y, lam[1][1]);
+            lam[1][2] = fmaf(w.y, h.z, lam[1][2]); lam[1][3] = fmaf(w.y, h.w, lam[1][3]);
+          }
+          if (MODE == MODE_G) {
+            st4(a_s + (n * kOT + o0) * ICP + ii, make_float4(lam[0][0], lam[0][1], lam[0][2], lam[0][3]));
+            st4(a_s + (n * kOT + o0 + 1) * ICP + ii, make_float4(lam[1][0], lam[1][1], lam[1][2], lam[1][3]));
+          }
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                if (m < M) {
+                  const float gv = F_OWN ? g_s[(n * kOT + o0 + a) * M + m] : g_s[(n * IC + ii + b) * M + m];
+                  y[a][b][m] = fmaf(lam[a][b], gv, y[a][b][m]);
+                }
+              }
+        }
+      }
+
+      if (MODE == MODE_Y) {
+        // write y~ (pre-normalisation) and 1/y~
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          float binv[4][MAXM];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const bool v = (o0 + a < n_own) && (ii + b < icn);
+            const size_t pt = (size_t)(o_base + o0 + a) * T + (i0 + ii + b);
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              binv[b][m] = 0.f;
+              if (v && m < M) {
+                p.yt[pt * M + m] = y[a][b][m];
+                binv[b][m] = __frcp_rn(y[a][b][m]);
+              }
+            }
+          }
+          if (flags & FLAG_DO_V) {
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m)
+              if (m < M) st4(b_s + ((o0 + a) * M + m) * ICP + ii, make_float4(binv[0][m], binv[1][m], binv[2][m], binv[3][m]));
+          }
+        }
+      } else {
+        // A = x~ / y~^2, B = 1 / y~
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          float A[4][MAXM], B[4][MAXM];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const bool v = (o0 + a < n_own) && (ii + b < icn);
+            const int f = F_OWN ? (o_base + o0 + a) : (i0 + ii + b);
+            const int t = F_OWN ? (i0 + ii + b) : (o_base + o0 + a);
+            const size_t pt = (size_t)f * T + t;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              A[b][m] = 0.f; B[b][m] = 0.f;
+              if (v && m < M) {
+                const float bi = __frcp_rn(y[a][b][m]);
+                const float x = p.xt[pt * M + m];
+                B[b][m] = bi;
+                A[b][m] = x * bi * bi;
+              }
+            }
+          }
+          if (MODE == MODE_G) {
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m)
+              if (m < M) {
+                st4(b_s + ((0 * kOT + o0 + a) * M + m) * ICP + ii, make_float4(A[0][m], A[1][m], A[2][m], A[3][m]));
+                st4(b_s + ((1 * kOT + o0 + a) * M + m) * ICP + ii, make_float4(B[0][m], B[1][m], B[2][m], B[3][m]));
+              }
+          } else {
+            // P_n = sum_m g~ A,  R_n = sum_m g~ B
+            for (int n = 0; n < N; ++n) {
+              float P4[4], R4[4];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                float pa = 0.f, ra = 0.f;
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m)
+                  if (m < M) {
+                    const float gv = F_OWN ? g_s[(n * kOT + o0 + a) * M + m] : g_s[(n * IC + ii + b) * M + m];
+                    pa = fmaf(gv, A[b][m], pa);
+                    ra = fmaf(gv, B[b][m], ra);
+                  }
+                P4[b] = pa; R4[b] = ra;
+              }
+              st4(a_s + ((0 * N + n) * kOT + o0 + a) * ICP + ii, make_float4(P4[0], P4[1], P4[2], P4[3]));
+              st4(a_s + ((1 * N + n) * kOT + o0 + a) * ICP + ii, make_float4(R4[0], R4[1], R4[2], R4[3]));
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase 2: contraction over the inner index ----------------------
+    const int icn4 = (icn + 3) & ~3;
+    if (MODE == MODE_W || MODE == MODE_H) {
+      const int KP = (K + 1) >> 1;
+      const int ntl = N * KP * (kOT / 2);
+      for (int tl = tid; tl < ntl; tl += kThreads) {
+        const int o0 = (tl & 3) * 2;
+        const int kp = (tl >> 2) % KP;
+        const int n = (tl >> 2) / KP;
+        const int k0 = 2 * kp;
+        const bool has1 = (k0 + 1 < K);
+        const int k1 = has1 ? k0 + 1 : k0;
+        const float* P0 = a_s + ((0 * N + n) * kOT + o0) * ICP;
+        const float* P1 = P0 + ICP;
+        const float* R0 = a_s + ((1 * N + n) * kOT + o0) * ICP;
+        const float* R1 = R0 + ICP;
+        const float* h0 = oth_s + (n * K + k0) * ICP;
+        const float* h1 = oth_s + (n * K + k1) * ICP;
+        float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int i = 0; i < icn4; i += 4) {
+          const float4 p0 = ld4(P0 + i), p1 = ld4(P1 + i), r0 = ld4(R0 + i), r1 = ld4(R1 + i);
+          const float4 x0 = ld4(h0 + i), x1 = ld4(h1 + i);
+          c[0] = dot4acc(x0, p0, c[0]); c[1] = dot4acc(x0, p1, c[1]);
+          c[2] = dot4acc(x1, p0, c[2]); c[3] = dot4acc(x1, p1, c[3]);
+          c[4] = dot4acc(x0, r0, c[4]); c[5] = dot4acc(x0, r1, c[5]);
+          c[6] = dot4acc(x1, r0, c[6]); c[7] = dot4acc(x1, r1, c[7]);
+        }
+        float* an = acc_s + (0 * NK + n * K + k0) * kOT + o0;
+        float* ad = acc_s + (1 * NK + n * K + k0) * kOT + o0;
+        an[0] += c[0]; an[1] += c[1]; ad[0] += c[4]; ad[1] += c[5];
+        if (has1) { an[kOT] += c[2]; an[kOT + 1] += c[3]; ad[kOT] += c[6]; ad[kOT + 1] += c[7]; }
+      }
+    } else if (MODE == MODE_G) {
+      const int ntl = N * kOT * M;
+      for (int tl = tid; tl < ntl; tl += kThreads) {
+        const int m = tl % M, o = (tl / M) % kOT, n = tl / (M * kOT);
+        const float* lp = a_s + (n * kOT + o) * ICP;
+        const float* ap = b_s + ((0 * kOT + o) * M + m) * ICP;
+        const float* bp = b_s + ((1 * kOT + o) * M + m) * ICP;
+        float cn = 0.f, cd = 0.f;
+        for (int i = 0; i < icn4; i += 4) {
+          const float4 l = ld4(lp + i);
+          cn = dot4acc(l, ld4(ap + i), cn);
+          cd = dot4acc(l, ld4(bp + i), cd);
+        }
+        acc_s[((0 * N + n) * kOT + o) * M + m] += cn;
+        acc_s[((1 * N + n) * kOT + o) * M + m] += cd;
+      }
+    } else if (flags & FLAG_DO_V) {
+      // V_fm partial sums: warp w <-> own element o = w; lanes split (m-group, t-subset)
+      constexpr int MPG = (MAXM <= 4) ? MAXM : 2;
+      constexpr int MM = MAXM * MAXM;
+      const int warp = tid >> 5, lane = tid & 31;
+      const int o = warp;
+      const int ngrp = (M + MPG - 1) / MPG;
+      const int IS = (ngrp == 1) ? 32 : (ngrp == 2 ? 16 : 8);
+      const int grp = lane / IS, isub = lane % IS;
+      float acc[MPG][MM];
+#pragma unroll
+      for (int mm = 0; mm < MPG; ++mm)
+#pragma unroll
+        for (int q = 0; q < MM; ++q) acc[mm][q] = 0.f;
+      if (o < n_own && grp < ngrp) {
+        const int f = o_base + o;
+        for (int i = isub; i < icn; i += IS) {
+          const float2* xp = p.X + ((size_t)f * T + i0 + i) * M;
+          float2 x[MAXM];
+#pragma unroll
+          for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? xp[j] : make_float2(0.f, 0.f);
+          float pr[MM];
+#pragma unroll
+          for (int a = 0; a < MAXM; ++a)
+#pragma unroll
+            for (int b = 0; b < MAXM; ++b) {
+              if (a <= b) pr[a * MAXM + b] = x[a].x * x[b].x + x[a].y * x[b].y;        // Re(x_a conj x_b)
+              else        pr[a * MAXM + b] = x[b].y * x[a].x - x[b].x * x[a].y;        // Im(x_b conj x_a)
+            }
+#pragma unroll
+          for (int mm = 0; mm < MPG; ++mm) {
+            const int m = grp * MPG + mm;
+            const float bv = (m < M) ? b_s[(o * M + m) * ICP + i] : 0.f;
+#pragma unroll
+            for (int q = 0; q < MM; ++q) acc[mm][q] = fmaf(bv, pr[q], acc[mm][q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int mm = 0; mm < MPG; ++mm)
+#pragma unroll
+        for (int q = 0; q < MM; ++q) {
+          float v = acc[mm][q];
+          for (int off = IS >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          acc[mm][q] = v;
+        }
+      if (o < n_own && grp < ngrp && isub == 0) {
+#pragma unroll
+        for (int mm = 0; mm < MPG; ++mm) {
+          const int m = grp * MPG + mm;
+          if (m < M) {
+#pragma unroll
+            for (int q = 0; q < MM; ++q) acc_s[(o * M + m) * MM + q] += acc[mm][q];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------- write this split's partial sums ---------------------------------
+  const bool has_parts = sweep && (MODE != MODE_Y || (flags & FLAG_DO_V));
+  if (!has_parts) return;
+  const size_t psz = tile_part_floats(MODE, F, T, M, N, K, MAXM);
+  float* part = p.part + (size_t)s * psz;
+  if (!has_parts) {
+    // nothing to write
+  } else if (MODE == MODE_W || MODE == MODE_H) {
+    for (int e = tid; e < 2 * NK * kOT; e += kThreads) {
+      const int o = e % kOT, r = e / kOT;  // r = pr*NK + nk
+      if (o < n_own) part[(size_t)r * SO + o_base + o] = acc_s[e];
+    }
+  } else if (MODE == MODE_G) {
+    for (int e = tid; e < 2 * N * kOT * M; e += kThreads) {
+      const int m = e % M, o = (e / M) % kOT, r = e / (M * kOT);  // r = pr*N + n
+      if (o < n_own) part[((size_t)r * F + o_base + o) * M + m] = acc_s[e];
+    }
+  } else {
+    constexpr int MM = MAXM * MAXM;
+    for (int e = tid; e < kOT * M * MM; e += kThreads) {
+      const int o = e / (M * MM);
+      if (o < n_own) part[(size_t)(o_base)*M * MM + e] = acc_s[e];
+    }
+  }
+  if (MODE == MODE_Y) return;  // k_ip reduces the V_fm splits
+  // Every split must have finished reading the state before the last one rewrites it.
+  if (sweep && !arrive_last(p.counters + ctr_base + ot, g.S)) return;
+
+  // ---------------- last CTA of this own tile: reduce splits, apply the update -------
+  if (MODE == MODE_W || MODE == MODE_H) {
+    float* fac = F_OWN ? p.W : p.H;
+    for (int e = tid; e < NK * kOT; e += kThreads) {
+      const int nk = e / kOT, o = e % kOT;
+      if (o >= n_own) continue;
+      float num = 0.f, den = 0.f;
+      for (int ss = 0; ss < g.S; ++ss) {
+        const float* pp = p.part + (size_t)ss * psz;
+        num += __ldcg(pp + (size_t)nk * SO + o_base + o);
+        den += __ldcg(pp + (size_t)(NK + nk) * SO + o_base + o);
+      }
+      const size_t idx = (size_t)nk * SO + o_base + o;
+      const float v = fac[idx] * sqrtf(num / den);
+      if (!finitef(v)) flag(p.status, ST_NONFINITE);
+      fac[idx] = v;
+    }
+  } else if (MODE == MODE_G) {
+    // g~ <- g~ sqrt(num/den)
+    for (int e = tid; (flags & FLAG_UPDATE) && e < N * kOT * M; e += kThreads) {
+      const int m = e % M, o = (e / M) % kOT, n = e / (M * kOT);
+      if (o >= n_own) continue;
+      float num = 0.f, den = 0.f;
+      for (int ss = 0; ss < g.S; ++ss) {
+        const float* pp = p.part + (size_t)ss * psz;
+        num += __ldcg(pp + ((size_t)n * F + o_base + o) * M + m);
+        den += __ldcg(pp + ((size_t)(N + n) * F + o_base + o) * M + m);
+      }
+      const size_t idx = ((size_t)n * F + o_base + o) * M + m;
+      const float v = p.G[idx] * sqrtf(num / den);
+      if (!finitef(v)) flag(p.status, ST_NONFINITE);
+      p.G[idx] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// IP update (Eqs. 18-20) and the per-bin normalisation, one warp per bin, float64:
+// V_fm = (1/T) sum of the MODE_Y splits; rows m = 0..M-1 in order; log|det Q_f|^2;
+// phi_f = tr(Q_f Q_f^H)/M with Q_f /= sqrt(phi_f), g~_nf /= phi_f; then
+// nu_nf = sum_m g~_nfm with g~_nf /= nu_nf, w_nkf *= nu_nf.
+// ---------------------------------------------------------------------------------
+constexpr int kIpWarps = 2;
+
+template <int MAXM>
+__global__ void __launch_bounds__(kIpWarps * 32) k_ip(Prob p, int S, int flags) {
+  constexpr int MM = MAXM * MAXM;
+  constexpr int LD = MAXM + 1;
+  __shared__ double vs_s[kIpWarps][MAXM * MM];
+  __shared__ double2 Q_s[kIpWarps][MM];
+  __shared__ double2 A_s[kIpWarps][MAXM * LD];
+  __shared__ double2 fac_s[kIpWarps][MAXM];
+  __shared__ double2 qv_s[kIpWarps][MAXM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kIpWarps + warp;
+  if (f >= p.F) return;
+  const int M = p.M, N = p.N, K = p.K, F = p.F;
+  double* vs = vs_s[warp];
+  double2* Q = Q_s[warp];
+  double2* A = A_s[warp];
+  double2* fac = fac_s[warp];
+  double2* qv = qv_s[warp];
+  bool ok = true;
+  for (int e = lane; e < MM; e += 32) {
+    const int r = e / MAXM, c = e % MAXM;
+    Q[e] = (r < M && c < M) ? p.Qd[((size_t)f * M + r) * M + c] : make_double2(0.0, 0.0);
+  }
+  if (flags & FLAG_DO_V) {
+    const size_t psz = (size_t)F * M * MM;
+    const double invT = 1.0 / (double)p.T;
+    for (int e = lane; e < M * MM; e += 32) {
+      float sum = 0.f;
+      for (int ss = 0; ss < S; ++ss) sum += __ldcg(p.part + (size_t)ss * psz + (size_t)f * M * MM + e);
+      vs[e] = (double)sum * invT;
+    }
+    __syncwarp();
+    ok = warp_ip_bin<MAXM>(M, vs, Q, A, fac, qv);
+  }
+  __syncwarp();
+  for (int e = lane; e < M * M; e += 32) A[(e / M) * LD + (e % M)] = Q[(e / M) * MAXM + (e % M)];
+  __syncwarp();
+  double ld = warp_logdet2(M, LD, A, fac);
+  double phi = 1.0;
+  if (flags & FLAG_NORMALISE) {
+    double tr = 0.0;
+    for (int e = lane; e < M * M; e += 32) tr += cabs2(Q[(e / M) * MAXM + (e % M)]);
+    for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    phi = tr / (double)M;
+    ld -= (double)M * log(phi);
+  }
+  const double sc = 1.0 / sqrt(phi);
+  for (int e = lane; e < M * M; e += 32) {
+    const double2 q = Q[(e / M) * MAXM + (e % M)];
+    const double2 qs = make_double2(q.x * sc, q.y * sc);
+    p.Qd[(size_t)f * M * M + e] = qs;
+    p.Qf[(size_t)f * M * M + e] = make_float2((float)qs.x, (float)qs.y);
+  }
+  if (flags & FLAG_NORMALISE) {
+    // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
+    const float fphi = (float)phi;
+    for (int n = lane; n < N; n += 32) {
+      float* gp = p.G + ((size_t)n * F + f) * M;
+      float nu = 0.f;
+      for (int m = 0; m < M; ++m) { const float gv = gp[m] / fphi; gp[m] = gv; nu += gv; }
+      for (int m = 0; m < M; ++m) gp[m] /= nu;
+      for (int k = 0; k < K; ++k) p.W[((size_t)n * K + k) * F + f] *= nu;
+      if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
+    }
+  }
+  if (lane == 0) {
+    p.logdet[f] = ld;
+    p.phi[f] = (float)phi;
+    if (!ok) flag(p.status, ST_SINGULAR);
+    if (!isfinite(ld)) flag(p.status, ST_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// x~ = |Q_f x_ft|^2 with the new (normalised) Q_f; y~ /= phi_f; log-likelihood (Eq. 17);
+// extra CTAs (blockIdx.x >= n_pt_blocks) apply the mu normalisation, one warp per (n,k).
+// ---------------------------------------------------------------------------------
+constexpr int kPtsPerThread = 4;
+
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int apply_phi, int do_mu,
+                                                    unsigned ctr) {
+  const int tid = threadIdx.x;
+  const int M = p.M, T = p.T, F = p.F;
+  if ((int)blockIdx.x < n_pt_blocks) {
+    const size_t npts = (size_t)F * T;
+    double part = 0.0;
+    for (int r = 0; r < kPtsPerThread; ++r) {
+      const size_t pt = (size_t)blockIdx.x * (kThreads * kPtsPerThread) + (size_t)r * kThreads + tid;
+      if (pt >= npts) break;
+      const int f = (int)(pt / T);
+      const float2* xp = p.X + pt * M;
+      const float2* qp = p.Qf + (size_t)f * M * M;
+      float2 x[MAXM];
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? xp[j] : make_float2(0.f, 0.f);
+      const float ph = apply_phi ? p.phi[f] : 1.f;
+      float ls = 0.f;
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          float re = 0.f, im = 0.f;
+#pragma unroll
+          for (int j = 0; j < MAXM; ++j) {
+            if (j < M) {
+              const float2 q = qp[m * M + j];
+              re = fmaf(q.x, x[j].x, fmaf(-q.y, x[j].y, re));
+              im = fmaf(q.x, x[j].y, fmaf(q.y, x[j].x, im));
+            }
+          }
+          const float xv = re * re + im * im;
+          float yv = p.yt[pt * M + m];
+          if (apply_phi) { yv = yv / ph; p.yt[pt * M + m] = yv; }
+          p.xt[pt * M + m] = xv;
+          ls += -xv / yv - logf(yv);
+        }
+      }
+      part += (double)ls;
+    }
+    // block reduction in a fixed order
+    __shared__ double red[kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+      p.llpart[blockIdx.x] = s;
+    }
+    if (!arrive_last(p.counters + ctr, (unsigned)n_pt_blocks)) return;
+    double s = 0.0;
+    for (int b = tid; b < n_pt_blocks; b += kThreads) s += __ldcg(p.llpart + b);
+    double ld = 0.0;
+    for (int f = tid; f < F; f += kThreads) ld += __ldcg(p.logdet + f);
+    __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, off);
+      ld += __shfl_xor_sync(0xffffffffu, ld, off);
+    }
+    __shared__ double red2[2][kThreads / 32];
+    if ((tid & 31) == 0) { red2[0][tid >> 5] = s; red2[1][tid >> 5] = ld; }
+    __syncthreads();
+    if (tid == 0) {
+      double S = 0.0, LD = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) { S += red2[0][w]; LD += red2[1][w]; }
+      const double ll = S + (double)T * LD - (double)F * T * M * 1.1447298858494002;  // log(pi)
+      *p.ll = ll;
+      if (!isfinite(ll)) flag(p.status, ST_NONFINITE);
+    }
+  } else if (do_mu) {
+    // mu_nk = sum_f w_nkf;  w_nk /= mu;  h_nk *= mu
+    const int NK = p.N * p.K;
+    const int wid = ((int)blockIdx.x - n_pt_blocks) * (kThreads / 32) + (tid >> 5);
+    const int lane = tid & 31;
+    if (wid >= NK) return;
+    float* w = p.W + (size_t)wid * F;
+    float* h = p.H + (size_t)wid * T;
+    float s = 0.f;
+    for (int f = lane; f < F; f += 32) s += w[f];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const float inv = 1.f / s;
+    for (int f = lane; f < F; f += 32) w[f] *= inv;
+    for (int t = lane; t < T; t += 32) h[t] *= s;
+    if (lane == 0 && !(s > 0.f && isfinite(s))) flag(p.status, ST_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Per-bin float64 preparation: log|det Q_f|^2, float32 copy of Q_f, phi_f = 1 (mode 0);
+// or the float32 inverse Q_f^-1 for the Wiener filter (mode 1).  One warp per bin.
+// ---------------------------------------------------------------------------------
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k_prep_q(Prob p, int mode) {
+  __shared__ double2 A_s[kThreads / 32][MAXM * 2 * MAXM];
+  __shared__ double2 fac_s[kThreads / 32][MAXM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (kThreads / 32) + warp;
+  if (f >= p.F) return;
+  const int M = p.M;
+  double2* A = A_s[warp];
+  const double2* q = p.Qd + (size_t)f * M * M;
+  if (mode == 0) {
+    const int LD = MAXM;
+    for (int e = lane; e < M * M; e += 32) {
+      A[(e / M) * LD + e % M] = q[e];
+      p.Qf[(size_t)f * M * M + e] = make_float2((float)q[e].x, (float)q[e].y);
+    }
+    __syncwarp();
+    const double ld = warp_logdet2(M, LD, A, fac_s[warp]);
+    if (lane == 0) {
+      p.logdet[f] = ld;
+      p.phi[f] = 1.f;
+      if (!isfinite(ld)) flag(p.status, ST_SINGULAR);
+    }
+  } else {
+    const int LD = 2 * MAXM;
+    for (int e = lane; e < M * 2 * M; e += 32) {
+      const int r = e / (2 * M), c = e % (2 * M);
+      A[r * LD + c] = (c < M) ? q[r * M + c] : make_double2(c - M == r ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
+    const bool ok = warp_gauss_jordan(M, M, LD, A, fac_s[warp]);
+    for (int e = lane; e < M * M; e += 32) {
+      const double2 v = A[(e / M) * LD + M + e % M];
+      p.Qinv[(size_t)f * M * M + e] = make_float2((float)v.x, (float)v.y);
+    }
+    if (lane == 0 && !ok) flag(p.status, ST_SINGULAR);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Multichannel Wiener filter (Eq. 3 with Eq. 16 substituted):
+//   x_ftn = Q_f^-1 ( lambda_ftn g~_nf / y~_ft  (elementwise)  Q_f x_ft )
+// grid = (F tiles of kOT, T splits), lambda formed on chip as in k_tile.
+// ---------------------------------------------------------------------------------
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* __restrict__ out) {
+  extern __shared__ __align__(16) float sm[];
+  const int tid = threadIdx.x;
+  const int N = p.N, K = p.K, M = p.M, NK = N * K, F = p.F, T = p.T;
+  const int o_base = blockIdx.x * kOT;
+  const int n_own = min(kOT, F - o_base);
+  const int i_begin = blockIdx.y * g.span;
+  const int i_end = min(T, i_begin + g.span);
+  const int IC = g.IC, ICP = g.ICP;
+  float* own_s = sm;                       // [NK][kOT]
+  float* oth_s = own_s + NK * kOT;         // [NK][ICP]
+  float* g_s = oth_s + NK * ICP;           // [N][kOT][M]
+  float* lam_s = g_s + ((N * kOT * M + 3) & ~3);   // [N][kOT][ICP]
+  float2* q_s = reinterpret_cast<float2*>(lam_s + N * kOT * ICP);   // [kOT][M*M]
+  float2* qi_s = q_s + kOT * MAXM * MAXM;                            // [kOT][M*M]
+
+  for (int e = tid; e < NK * kOT; e += kThreads) {
+    const int nk = e / kOT, o = e % kOT;
+    own_s[e] = (o < n_own) ? p.W[(size_t)nk * F + o_base + o] : 0.f;
+  }
+  for (int e = tid; e < N * kOT * M; e += kThreads) {
+    const int n = e / (kOT * M), o = (e / M) % kOT, m = e % M;
+    g_s[e] = (o < n_own) ? p.G[((size_t)n * F + o_base + o) * M + m] : 0.f;
+  }
+  for (int e = tid; e < kOT * M * M; e += kThreads) {
+    const int o = e / (M * M);
+    q_s[e] = (o < n_own) ? p.Qf[(size_t)o_base * M * M + e] : make_float2(0.f, 0.f);
+    qi_s[e] = (o < n_own) ? p.Qinv[(size_t)o_base * M * M + e] : make_float2(0.f, 0.f);
+  }
+  for (int i0 = i_begin; i0 < i_end; i0 += IC) {
+    const int icn = min(IC, i_end - i0);
+    __syncthreads();
+    for (int e = tid; e < NK * IC; e += kThreads) {
+      const int nk = e / IC, i = e % IC;
+      oth_s[nk * ICP + i] = (i < icn) ? p.H[(size_t)nk * T + i0 + i] : 0.f;
+    }
+    __syncthreads();
+    const int nq = IC / 4;
+    for (int it = tid; it < (kOT / 2) * nq; it += kThreads) {
+      const int o0 = (it / nq) * 2, ii = (it % nq) * 4;
+      for (int n = 0; n < N; ++n) {
+        float lam[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int k = 0; k < K; ++k) {
+          const int nk = n * K + k;
+          const float2 w = *reinterpret_cast<const float2*>(own_s + nk * kOT + o0);
+          const float4 h = ld4(oth_s + nk * ICP + ii);
+          lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);
+          lam[0][2] = fmaf(w.x, h.z, lam[0][2]); lam[0][3] = fmaf(w.x, h.w, lam[0][3]);
+          lam[1][0] = fmaf(w.y, h.x, lam[1][0]); lam[1][1] = fmaf(w.y, h.y, lam[1][1]);
+          lam[1][2] = fmaf(w.y, h.z, lam[1][2]); lam[1][3] = fmaf(w.y, h.w, lam[1][3]);
+        }
+        st4(lam_s + (n * kOT + o0) * ICP + ii, make_float4(lam[0][0], lam[0][1], lam[0][2], lam[0][3]));
+        st4(lam_s + (n * kOT + o0 + 1) * ICP + ii, make_float4(lam[1][0], lam[1][1], lam[1][2], lam[1][3]));
+      }
+    }
+    __syncthreads();
+    // one point per thread (t fastest across lanes)
+    for (int e = tid; e < kOT * IC; e += kThreads) {
+      const int o = e / IC, i = e % IC;
+      if (o >= n_own || i >= icn) continue;
+      const int f = o_base + o, t = i0 + i;
+      const size_t pt = (size_t)f * T + t;
+      float2 x[MAXM], y[MAXM];
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? p.X[pt * M + j] : make_float2(0.f, 0.f);
+      const float2* Qo = q_s + o * M * M;
+      const float2* Qi = qi_s + o * M * M;
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        float2 s = make_float2(0.f, 0.f);
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < MAXM; ++j)
+            if (j < M) { const float2 c = cmulf(Qo[m * M + j], x[j]); s.x += c.x; s.y += c.y; }
+        }
+        y[m] = s;
+      }
+      float ytot[MAXM];
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) ytot[m] = 0.f;
+      for (int n = 0; n < N; ++n) {
+        const float l = lam_s[(n * kOT + o) * ICP + i];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) ytot[m] = fmaf(l, g_s[(n * kOT + o) * M + m], ytot[m]);
+      }
+      float yinv[MAXM];
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) yinv[m] = (m < M) ? __frcp_rn(ytot[m]) : 0.f;
+      for (int n = 0; n < N; ++n) {
+        const float l = lam_s[(n * kOT + o) * ICP + i];
+        float2 z[MAXM];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+          const float gain = (m < M) ? l * g_s[(n * kOT + o) * M + m] * yinv[m] : 0.f;
+          z[m] = make_float2(gain * y[m].x, gain * y[m].y);
+        }
+        float2* op = out + (((size_t)n * F + f) * T + t) * M;
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+          if (m < M) {
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j)
+              if (j < M) { const float2 c = cmulf(Qi[m * M + j], z[j]); s.x += c.x; s.y += c.y; }
+            op[m] = s;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace fm

@@ -1,0 +1,39 @@
+// Instantiates the kernels of one channel bucket (FM_MAXM) and its launch entry points.
+#include "fm_kernels.cuh"
+#include "fm_launch.h"
+
+#define FM_CAT2(a, b) a##b
+#define FM_CAT(a, b) FM_CAT2(a, b)
+
+namespace fm {
+
+cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
+  constexpr int MX = FM_MAXM;
+  switch (k) {
+    case KK_W: k_tile<MX, MODE_W><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
+    case KK_H: k_tile<MX, MODE_H><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
+    case KK_G: k_tile<MX, MODE_G><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
+    case KK_Y: k_tile<MX, MODE_Y><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
+    case KK_XT:
+      k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr);
+      break;
+    case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.prep_mode); break;
+    case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;
+    case KK_IP: k_ip<MX><<<a.grid, kIpWarps * 32, 0, a.st>>>(a.p, a.S, a.flags); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t FM_CAT(configure_m, FM_MAXM)(int bytes) {
+  constexpr int MX = FM_MAXM;
+  cudaError_t e = cudaSuccess;
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_W>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_H>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_G>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_Y>, A, bytes)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_separate<MX>, A, bytes);
+}
+
+}  // namespace fm

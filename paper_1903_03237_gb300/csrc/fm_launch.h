@@ -1,0 +1,45 @@
+// Host-side launch interface of the FastMNMF kernels (one translation unit per channel
+// bucket MAXM in {2, 4, 8}; fm_api.cu dispatches on the bucket).
+#pragma once
+#include <cuda_runtime.h>
+#include "fm_common.cuh"
+
+namespace fm {
+
+enum KernelKind {
+  KK_W = 0,      // W update (Eq. 23)
+  KK_H = 1,      // H update (Eq. 24)
+  KK_G = 2,      // g~ update (Eq. 21) + nu normalisation
+  KK_Y = 3,      // y~ refresh, V_fm (Eq. 18), IP (Eqs. 19-20) + phi normalisation
+  KK_XT = 4,     // x~, log-likelihood (Eq. 17), mu normalisation
+  KK_PREP = 5,   // per-bin float64 preparation (log-det, Q^-1)
+  KK_SEP = 6,    // Wiener filter (Eq. 3)
+  KK_IP = 7,     // IP solve (Eqs. 19-20) + per-bin normalisation
+  KK_COUNT = 8
+};
+
+struct LaunchArgs {
+  Prob p;
+  Geom g;
+  dim3 grid;
+  size_t smem = 0;
+  cudaStream_t st = nullptr;
+  int flags = 0;          // k_tile / k_ip flags
+  int S = 0;              // k_ip: number of V_fm splits
+  unsigned ctr = 0;       // first arrival counter of this launch
+  int n_pt_blocks = 0;    // k_xt_ll
+  int apply_phi = 0;      // k_xt_ll
+  int do_mu = 0;          // k_xt_ll
+  int prep_mode = 0;      // k_prep_q: 0 log-det/copy, 1 inverse
+  float2* out = nullptr;  // k_separate
+};
+
+cudaError_t launch_m2(KernelKind k, const LaunchArgs& a);
+cudaError_t launch_m4(KernelKind k, const LaunchArgs& a);
+cudaError_t launch_m8(KernelKind k, const LaunchArgs& a);
+// Raises the dynamic shared-memory limit of every kernel of the bucket to `bytes`.
+cudaError_t configure_m2(int bytes);
+cudaError_t configure_m4(int bytes);
+cudaError_t configure_m8(int bytes);
+
+}  // namespace fm

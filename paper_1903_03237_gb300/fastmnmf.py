@@ -1,0 +1,213 @@
+"""Thin Python binding of libfastmnmf.so (ctypes).  Argument marshalling only: every step
+of FastMNMF runs in the library's CUDA kernels.  Host arrays are NumPy; device arrays are
+torch CUDA tensors (their data pointers are handed to the C ABI).
+
+The library must have been built (``paper_1903_03237_gb300.build.build()``); importing
+this module without it raises ImportError - there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+try:  # load torch first so the library binds to the same CUDA runtime instance
+    import torch  # noqa: F401
+except Exception:  # pragma: no cover - torch is optional for pure host use
+    torch = None
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfastmnmf.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with paper_1903_03237_gb300.build.build()")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESINGULAR, ETIMEOUT, EBUSY = range(8)
+UPDATE_W, UPDATE_H, UPDATE_G, UPDATE_Q, UPDATE_ALL = 1, 2, 4, 8, 15
+PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ESINGULAR",
+                6: "ETIMEOUT", 7: "EBUSY"}
+
+# every symbol include/fastmnmf.h declares
+EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "fmnmf_iterate", "fmnmf_sync",
+           "fmnmf_loglik", "fmnmf_separate", "fmnmf_get_state", "fmnmf_set_state", "fmnmf_shape",
+           "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
+           "fmnmf_kernel_name", "fmnmf_launch_count"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("update_mask", ctypes.c_uint), ("normalise", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_size_t)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_S = ctypes.c_int  # fmnmf_status
+_sig = {
+    "fmnmf_default_opts": (_S, [ctypes.POINTER(Opts)]),
+    "fmnmf_init": (_S, [ctypes.POINTER(_P), _P, _I, _I, _I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(Opts)]),
+    "fmnmf_reset": (_S, [_P, _P, _I, ctypes.c_uint64]),
+    "fmnmf_restart": (_S, [_P]),
+    "fmnmf_iterate": (_S, [_P, _I]),
+    "fmnmf_sync": (_S, [_P]),
+    "fmnmf_loglik": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_separate": (_S, [_P, _P, _I]),
+    "fmnmf_get_state": (_S, [_P, _P, _P, _P, _P]),
+    "fmnmf_set_state": (_S, [_P, _P, _P, _P, _P]),
+    "fmnmf_shape": (_S, [_P] + [ctypes.POINTER(_I)] * 5),
+    "fmnmf_destroy": (_S, [_P]),
+    "fmnmf_last_error": (ctypes.c_char_p, [_P]),
+    "fmnmf_set_timing": (_S, [_P, _I]),
+    "fmnmf_kernel_times": (_S, [_P, _P, _P, ctypes.POINTER(_I)]),
+    "fmnmf_kernel_name": (ctypes.c_char_p, [_I]),
+    "fmnmf_launch_count": (ctypes.c_longlong, [_P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class FastMNMFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != OK:
+        msg = _lib.fmnmf_last_error(ctx)
+        raise FastMNMFError(st, msg.decode() if msg else "")
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    _check(_lib.fmnmf_default_opts(ctypes.byref(o)))
+    return o
+
+
+def _host_ptr(a: np.ndarray, dtype) -> tuple[np.ndarray, int]:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+class Context:
+    """One mixture's device-resident FastMNMF state (wraps fmnmf_ctx)."""
+
+    def __init__(self, X, N: int, K: int, seed: int = 0, *, update_mask: int = UPDATE_ALL,
+                 normalise: bool = True, precision: int = PREC_FP32, stream=None, hbm_budget: int = 0):
+        opts = default_opts()
+        opts.update_mask = update_mask
+        opts.normalise = 1 if normalise else 0
+        opts.precision = precision
+        opts.stream = stream
+        opts.hbm_budget = hbm_budget
+        self._ctx = _P()
+        self._keep = None
+        if torch is not None and isinstance(X, torch.Tensor) and X.is_cuda:
+            assert X.dtype == torch.complex64 and X.dim() == 3 and X.is_contiguous()
+            F, T, M = X.shape
+            torch.cuda.synchronize(X.device)  # the library reads X on its own stream
+            ptr, on_dev = X.data_ptr(), 1
+        else:
+            Xh, ptr = _host_ptr(X, np.complex64)
+            F, T, M = Xh.shape
+            self._keep, on_dev = Xh, 0
+        st = _lib.fmnmf_init(ctypes.byref(self._ctx), ptr, on_dev, F, T, M, N, K, seed, ctypes.byref(opts))
+        self._keep = None
+        _check(st, None)
+        self.F, self.T, self.M, self.N, self.K = F, T, M, N, K
+
+    # -- lifecycle ----------------------------------------------------------------------
+    def close(self):
+        if self._ctx:
+            _lib.fmnmf_destroy(self._ctx)
+            self._ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    # -- calls --------------------------------------------------------------------------
+    def reset(self, X, seed: int = 0):
+        if torch is not None and isinstance(X, torch.Tensor) and X.is_cuda:
+            torch.cuda.synchronize(X.device)  # the library reads X on its own stream
+            _check(_lib.fmnmf_reset(self._ctx, X.data_ptr(), 1, seed), self._ctx)
+        else:
+            Xh, ptr = _host_ptr(X, np.complex64)
+            _check(_lib.fmnmf_reset(self._ctx, ptr, 0, seed), self._ctx)
+
+    def restart(self):
+        """Back to the state of the last init / reset / set_state (device-side, async)."""
+        _check(_lib.fmnmf_restart(self._ctx), self._ctx)
+
+    def iterate(self, n: int = 1):
+        _check(_lib.fmnmf_iterate(self._ctx, n), self._ctx)
+
+    def sync(self):
+        _check(_lib.fmnmf_sync(self._ctx), self._ctx)
+
+    def loglik(self) -> float:
+        v = ctypes.c_double()
+        _check(_lib.fmnmf_loglik(self._ctx, ctypes.byref(v)), self._ctx)
+        return v.value
+
+    def separate(self, out=None) -> np.ndarray:
+        """Wiener-filtered source images [N, F, T, M] complex64.  ``out`` may be a torch
+        CUDA tensor of that shape (filled asynchronously) or None (a NumPy array is returned)."""
+        if out is not None and torch is not None and isinstance(out, torch.Tensor) and out.is_cuda:
+            assert out.dtype == torch.complex64 and out.is_contiguous()
+            assert tuple(out.shape) == (self.N, self.F, self.T, self.M)
+            _check(_lib.fmnmf_separate(self._ctx, out.data_ptr(), 1), self._ctx)
+            return out
+        res = np.empty((self.N, self.F, self.T, self.M), dtype=np.complex64) if out is None else out
+        _check(_lib.fmnmf_separate(self._ctx, res.ctypes.data, 0), self._ctx)
+        return res
+
+    def get_state(self):
+        W = np.empty((self.N, self.K, self.F), np.float32)
+        H = np.empty((self.N, self.K, self.T), np.float32)
+        G = np.empty((self.N, self.F, self.M), np.float32)
+        Q = np.empty((self.F, self.M, self.M), np.complex64)
+        _check(_lib.fmnmf_get_state(self._ctx, W.ctypes.data, H.ctypes.data, G.ctypes.data, Q.ctypes.data), self._ctx)
+        return W, H, G, Q
+
+    def set_state(self, W, H, G, Q):
+        W, wp = _host_ptr(W, np.float32)
+        H, hp = _host_ptr(H, np.float32)
+        G, gp = _host_ptr(G, np.float32)
+        Q, qp = _host_ptr(Q, np.complex64)
+        assert W.shape == (self.N, self.K, self.F) and H.shape == (self.N, self.K, self.T)
+        assert G.shape == (self.N, self.F, self.M) and Q.shape == (self.F, self.M, self.M)
+        _check(_lib.fmnmf_set_state(self._ctx, wp, hp, gp, qp), self._ctx)
+
+    # -- measurement --------------------------------------------------------------------
+    def set_timing(self, enable: bool):
+        _check(_lib.fmnmf_set_timing(self._ctx, 1 if enable else 0), self._ctx)
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last call (synchronises)."""
+        ms = (ctypes.c_double * 16)()
+        cnt = (ctypes.c_longlong * 16)()
+        n = _I(16)
+        _check(_lib.fmnmf_kernel_times(self._ctx, ctypes.addressof(ms), ctypes.addressof(cnt), ctypes.byref(n)), self._ctx)
+        return {_lib.fmnmf_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n.value)}
+
+    def launch_count(self) -> int:
+        return int(_lib.fmnmf_launch_count(self._ctx))

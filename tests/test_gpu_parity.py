@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Bar for the plain FP32 form: after one iteration from the same state, every result
+(W, H, g~, Q, log-likelihood) is within 1e-5 relative of the oracle
+(||a - b|| / ||b|| per tensor; |dLL| / sum|terms of Eq. 17| for the log-likelihood).
+Shapes span several tiles with ragged tails in F, T, K and every channel bucket.
+"""
+import numpy as np
+import pytest
+
+from oracle import fastmnmf_oracle as O
+from paper_1903_03237_gb300.synth import make_mixture, make_state, config_mixture, CONFIGS
+
+from tests._parity import rel, maxrel, ll_rel, as64
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5          # plain FP32 form, one iteration from the same state
+TOL_WIENER = 1e-5   # separated images, same state
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf
+    return fastmnmf
+
+
+# (F, T, M, N, K): ragged tails everywhere, every M bucket, odd K, N > M and N < M
+SHAPES = [
+    (37, 150, 3, 3, 5),
+    (20, 64, 8, 3, 4),
+    (19, 45, 1, 2, 3),
+    (33, 70, 2, 4, 7),
+    (9, 300, 5, 2, 1),
+    (70, 33, 6, 2, 9),
+    (13, 29, 7, 4, 2),
+    (40, 90, 4, 6, 16),
+]
+
+
+def _one_iter_case(fm, F, T, M, N, K, seed=1, mask=O.UPDATE_ALL, normalise=True):
+    mix = make_mixture(F, T, M, N, K, seed)
+    W, H, G, Q = make_state(F, T, M, N, K, seed)
+    ctx = fm.Context(mix.X, N, K, seed=0, update_mask=mask, normalise=normalise)
+    ctx.set_state(W, H, G, Q)
+    X64 = mix.X.astype(np.complex128)
+    ll0 = ctx.loglik()
+    ll0_ref = O.loglik(X64, *as64(W, H, G, Q))
+    assert ll_rel(ll0, ll0_ref, X64, *as64(W, H, G, Q)) < TOL
+    ctx.iterate(1)
+    ll = ctx.loglik()
+    Wg, Hg, Gg, Qg = ctx.get_state()
+    Wr, Hr, Gr, Qr, tr = O.iterate(X64, *as64(W, H, G, Q), n_iter=1, mask=mask, do_normalise=normalise)
+    ctx.close()
+    return dict(W=rel(Wg, Wr), H=rel(Hg, Hr), G=rel(Gg, Gr), Q=rel(Qg, Qr),
+                LL=ll_rel(ll, tr[-1], X64, Wr, Hr, Gr, Qr))
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in SHAPES])
+def test_one_iteration_matches_oracle(fm, shape):
+    err = _one_iter_case(fm, *shape)
+    assert max(err.values()) < TOL, err
+
+
+@pytest.mark.parametrize("mask", [O.UPDATE_W, O.UPDATE_H, O.UPDATE_G, O.UPDATE_Q],
+                         ids=["W", "H", "G", "Q"])
+@pytest.mark.parametrize("normalise", [False, True], ids=["raw", "norm"])
+def test_each_block_alone(fm, mask, normalise):
+    err = _one_iter_case(fm, 29, 77, 3, 3, 5, seed=3, mask=mask, normalise=normalise)
+    assert max(err.values()) < TOL, err
+
+
+def test_init_state_matches_spec(fm):
+    F, T, M, N, K, seed = 21, 35, 3, 4, 6, 12345
+    mix = make_mixture(F, T, M, N, K, 5)
+    ctx = fm.Context(mix.X, N, K, seed=seed)
+    W, H, G, Q = ctx.get_state()
+    Wr, Hr, Gr, Qr = O.init_state(F, T, M, N, K, seed)
+    np.testing.assert_array_equal(W, Wr.astype(np.float32))
+    np.testing.assert_array_equal(H, Hr.astype(np.float32))
+    np.testing.assert_allclose(G, Gr, rtol=1e-7)
+    np.testing.assert_array_equal(Q, Qr.astype(np.complex64))
+    X64 = mix.X.astype(np.complex128)
+    assert ll_rel(ctx.loglik(), O.loglik(X64, Wr, Hr, Gr, Qr), X64, Wr, Hr, Gr, Qr) < TOL
+
+
+def test_c0_trajectory_monotone_and_close(fm):
+    c = CONFIGS["c0"]
+    F, T, M, N, K = c["F"], c["T"], c["M"], c["N"], c["K"]
+    mix = config_mixture("c0", seed=0)
+    W, H, G, Q = make_state(F, T, M, N, K, 0)
+    ctx = fm.Context(mix.X, N, K)
+    ctx.set_state(W, H, G, Q)
+    lls = [ctx.loglik()]
+    for _ in range(c["iters"]):
+        ctx.iterate(1)
+        lls.append(ctx.loglik())
+    d = np.diff(lls)
+    scale = np.abs(lls).max()
+    assert np.all(d >= -1e-6 * scale), d.min()
+    X64 = mix.X.astype(np.complex128)
+    *_, tr = O.iterate(X64, *as64(W, H, G, Q), n_iter=c["iters"])
+    # FP32 trajectory drift over 20 iterations (reported bar: 1e-4 of the LL scale)
+    assert abs(lls[-1] - tr[-1]) / abs(tr[-1]) < 1e-4, (lls[-1], tr[-1])
+
+
+def test_c1_full_size_one_iteration(fm):
+    c = CONFIGS["c1"]
+    F, T, M, N, K = c["F"], c["T"], c["M"], c["N"], c["K"]
+    mix = config_mixture("c1", seed=0)
+    ctx = fm.Context(mix.X, N, K, seed=0)
+    W, H, G, Q = ctx.get_state()
+    ctx.iterate(1)
+    Wg, Hg, Gg, Qg = ctx.get_state()
+    ll = ctx.loglik()
+    X64 = mix.X.astype(np.complex128)
+    Wr, Hr, Gr, Qr, tr = O.iterate(X64, *as64(W, H, G, Q), n_iter=1)
+    err = dict(W=rel(Wg, Wr), H=rel(Hg, Hr), G=rel(Gg, Gr), Q=rel(Qg, Qr),
+               LL=ll_rel(ll, tr[-1], X64, Wr, Hr, Gr, Qr))
+    assert max(err.values()) < TOL, err
+
+
+@pytest.mark.parametrize("shape", [(37, 150, 3, 3, 5), (20, 64, 8, 3, 4), (33, 70, 2, 4, 7), (19, 45, 1, 2, 3)],
+                         ids=["M3", "M8", "M2", "M1"])
+def test_wiener_matches_oracle(fm, shape):
+    F, T, M, N, K = shape
+    mix = make_mixture(F, T, M, N, K, 2)
+    W, H, G, Q = make_state(F, T, M, N, K, 2)
+    ctx = fm.Context(mix.X, N, K)
+    ctx.set_state(W, H, G, Q)
+    S = ctx.separate()
+    X64 = mix.X.astype(np.complex128)
+    Sr = O.separate(X64, *as64(W, H, G, Q))
+    assert rel(S, Sr) < TOL_WIENER and maxrel(S, Sr) < 10 * TOL_WIENER
+    # the images add up to the mixture (Eq. 2)
+    assert rel(S.sum(axis=0), X64) < TOL_WIENER
+
+
+def test_wiener_device_output(fm):
+    import torch
+    F, T, M, N, K = 37, 150, 3, 3, 5
+    mix = make_mixture(F, T, M, N, K, 4)
+    ctx = fm.Context(torch.from_numpy(mix.X).cuda(), N, K, seed=3)
+    ctx.iterate(3)
+    out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
+    ctx.separate(out)
+    host = ctx.separate()
+    np.testing.assert_array_equal(out.cpu().numpy(), host)
+
+
+def test_degenerate_shapes(fm):
+    for (F, T, M, N, K) in [(1, 1, 1, 1, 1), (1, 7, 2, 1, 1), (5, 2, 2, 3, 1), (2, 1, 1, 2, 2)]:
+        err = _one_iter_case(fm, F, T, M, N, K, seed=9)
+        assert max(err.values()) < TOL, ((F, T, M, N, K), err)
+
+
+def test_deterministic(fm):
+    mix = make_mixture(37, 150, 3, 3, 5, 6)
+    outs = []
+    for _ in range(2):
+        ctx = fm.Context(mix.X, 3, 5, seed=11)
+        ctx.iterate(5)
+        outs.append(ctx.get_state() + (ctx.loglik(),))
+        ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_resume_from_checkpoint(fm):
+    mix = make_mixture(37, 150, 3, 3, 5, 7)
+    a = fm.Context(mix.X, 3, 5, seed=2)
+    a.iterate(6)
+    ref = a.get_state()
+    b = fm.Context(mix.X, 3, 5, seed=2)
+    b.iterate(3)
+    st = b.get_state()
+    c = fm.Context(mix.X, 3, 5, seed=99)
+    c.set_state(*st)
+    c.iterate(3)
+    got = c.get_state()
+    for x, y in zip(got, ref):
+        assert rel(x, y) < 1e-5
+
+
+def test_errors(fm):
+    X = make_mixture(10, 20, 2, 2, 2, 1).X.copy()
+    X[3, 4, 1] = np.nan
+    with pytest.raises(fm.FastMNMFError) as e:
+        fm.Context(X, 2, 2)
+    assert e.value.status == fm.ENONFINITE
+    with pytest.raises(fm.FastMNMFError) as e:
+        fm.Context(make_mixture(10, 20, 2, 2, 2, 1).X, 2, 2, hbm_budget=1000)
+    assert e.value.status == fm.ENOMEM
+    ctx = fm.Context(make_mixture(10, 20, 2, 2, 2, 1).X, 2, 2)
+    W, H, G, Q = ctx.get_state()
+    W[0, 0, 0] = -1.0
+    with pytest.raises(fm.FastMNMFError) as e:
+        ctx.set_state(W, H, G, Q)
+    assert e.value.status == fm.EINVAL
+    # an all-zero bin makes every V_fm of that bin vanish: the IP system is singular
+    X = make_mixture(10, 20, 2, 2, 2, 1).X.copy()
+    X[4] = 0
+    ctx = fm.Context(X, 2, 2)
+    ctx.iterate(1)
+    with pytest.raises(fm.FastMNMFError) as e:
+        ctx.sync()
+    assert e.value.status in (fm.ESINGULAR, fm.ENONFINITE)
+
+
+def test_restart_reproduces_job(fm):
+    mix = make_mixture(37, 150, 3, 3, 5, 8)
+    ctx = fm.Context(mix.X, 3, 5, seed=4)
+    ctx.iterate(7)
+    a = ctx.get_state() + (ctx.loglik(),)
+    ctx.iterate(5)
+    ctx.restart()
+    ctx.iterate(7)
+    b = ctx.get_state() + (ctx.loglik(),)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
