@@ -26,7 +26,7 @@ using namespace fm;
 thread_local std::string g_thread_err;
 
 constexpr int kMaxChunk = 100;          // iterations per captured graph
-constexpr int kSmemTarget = 100 * 1024;  // bytes per CTA aimed for (two CTAs per SM)
+constexpr int kSmemTarget = 72 * 1024;   // bytes per CTA aimed for (three CTAs per SM)
 constexpr int kSmemMax = 220 * 1024;     // hard ceiling (227 KB per CTA on sm_103a)
 
 const char* kKindNames[KK_COUNT] = {"w_update", "h_update", "g_update", "scm", "xt_loglik",
@@ -57,7 +57,7 @@ struct fmnmf_ctx {
   float* W0 = nullptr;
   float* H0 = nullptr;
   float* G0 = nullptr;
-  double2* Q0 = nullptr;
+  float4* Q0 = nullptr;
   std::map<std::pair<int, int>, GraphEntry> graphs;  // (chunk, timing) -> graph
   std::string err;
   bool timing = false;
@@ -99,6 +99,14 @@ cudaError_t launch(fmnmf_ctx* c, KernelKind k, const LaunchArgs& a) {
   }
 }
 
+int occupancy(int maxm, KernelKind k, size_t smem) {
+  switch (maxm) {
+    case 2: return occupancy_m2(k, smem);
+    case 4: return occupancy_m4(k, smem);
+    default: return occupancy_m8(k, smem);
+  }
+}
+
 cudaError_t configure(int maxm, int bytes) {
   switch (maxm) {
     case 2: return configure_m2(bytes);
@@ -108,11 +116,12 @@ cudaError_t configure(int maxm, int bytes) {
 }
 
 // Tiling of a sweep over an own extent SO (tiles of kOT) and an inner extent SI split
-// S ways so that the grid has about `target` CTAs; sub-chunks of at most ic_cap.
-Geom make_geom(int SO, int SI, int ic_cap, int target) {
+// S ways so that the grid fills the `slots` CTAs the device holds at once (one wave);
+// sub-chunks of at most ic_cap.
+Geom make_geom(int SO, int SI, int ic_cap, int slots) {
   Geom g;
   g.n_own_tiles = (SO + kOT - 1) / kOT;
-  int S = std::max(1, (target + g.n_own_tiles - 1) / g.n_own_tiles);
+  int S = std::max(1, slots / g.n_own_tiles);
   S = std::min(S, (SI + 3) / 4);
   int span = (SI + S - 1) / S;
   span = (span + 3) & ~3;
@@ -149,7 +158,6 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int target = 2 * sms;
   int caps[4];
   for (int mode = 0; mode < 4; ++mode) {
     int cap = ic_cap_for(mode, N, K, M, mx, kSmemTarget);
@@ -157,10 +165,18 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     if (cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K = %d too large for the shared-memory tiles", N * K);
     caps[mode] = cap;
   }
-  ctx->gW = make_geom(F, T, caps[MODE_W], target);
-  ctx->gH = make_geom(T, F, caps[MODE_H], target);
-  ctx->gG = make_geom(F, T, caps[MODE_G], target);
-  ctx->gY = make_geom(F, T, caps[MODE_Y], target);
+  size_t mx_cap_smem = 48 * 1024;
+  for (int mode = 0; mode < 4; ++mode)
+    mx_cap_smem = std::max(mx_cap_smem, smem_bytes(mode, N, K, M, mx, caps[mode]));
+  CK(configure(mx, (int)mx_cap_smem));
+  const KernelKind kinds[4] = {KK_W, KK_H, KK_G, KK_Y};
+  auto slots = [&](int mode) {
+    return sms * occupancy(mx, kinds[mode], smem_bytes(mode, N, K, M, mx, caps[mode]));
+  };
+  ctx->gW = make_geom(F, T, caps[MODE_W], slots(MODE_W));
+  ctx->gH = make_geom(T, F, caps[MODE_H], slots(MODE_H));
+  ctx->gG = make_geom(F, T, caps[MODE_G], slots(MODE_G));
+  ctx->gY = make_geom(F, T, caps[MODE_Y], slots(MODE_Y));
   ctx->smW = smem_bytes(MODE_W, N, K, M, mx, ctx->gW.IC);
   ctx->smH = smem_bytes(MODE_H, N, K, M, mx, ctx->gH.IC);
   ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC);
@@ -172,10 +188,10 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     for (int ic = 256; ic >= 4; ic -= 4)
       if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemMax) { sep_cap = ic; break; }
   if (sep_cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K too large for the Wiener tiles");
-  ctx->gS = make_geom(F, T, sep_cap, target);
+  mx_cap_smem = std::max(mx_cap_smem, sep_smem_bytes(N, K, M, mx, sep_cap));
+  CK(configure(mx, (int)mx_cap_smem));
+  ctx->gS = make_geom(F, T, sep_cap, sms * occupancy(mx, KK_SEP, sep_smem_bytes(N, K, M, mx, sep_cap)));
   ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC);
-  size_t mx_smem = std::max({ctx->smW, ctx->smH, ctx->smG, ctx->smY, ctx->smS});
-  CK(configure(mx, (int)std::max<size_t>(mx_smem, 48 * 1024)));
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = (N * K + (kThreads / 32) - 1) / (kThreads / 32);
   return FMNMF_OK;
@@ -206,7 +222,8 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
       {(void**)&p.W, N * K * F * 4},
       {(void**)&p.H, N * K * T * 4},
       {(void**)&p.G, N * F * M * 4},
-      {(void**)&p.Qd, F * M * M * sizeof(double2)},
+      {(void**)&p.Qx, F * M * M * sizeof(float4)},
+      {(void**)&p.Qix, F * M * M * sizeof(float4)},
       {(void**)&p.Qf, F * M * M * sizeof(float2)},
       {(void**)&p.Qinv, F * M * M * sizeof(float2)},
       {(void**)&p.xt, F * T * M * 4},
@@ -221,7 +238,7 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
       {(void**)&ctx->W0, N * K * F * 4},
       {(void**)&ctx->H0, N * K * T * 4},
       {(void**)&ctx->G0, N * F * M * 4},
-      {(void**)&ctx->Q0, F * M * M * sizeof(double2)},
+      {(void**)&ctx->Q0, F * M * M * sizeof(float4)},
   };
   size_t total = 0;
   for (auto& s : slots) total += align256(s.bytes);
@@ -288,7 +305,7 @@ cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
   if (yflags) {
     LaunchArgs a;
     a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
-    a.grid = dim3((c->F + kIpWarps - 1) / kIpWarps);
+    a.grid = dim3(c->F);
     if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
   }
   LaunchArgs x;
@@ -305,7 +322,6 @@ fmnmf_status refresh_state(fmnmf_ctx* ctx) {
   LaunchArgs a;
   a.p = ctx->p; a.st = ctx->st;
   a.grid = dim3((ctx->F + 7) / 8);
-  a.prep_mode = 0;
   CK(launch(ctx, KK_PREP, a));
   CK(launch(ctx, KK_Y, tile_args(ctx, ctx->gY, ctx->smY, 0, ctx->ctrY)));
   LaunchArgs x;
@@ -320,7 +336,7 @@ fmnmf_status snapshot(fmnmf_ctx* ctx, bool restore) {
   const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
   struct { void* live; void* snap; size_t bytes; } c[4] = {
       {ctx->p.W, ctx->W0, N * K * F * 4}, {ctx->p.H, ctx->H0, N * K * T * 4},
-      {ctx->p.G, ctx->G0, N * F * M * 4}, {ctx->p.Qd, ctx->Q0, F * M * M * sizeof(double2)}};
+      {ctx->p.G, ctx->G0, N * F * M * 4}, {ctx->p.Qx, ctx->Q0, F * M * M * sizeof(float4)}};
   for (auto& e : c)
     CK(cudaMemcpyAsync(restore ? e.live : e.snap, restore ? e.snap : e.live, e.bytes,
                        cudaMemcpyDeviceToDevice, ctx->st));
@@ -382,7 +398,7 @@ fmnmf_status seed_state(fmnmf_ctx* ctx, uint64_t seed) {
   const int F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
   const size_t nw = (size_t)N * K * F, nh = (size_t)N * K * T;
   std::vector<float> W(nw), H(nh), G((size_t)N * F * M);
-  std::vector<double2> Q((size_t)F * M * M);
+  std::vector<float4> Q((size_t)F * M * M);
   for (size_t i = 0; i < nw; ++i) W[i] = (float)(0.1 + (double)(sm64(seed, i) >> 11) * 0x1.0p-53);
   for (size_t i = 0; i < nh; ++i) H[i] = (float)(0.1 + (double)(sm64(seed, nw + i) >> 11) * 0x1.0p-53);
   for (int n = 0; n < N; ++n) {
@@ -393,11 +409,11 @@ fmnmf_status seed_state(fmnmf_ctx* ctx, uint64_t seed) {
   }
   for (int f = 0; f < F; ++f)
     for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) Q[((size_t)f * M + i) * M + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      for (int j = 0; j < M; ++j) Q[((size_t)f * M + i) * M + j] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
   CK(cudaMemcpyAsync(ctx->p.W, W.data(), nw * 4, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->p.H, H.data(), nh * 4, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->p.G, G.data(), G.size() * 4, cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->p.Qd, Q.data(), Q.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.Qx, Q.data(), Q.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
   // the host vectors die at return: wait for the copies
   CK(cudaStreamSynchronize(ctx->st));
@@ -555,16 +571,12 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
     if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     dst = tmp;
   }
+  // Q_f^-1 is kept current by the IP update (and by the preparation of a set state)
   Recorder rec{ctx, ctx->timing ? &ctx->pending : nullptr};
   LaunchArgs a;
-  a.p = ctx->p; a.st = ctx->st; a.grid = dim3((ctx->F + 7) / 8); a.prep_mode = 1;
-  cudaError_t e = rec.run(KK_PREP, a);
-  if (e == cudaSuccess) {
-    LaunchArgs s;
-    s.p = ctx->p; s.g = ctx->gS; s.smem = ctx->smS; s.st = ctx->st; s.out = dst;
-    s.grid = dim3(ctx->gS.n_own_tiles, ctx->gS.S);
-    e = rec.run(KK_SEP, s);
-  }
+  a.p = ctx->p; a.g = ctx->gS; a.smem = ctx->smS; a.st = ctx->st; a.out = dst;
+  a.grid = dim3(ctx->gS.n_own_tiles, ctx->gS.S);
+  cudaError_t e = rec.run(KK_SEP, a);
   if (e != cudaSuccess) {
     if (tmp) cudaFreeAsync(tmp, ctx->st);
     return set_err(ctx, FMNMF_ECUDA, "separate launch: %s", cudaGetErrorString(e));
@@ -599,16 +611,16 @@ fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, con
   if (!nonneg(W, N * K * F) || !nonneg(H, N * K * T) || !nonneg(G, N * F * M))
     return set_err(ctx, FMNMF_EINVAL, "W, H and G must be finite and nonnegative");
   const float* q = (const float*)Q;
-  std::vector<double2> Qd(F * M * M);
+  std::vector<float4> Qx(F * M * M);
   for (size_t i = 0; i < F * M * M; ++i) {
     if (!std::isfinite(q[2 * i]) || !std::isfinite(q[2 * i + 1])) return set_err(ctx, FMNMF_EINVAL, "Q must be finite");
-    Qd[i] = make_double2(q[2 * i], q[2 * i + 1]);
+    Qx[i] = make_float4(q[2 * i], 0.f, q[2 * i + 1], 0.f);
   }
   CK(cudaStreamSynchronize(ctx->st));
   CK(cudaMemcpy(ctx->p.W, W, N * K * F * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->p.H, H, N * K * T * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->p.G, G, N * F * M * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->p.Qd, Qd.data(), Qd.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->p.Qx, Qx.data(), Qx.size() * sizeof(float4), cudaMemcpyHostToDevice));
   CK(cudaMemset(ctx->p.status, 0, 4));
   fmnmf_status s = snapshot(ctx, false);
   if (s != FMNMF_OK) return s;

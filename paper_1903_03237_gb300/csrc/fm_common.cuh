@@ -22,12 +22,13 @@ struct Prob {
   float* W;            // [N][K][F]
   float* H;            // [N][K][T]
   float* G;            // [N][F][M]
-  double2* Qd;         // [F][M][M] float64 master copy of the diagonalisers
-  float2* Qf;          // [F][M][M] float32 copy used by the sweeps
-  float2* Qinv;        // [F][M][M] float32 inverse (Wiener filter)
+  float4* Qx;          // [F][M][M] diagonalisers, float-float (re.hi, re.lo, im.hi, im.lo)
+  float4* Qix;         // [F][M][M] their inverses, float-float (carried by the IP update)
+  float2* Qf;          // [F][M][M] float32 copy of Q used by the sweeps
+  float2* Qinv;        // [F][M][M] float32 copy of Q^-1 (Wiener filter)
   float* xt;           // [F][T][M] projected powers x~
   float* yt;           // [F][T][M] model powers y~
-  double* logdet;      // [F] log|det Q_f|^2
+  double* logdet;      // [F] log|det Q_f|^2 (carried by the IP update)
   float* phi;          // [F] tr(Q_f Q_f^H)/M of the last IP update (1 if none)
   double* ll;          // [1] log-likelihood of the current state
   unsigned* status;    // [1] sticky ST_* bits

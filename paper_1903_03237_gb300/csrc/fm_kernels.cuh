@@ -15,6 +15,7 @@
 // tiles staged in shared memory; it is never written to memory.
 #pragma once
 #include "fm_common.cuh"
+#include "fm_df64.cuh"
 
 namespace fm {
 
@@ -256,14 +257,18 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
   for (int i0 = i_begin; sweep && i0 < i_end; i0 += IC) {
     const int icn = min(IC, i_end - i0);
     __syncthreads();  // previous sub-chunk fully consumed
-    for (int e = tid; e < NK * IC; e += kThreads) {
-      int nk = e / IC, i = e % IC;
-      oth_s[nk * ICP + i] = (i < icn) ? othF[(size_t)nk * SI + i0 + i] : 0.f;
+    // stage the other factor: one warp per row, lanes along the contiguous index
+    for (int row = tid >> 5; row < NK; row += kThreads / 32) {
+      const float* src = othF + (size_t)row * SI + i0;
+      float* dst = oth_s + row * ICP;
+      for (int i = tid & 31; i < IC; i += 32) dst[i] = (i < icn) ? src[i] : 0.f;
     }
     if (!F_OWN) {
-      for (int e = tid; e < N * IC * M; e += kThreads) {
-        int n = e / (IC * M), i = (e / M) % IC, m = e % M;
-        g_s[e] = (i < icn) ? p.G[((size_t)n * F + i0 + i) * M + m] : 0.f;
+      // g~[n][i0 .. i0+icn)[0..M) is contiguous for each n
+      const int len = IC * M, valid = icn * M;
+      for (int n = 0; n < N; ++n) {
+        const float* src = p.G + ((size_t)n * F + i0) * M;
+        for (int j = tid; j < len; j += kThreads) g_s[n * len + j] = (j < valid) ? src[j] : 0.f;
       }
     }
     __syncthreads();
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
               binv[b][m] = 0.f;
               if (v && m < M) {
                 p.yt[pt * M + m] = y[a][b][m];
-                binv[b][m] = __frcp_rn(y[a][b][m]);
+                binv[b][m] = __fdividef(1.f, y[a][b][m]);
               }
             }
           }
@@ -364,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
             for (int m = 0; m < MAXM; ++m) {
               A[b][m] = 0.f; B[b][m] = 0.f;
               if (v && m < M) {
-                const float bi = __frcp_rn(y[a][b][m]);
+                const float bi = __fdividef(1.f, y[a][b][m]);
                 const float x = p.xt[pt * M + m];
                 B[b][m] = bi;
                 A[b][m] = x * bi * bi;
@@ -576,83 +581,184 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 }
 
 // ---------------------------------------------------------------------------------
-// IP update (Eqs. 18-20) and the per-bin normalisation, one warp per bin, float64:
-// V_fm = (1/T) sum of the MODE_Y splits; rows m = 0..M-1 in order; log|det Q_f|^2;
-// phi_f = tr(Q_f Q_f^H)/M with Q_f /= sqrt(phi_f), g~_nf /= phi_f; then
-// nu_nf = sum_m g~_nfm with g~_nf /= nu_nf, w_nkf *= nu_nf.
+// IP update (Eqs. 18-20) and the per-bin normalisation.  One CTA per bin, one warp per
+// channel, float-float arithmetic (about 48 significand bits) on the FP32 pipes.
+//
+// Eq. 19 solves (Q_f V_fm) q = e_m with the current Q_f.  Since (Q_f V_fm)^-1 =
+// V_fm^-1 Q_f^-1, q = V_fm^-1 c_m with c_m = Q_f^-1 e_m.  V_fm depends only on y~, so the
+// M inverses are formed first, in parallel (warp m sweeps V_fm: Hermitian positive
+// definite, no pivoting).  Warp 0 then runs the rows in order m = 0..M-1:
+//   q = V_fm^-1 c_m,   s = c_m^H q  (= q^H V_fm q, Eq. 20),   q_new = q / sqrt(s),
+//   row m of Q_f <- q_new^H,
+//   Q_f^-1 <- Q_f^-1 - c_m (q_new^H Q_f^-1 - e_m^T) / sqrt(s)   (Sherman-Morrison),
+//   log|det Q_f|^2 += log s                                      (determinant lemma),
+// so Q_f^-1 and log|det Q_f|^2 are carried across iterations instead of re-factored.
+// Then phi_f = tr(Q_f Q_f^H)/M: Q_f /= sqrt(phi), Q_f^-1 *= sqrt(phi), g~_nf /= phi,
+// log|det|^2 -= M log phi; nu_nf = sum_m g~_nfm: g~_nf /= nu, w_nkf *= nu.
 // ---------------------------------------------------------------------------------
-constexpr int kIpWarps = 2;
-
 template <int MAXM>
-__global__ void __launch_bounds__(kIpWarps * 32) k_ip(Prob p, int S, int flags) {
+__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
   constexpr int MM = MAXM * MAXM;
-  constexpr int LD = MAXM + 1;
-  __shared__ double vs_s[kIpWarps][MAXM * MM];
-  __shared__ double2 Q_s[kIpWarps][MM];
-  __shared__ double2 A_s[kIpWarps][MAXM * LD];
-  __shared__ double2 fac_s[kIpWarps][MAXM];
-  __shared__ double2 qv_s[kIpWarps][MAXM];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f = blockIdx.x * kIpWarps + warp;
-  if (f >= p.F) return;
+  __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
+  __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
+  __shared__ float4 row_s[MAXM][MAXM];   // per warp: row k after scaling
+  __shared__ float4 Q_s[MM], Qi_s[MM];
+  __shared__ float4 c_s[MAXM], q_s[MAXM], u_s[MAXM];
+  __shared__ float vsum_s[MAXM][MM];      // packed split sums per m
+  __shared__ double ld_s;
+  __shared__ int bad_s;
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = p.M, N = p.N, K = p.K, F = p.F;
-  double* vs = vs_s[warp];
-  double2* Q = Q_s[warp];
-  double2* A = A_s[warp];
-  double2* fac = fac_s[warp];
-  double2* qv = qv_s[warp];
-  bool ok = true;
-  for (int e = lane; e < MM; e += 32) {
-    const int r = e / MAXM, c = e % MAXM;
-    Q[e] = (r < M && c < M) ? p.Qd[((size_t)f * M + r) * M + c] : make_double2(0.0, 0.0);
+  if (f >= F) return;
+  for (int e = tid; e < M * M; e += blockDim.x) {
+    const int r = e / M, c = e % M;
+    Q_s[r * MAXM + c] = p.Qx[(size_t)f * M * M + e];
+    Qi_s[r * MAXM + c] = p.Qix[(size_t)f * M * M + e];
   }
+  if (tid == 0) { ld_s = p.logdet[f]; bad_s = 0; }
   if (flags & FLAG_DO_V) {
+    // packed split sums (float32, fixed order over the splits)
     const size_t psz = (size_t)F * M * MM;
-    const double invT = 1.0 / (double)p.T;
-    for (int e = lane; e < M * MM; e += 32) {
+    for (int e = tid; e < M * MM; e += blockDim.x) {
       float sum = 0.f;
       for (int ss = 0; ss < S; ++ss) sum += __ldcg(p.part + (size_t)ss * psz + (size_t)f * M * MM + e);
-      vs[e] = (double)sum * invT;
+      vsum_s[e / MM][e % MM] = sum;
     }
-    __syncwarp();
-    ok = warp_ip_bin<MAXM>(M, vs, Q, A, fac, qv);
-  }
-  __syncwarp();
-  for (int e = lane; e < M * M; e += 32) A[(e / M) * LD + (e % M)] = Q[(e / M) * MAXM + (e % M)];
-  __syncwarp();
-  double ld = warp_logdet2(M, LD, A, fac);
-  double phi = 1.0;
-  if (flags & FLAG_NORMALISE) {
-    double tr = 0.0;
-    for (int e = lane; e < M * M; e += 32) tr += cabs2(Q[(e / M) * MAXM + (e % M)]);
-    for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    phi = tr / (double)M;
-    ld -= (double)M * log(phi);
-  }
-  const double sc = 1.0 / sqrt(phi);
-  for (int e = lane; e < M * M; e += 32) {
-    const double2 q = Q[(e / M) * MAXM + (e % M)];
-    const double2 qs = make_double2(q.x * sc, q.y * sc);
-    p.Qd[(size_t)f * M * M + e] = qs;
-    p.Qf[(size_t)f * M * M + e] = make_float2((float)qs.x, (float)qs.y);
-  }
-  if (flags & FLAG_NORMALISE) {
-    // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
-    const float fphi = (float)phi;
-    for (int n = lane; n < N; n += 32) {
-      float* gp = p.G + ((size_t)n * F + f) * M;
-      float nu = 0.f;
-      for (int m = 0; m < M; ++m) { const float gv = gp[m] / fphi; gp[m] = gv; nu += gv; }
-      for (int m = 0; m < M; ++m) gp[m] /= nu;
-      for (int k = 0; k < K; ++k) p.W[((size_t)n * K + k) * F + f] *= nu;
-      if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
+    __syncthreads();
+    if (warp < M) {
+      const int m = warp;
+      float4* A = A_s[m];
+      const float* v = vsum_s[m];
+      for (int e = lane; e < M * M; e += 32) {
+        const int j = e / M, c = e % M;
+        float re, im;
+        if (j == c) { re = v[j * MAXM + j]; im = 0.f; }
+        else if (j < c) { re = v[j * MAXM + c]; im = v[c * MAXM + j]; }
+        else { re = v[c * MAXM + j]; im = -v[j * MAXM + c]; }
+        A[j * MAXM + c] = make_float4(re, 0.f, im, 0.f);
+      }
+      __syncwarp();
+      // in-place Gauss-Jordan sweep of the Hermitian positive definite matrix
+      bool ok = true;
+      for (int k = 0; k < M; ++k) {
+        if (lane < M) col_s[m][lane] = A[lane * MAXM + k];
+        __syncwarp();
+        const df piv = cdf_unpack(col_s[m][k]).re;
+        ok = ok && (piv.hi > 0.f) && isfinite(piv.hi);
+        const df inv = df_rcp(piv);
+        if (lane < M) row_s[m][lane] = cdf_pack(cdf_scale(cdf_unpack(A[k * MAXM + lane]), inv));
+        __syncwarp();
+        for (int e = lane; e < M * M; e += 32) {
+          const int i = e / M, j = e % M;
+          cdf val;
+          if (i == k && j == k) val = cdf{inv, df{0.f, 0.f}};
+          else if (i == k) val = cdf_unpack(row_s[m][j]);
+          else if (j == k) val = cdf_scale(cdf_unpack(col_s[m][i]), df_neg(inv));
+          else val = cdf_sub(cdf_unpack(A[i * MAXM + j]), cdf_mul(cdf_unpack(col_s[m][i]), cdf_unpack(row_s[m][j])));
+          A[i * MAXM + j] = cdf_pack(val);
+        }
+        __syncwarp();
+      }
+      if (!ok && lane == 0) bad_s = 1;
     }
+    __syncthreads();
+    if (warp == 0) {
+      const df Tdf = df_make((float)p.T);
+      double ld_add = 0.0;
+      for (int m = 0; m < M; ++m) {
+        const float4* Vi = A_s[m];
+        if (lane < M) c_s[lane] = Qi_s[lane * MAXM + m];
+        __syncwarp();
+        // q_i = T sum_j Vi[i][j] c_j   (lanes: i = lane / MAXM, j = lane % MAXM, MAXM*MAXM <= 64)
+        for (int base = 0; base < MM; base += 32) {
+          const int e = base + lane;
+          const int i = e / MAXM, j = e % MAXM;
+          cdf t = cdf_zero();
+          if (e < MM && i < M && j < M) t = cdf_mul(cdf_unpack(Vi[i * MAXM + j]), cdf_unpack(c_s[j]));
+          for (int o = 1; o < MAXM; o <<= 1) t = cdf_add(t, shfl_xor_cdf(t, o));
+          if (e < MM && j == 0 && i < M) q_s[i] = cdf_pack(cdf_scale(t, Tdf));
+        }
+        __syncwarp();
+        // s = Re(c^H q)
+        df sv = df{0.f, 0.f};
+        if (lane < M) sv = cdf_cmul(cdf_unpack(c_s[lane]), cdf_unpack(q_s[lane])).re;
+        for (int o = 16; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
+        if (!(sv.hi > 0.f) || !isfinite(sv.hi)) { if (lane == 0) bad_s = 1; sv = df_make(1.f); }
+        const df r = df_rsqrt(sv);
+        ld_add += (double)logf(sv.hi) + (double)(sv.lo / sv.hi);
+        // q_new, row m of Q = q_new^H
+        if (lane < M) {
+          const cdf qn = cdf_scale(cdf_unpack(q_s[lane]), r);
+          q_s[lane] = cdf_pack(qn);
+          Q_s[m * MAXM + lane] = cdf_pack(cdf_conj(qn));
+        }
+        __syncwarp();
+        // u_j = sum_i conj(qn_i) Qi[i][j]   (lanes: j = lane / MAXM, i = lane % MAXM)
+        for (int base = 0; base < MM; base += 32) {
+          const int e = base + lane;
+          const int j = e / MAXM, i = e % MAXM;
+          cdf t = cdf_zero();
+          if (e < MM && i < M && j < M) t = cdf_cmul(cdf_unpack(q_s[i]), cdf_unpack(Qi_s[i * MAXM + j]));
+          for (int o = 1; o < MAXM; o <<= 1) t = cdf_add(t, shfl_xor_cdf(t, o));
+          if (e < MM && i == 0 && j < M) u_s[j] = cdf_pack(t);
+        }
+        __syncwarp();
+        // Qi[i][j] -= c_i (u_j - delta_jm) r
+        for (int e = lane; e < M * M; e += 32) {
+          const int i = e / M, j = e % M;
+          cdf uj = cdf_unpack(u_s[j]);
+          if (j == m) uj.re = df_sub(uj.re, df_make(1.f));
+          const cdf d = cdf_scale(cdf_mul(cdf_unpack(c_s[i]), uj), r);
+          Qi_s[i * MAXM + j] = cdf_pack(cdf_sub(cdf_unpack(Qi_s[i * MAXM + j]), d));
+        }
+        __syncwarp();
+      }
+      if (lane == 0) ld_s += ld_add;
+    }
+    __syncthreads();
   }
-  if (lane == 0) {
-    p.logdet[f] = ld;
-    p.phi[f] = (float)phi;
-    if (!ok) flag(p.status, ST_SINGULAR);
-    if (!isfinite(ld)) flag(p.status, ST_NONFINITE);
+  // phi normalisation, write-back (warp 0)
+  if (warp == 0) {
+    double phi = 1.0;
+    df sq = df_make(1.f), isq = df_make(1.f);
+    if (flags & FLAG_NORMALISE) {
+      df tr = df{0.f, 0.f};
+      for (int e = lane; e < M * M; e += 32) tr = df_add(tr, cdf_abs2(cdf_unpack(Q_s[(e / M) * MAXM + e % M])));
+      for (int o = 16; o > 0; o >>= 1) tr = df_add(tr, shfl_xor_df(tr, o));
+      const df ph = df_div(tr, df_make((float)M));
+      phi = df_to_double(ph);
+      sq = df_sqrt(ph);
+      isq = df_rcp(sq);
+    }
+    for (int e = lane; e < M * M; e += 32) {
+      const int r = e / M, c = e % M;
+      const cdf q = cdf_scale(cdf_unpack(Q_s[r * MAXM + c]), isq);
+      const cdf qi = cdf_scale(cdf_unpack(Qi_s[r * MAXM + c]), sq);
+      p.Qx[(size_t)f * M * M + e] = cdf_pack(q);
+      p.Qix[(size_t)f * M * M + e] = cdf_pack(qi);
+      p.Qf[(size_t)f * M * M + e] = make_float2(q.re.hi, q.im.hi);
+      p.Qinv[(size_t)f * M * M + e] = make_float2(qi.re.hi, qi.im.hi);
+    }
+    if (flags & FLAG_NORMALISE) {
+      // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
+      const float fphi = (float)phi;
+      for (int n = lane; n < N; n += 32) {
+        float* gp = p.G + ((size_t)n * F + f) * M;
+        float nu = 0.f;
+        for (int m = 0; m < M; ++m) { const float gv = gp[m] / fphi; gp[m] = gv; nu += gv; }
+        for (int m = 0; m < M; ++m) gp[m] /= nu;
+        for (int k = 0; k < K; ++k) p.W[((size_t)n * K + k) * F + f] *= nu;
+        if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
+      }
+    }
+    if (lane == 0) {
+      const double ld = ld_s - (double)M * log(phi);
+      p.logdet[f] = ld;
+      p.phi[f] = (float)phi;
+      if (bad_s) flag(p.status, ST_SINGULAR);
+      if (!isfinite(ld)) flag(p.status, ST_NONFINITE);
+    }
   }
 }
 
@@ -669,7 +775,7 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
   const int M = p.M, T = p.T, F = p.F;
   if ((int)blockIdx.x < n_pt_blocks) {
     const size_t npts = (size_t)F * T;
-    double part = 0.0;
+    float part = 0.f;
     for (int r = 0; r < kPtsPerThread; ++r) {
       const size_t pt = (size_t)blockIdx.x * (kThreads * kPtsPerThread) + (size_t)r * kThreads + tid;
       if (pt >= npts) break;
@@ -700,12 +806,12 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
           ls += -xv / yv - logf(yv);
         }
       }
-      part += (double)ls;
+      part += ls;
     }
-    // block reduction in a fixed order
+    // block reduction in a fixed order (float64 from the warp sums on)
     __shared__ double red[kThreads / 32];
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)part;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
@@ -751,11 +857,12 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
 }
 
 // ---------------------------------------------------------------------------------
-// Per-bin float64 preparation: log|det Q_f|^2, float32 copy of Q_f, phi_f = 1 (mode 0);
-// or the float32 inverse Q_f^-1 for the Wiener filter (mode 1).  One warp per bin.
+// Per-bin preparation of a newly set state (init / set_state / restart), float64, one
+// warp per bin: Q_f^-1 (Gauss-Jordan) and log|det Q_f|^2 (LU), stored in the float-float
+// format the IP kernel carries across iterations; float32 copies; phi_f = 1.
 // ---------------------------------------------------------------------------------
 template <int MAXM>
-__global__ void __launch_bounds__(kThreads) k_prep_q(Prob p, int mode) {
+__global__ void __launch_bounds__(kThreads) k_prep_q(Prob p) {
   __shared__ double2 A_s[kThreads / 32][MAXM * 2 * MAXM];
   __shared__ double2 fac_s[kThreads / 32][MAXM];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -763,33 +870,38 @@ __global__ void __launch_bounds__(kThreads) k_prep_q(Prob p, int mode) {
   if (f >= p.F) return;
   const int M = p.M;
   double2* A = A_s[warp];
-  const double2* q = p.Qd + (size_t)f * M * M;
-  if (mode == 0) {
-    const int LD = MAXM;
-    for (int e = lane; e < M * M; e += 32) {
-      A[(e / M) * LD + e % M] = q[e];
-      p.Qf[(size_t)f * M * M + e] = make_float2((float)q[e].x, (float)q[e].y);
+  const float4* q = p.Qx + (size_t)f * M * M;
+  // log|det Q|^2
+  for (int e = lane; e < M * M; e += 32) {
+    const float4 v = q[e];
+    A[(e / M) * MAXM + e % M] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    p.Qf[(size_t)f * M * M + e] = make_float2(v.x, v.z);
+  }
+  __syncwarp();
+  const double ld = warp_logdet2(M, MAXM, A, fac_s[warp]);
+  // Q^-1
+  const int LD = 2 * MAXM;
+  for (int e = lane; e < M * 2 * M; e += 32) {
+    const int r = e / (2 * M), c = e % (2 * M);
+    if (c < M) {
+      const float4 v = q[r * M + c];
+      A[r * LD + c] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    } else {
+      A[r * LD + c] = make_double2(c - M == r ? 1.0 : 0.0, 0.0);
     }
-    __syncwarp();
-    const double ld = warp_logdet2(M, LD, A, fac_s[warp]);
-    if (lane == 0) {
-      p.logdet[f] = ld;
-      p.phi[f] = 1.f;
-      if (!isfinite(ld)) flag(p.status, ST_SINGULAR);
-    }
-  } else {
-    const int LD = 2 * MAXM;
-    for (int e = lane; e < M * 2 * M; e += 32) {
-      const int r = e / (2 * M), c = e % (2 * M);
-      A[r * LD + c] = (c < M) ? q[r * M + c] : make_double2(c - M == r ? 1.0 : 0.0, 0.0);
-    }
-    __syncwarp();
-    const bool ok = warp_gauss_jordan(M, M, LD, A, fac_s[warp]);
-    for (int e = lane; e < M * M; e += 32) {
-      const double2 v = A[(e / M) * LD + M + e % M];
-      p.Qinv[(size_t)f * M * M + e] = make_float2((float)v.x, (float)v.y);
-    }
-    if (lane == 0 && !ok) flag(p.status, ST_SINGULAR);
+  }
+  __syncwarp();
+  const bool ok = warp_gauss_jordan(M, M, LD, A, fac_s[warp]);
+  for (int e = lane; e < M * M; e += 32) {
+    const double2 v = A[(e / M) * LD + M + e % M];
+    const df re = df_from_double(v.x), im = df_from_double(v.y);
+    p.Qix[(size_t)f * M * M + e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    p.Qinv[(size_t)f * M * M + e] = make_float2(re.hi, im.hi);
+  }
+  if (lane == 0) {
+    p.logdet[f] = ld;
+    p.phi[f] = 1.f;
+    if (!ok || !isfinite(ld)) flag(p.status, ST_SINGULAR);
   }
 }
 
@@ -831,9 +943,10 @@ __global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* _
   for (int i0 = i_begin; i0 < i_end; i0 += IC) {
     const int icn = min(IC, i_end - i0);
     __syncthreads();
-    for (int e = tid; e < NK * IC; e += kThreads) {
-      const int nk = e / IC, i = e % IC;
-      oth_s[nk * ICP + i] = (i < icn) ? p.H[(size_t)nk * T + i0 + i] : 0.f;
+    for (int row = tid >> 5; row < NK; row += kThreads / 32) {
+      const float* src = p.H + (size_t)row * T + i0;
+      float* dst = oth_s + row * ICP;
+      for (int i = tid & 31; i < IC; i += 32) dst[i] = (i < icn) ? src[i] : 0.f;
     }
     __syncthreads();
     const int nq = IC / 4;
@@ -887,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* _
       }
       float yinv[MAXM];
 #pragma unroll
-      for (int m = 0; m < MAXM; ++m) yinv[m] = (m < M) ? __frcp_rn(ytot[m]) : 0.f;
+      for (int m = 0; m < MAXM; ++m) yinv[m] = (m < M) ? __fdividef(1.f, ytot[m]) : 0.f;
       for (int n = 0; n < N; ++n) {
         const float l = lam_s[(n * kOT + o) * ICP + i];
         float2 z[MAXM];

@@ -17,12 +17,26 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
     case KK_XT:
       k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr);
       break;
-    case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.prep_mode); break;
+    case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p); break;
     case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;
-    case KK_IP: k_ip<MX><<<a.grid, kIpWarps * 32, 0, a.st>>>(a.p, a.S, a.flags); break;
+    case KK_IP: k_ip<MX><<<a.grid, MX * 32, 0, a.st>>>(a.p, a.S, a.flags); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+int FM_CAT(occupancy_m, FM_MAXM)(KernelKind k, size_t smem) {
+  constexpr int MX = FM_MAXM;
+  int n = 0;
+  switch (k) {
+    case KK_W: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<MX, MODE_W>, kThreads, smem); break;
+    case KK_H: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<MX, MODE_H>, kThreads, smem); break;
+    case KK_G: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<MX, MODE_G>, kThreads, smem); break;
+    case KK_Y: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<MX, MODE_Y>, kThreads, smem); break;
+    case KK_SEP: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_separate<MX>, kThreads, smem); break;
+    default: n = 1;
+  }
+  return n > 0 ? n : 1;
 }
 
 cudaError_t FM_CAT(configure_m, FM_MAXM)(int bytes) {

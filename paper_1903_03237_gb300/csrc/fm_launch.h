@@ -30,13 +30,16 @@ struct LaunchArgs {
   int n_pt_blocks = 0;    // k_xt_ll
   int apply_phi = 0;      // k_xt_ll
   int do_mu = 0;          // k_xt_ll
-  int prep_mode = 0;      // k_prep_q: 0 log-det/copy, 1 inverse
   float2* out = nullptr;  // k_separate
 };
 
 cudaError_t launch_m2(KernelKind k, const LaunchArgs& a);
 cudaError_t launch_m4(KernelKind k, const LaunchArgs& a);
 cudaError_t launch_m8(KernelKind k, const LaunchArgs& a);
+// Resident CTAs per SM of a kernel class at a dynamic shared-memory size.
+int occupancy_m2(KernelKind k, size_t smem);
+int occupancy_m4(KernelKind k, size_t smem);
+int occupancy_m8(KernelKind k, size_t smem);
 // Raises the dynamic shared-memory limit of every kernel of the bucket to `bytes`.
 cudaError_t configure_m2(int bytes);
 cudaError_t configure_m4(int bytes);
