@@ -170,6 +170,30 @@ const char* fmnmf_kernel_name(int i);
 /* Number of kernel launches this context has enqueued since creation. */
 long long fmnmf_launch_count(const fmnmf_ctx* ctx);
 
+/*
+ * Log-likelihood of Eq. 17 (constant included, as fmnmf_loglik) for a state held in the
+ * caller's own device buffers, computed without allocating any memory.  The paper has no
+ * counterpart to this call: it is for callers that cannot call cudaMalloc - a real-time
+ * audio thread that must not block (cudaMalloc may wait on the device for an unbounded
+ * time), or an application whose device memory is owned entirely by its own pool
+ * allocator.
+ *  X, W, H, G, Q  device pointers, layouts as above (X, Q complex64; W, H, G float32).
+ *  ll             device pointer to one double, written when the work completes.
+ *  stream         cudaStream_t the work is enqueued on (NULL = legacy default stream);
+ *                 the call is asynchronous.
+ * The working memory is one static device array of 1 MiB that the library holds on every
+ * device it is loaded on, until the process exits: the call rejects F > 16384 bins or
+ * F*T > 117,407,744 TF bins with FMNMF_EINVAL (message via fmnmf_last_error(NULL)).  Every
+ * call shares that array and it keeps the last call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU race: order them on one stream or with
+ * events.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture begins on the device.
+ */
+fmnmf_status fmnmf_loglik_noalloc(const void* X, const float* W, const float* H, const float* G,
+                                  const void* Q, int F, int T, int M, int N, int K, double* ll,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

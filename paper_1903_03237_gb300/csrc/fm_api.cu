@@ -436,6 +436,10 @@ void free_ctx(fmnmf_ctx* ctx) {
 
 }  // namespace
 
+namespace fm {
+void set_thread_error(const char* msg) { g_thread_err = msg; }
+}  // namespace fm
+
 // =====================================================================================
 // C ABI
 // =====================================================================================

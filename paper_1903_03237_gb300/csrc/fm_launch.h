@@ -45,4 +45,7 @@ cudaError_t configure_m2(int bytes);
 cudaError_t configure_m4(int bytes);
 cudaError_t configure_m8(int bytes);
 
+// Sets the calling thread's message returned by fmnmf_last_error(NULL).
+void set_thread_error(const char* msg);
+
 }  // namespace fm

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
 EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "fmnmf_iterate", "fmnmf_sync",
            "fmnmf_loglik", "fmnmf_separate", "fmnmf_get_state", "fmnmf_set_state", "fmnmf_shape",
            "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
-           "fmnmf_kernel_name", "fmnmf_launch_count"]
+           "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc"]
 
 
 class Opts(ctypes.Structure):
@@ -61,6 +61,7 @@ _sig = {
     "fmnmf_kernel_times": (_S, [_P, _P, _P, ctypes.POINTER(_I)]),
     "fmnmf_kernel_name": (ctypes.c_char_p, [_I]),
     "fmnmf_launch_count": (ctypes.c_longlong, [_P]),
+    "fmnmf_loglik_noalloc": (_S, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
