@@ -193,7 +193,7 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   ctx->gS = make_geom(F, T, sep_cap, sms * occupancy(mx, KK_SEP, sep_smem_bytes(N, K, M, mx, sep_cap)));
   ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC);
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
-  ctx->n_mu_blocks = (N * K + (kThreads / 32) - 1) / (kThreads / 32);
+  ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
   return FMNMF_OK;
 }
 
@@ -461,7 +461,7 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
   *out = nullptr;
   if (F < 1 || T < 1 || M < 1 || M > kMaxM || N < 1 || K < 1)
     return set_err(nullptr, FMNMF_EINVAL, "bad shape F=%d T=%d M=%d N=%d K=%d (need F,T,N,K >= 1, 1 <= M <= 8)", F, T, M, N, K);
-  if ((double)F * T * M > 2.0e9) return set_err(nullptr, FMNMF_EINVAL, "F*T*M too large");
+  if ((double)F * T * M > 2.0e9) return set_err(nullptr, FMNMF_EINVAL, "F*T*M too large (> 2e9)");
   if (!X) return set_err(nullptr, FMNMF_EINVAL, "X is NULL");
   if (opts && opts->precision != FMNMF_PREC_FP32)
     return set_err(nullptr, FMNMF_EINVAL, "precision %d not available in this build", opts->precision);

@@ -32,26 +32,65 @@ __device__ __forceinline__ float dot4acc(float4 a, float4 b, float c) {
 __device__ __forceinline__ bool finitef(float v) { return isfinite(v); }
 
 // Shared-memory carve-up of k_tile (in floats; every region a multiple of 4 floats).
+// "o" is the own index within the tile (kOT), "i" the inner index within the sub-chunk
+// (IC, rows padded to ICP = IC + 4 so that 16-byte rows fall on different banks).
 struct TileSmem {
-  int own, oth, g, a, b, acc, total;
+  int own, oth, gw, gi, xs, ys, xc, a, b, acc, total;
 };
+__host__ __device__ inline int r4(int x) { return (x + 3) & ~3; }
 __host__ __device__ inline TileSmem tile_smem(int mode, int N, int K, int M, int MAXM, int IC) {
   const int ICP = IC + 4, NK = N * K;
+  const bool f_own = (mode != MODE_H);
   TileSmem s;
-  s.own = 0;
-  s.oth = s.own + NK * kOT;
-  s.g = s.oth + NK * ICP;
-  int gsz = (mode == MODE_H) ? N * IC * M : N * kOT * M;
-  gsz = (gsz + 3) & ~3;
-  s.a = s.g + gsz;
-  int asz = 0, bsz = 0, accsz = 0;
-  if (mode == MODE_W || mode == MODE_H) { asz = 2 * N * kOT * ICP; accsz = 2 * NK * kOT; }
-  if (mode == MODE_G) { asz = N * kOT * ICP; bsz = 2 * kOT * M * ICP; accsz = 2 * N * kOT * M; }
-  if (mode == MODE_Y) { asz = 0; bsz = kOT * M * ICP; accsz = kOT * M * MAXM * MAXM; }
-  s.b = s.a + asz;
-  s.acc = s.b + bsz;
-  s.total = s.acc + ((accsz + 3) & ~3);
+  int o = 0;
+  s.own = o; o += (mode != MODE_W) ? NK * kOT : 0;           // own factor tile [NK][kOT]
+  s.oth = o; o += NK * ICP;                                   // other factor chunk [NK][ICP]
+  s.gw = o;  o += f_own ? r4(N * kOT * M) : 0;                // g~ of the own bins [N][kOT][M]
+  s.gi = o;  o += (mode == MODE_H) ? N * M * ICP : 0;         // g~ of the chunk bins [N][M][ICP]
+  s.xs = o;  o += (mode != MODE_Y) ? kOT * M * ICP : 0;       // x~ [kOT][M][ICP]
+  s.ys = o;  o += (mode == MODE_W) ? kOT * M * ICP : 0;       // y~ [kOT][M][ICP]
+  s.xc = o;  o += (mode == MODE_Y) ? r4(kOT * IC * M * 2) : 0;  // X [kOT][IC][M] complex
+  s.a = o;
+  if (mode == MODE_W || mode == MODE_H) o += 2 * N * kOT * ICP;  // P, R [2][N][kOT][ICP]
+  if (mode == MODE_G) o += N * kOT * ICP;                        // lambda [N][kOT][ICP]
+  s.b = o;
+  if (mode == MODE_G) o += 2 * kOT * M * ICP;                    // A, B [2][kOT][M][ICP]
+  if (mode == MODE_Y) o += kOT * M * ICP;                        // 1/y~ [kOT][M][ICP]
+  s.acc = o;
+  int accsz = (mode == MODE_W || mode == MODE_H) ? 2 * NK * kOT
+            : (mode == MODE_G) ? 2 * N * kOT * M : kOT * M * MAXM * MAXM;
+  o += r4(accsz);
+  s.total = o;
   return s;
+}
+
+// 4- and 8-byte asynchronous global->shared copies (cp.async, L1-allocating); a copy with
+// valid == false writes zeros and reads nothing.
+__device__ __forceinline__ void cpa4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cpa8(float2* dst, const float2* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Sum of S split partials at p + ss*stride (ss = 0..S-1), in that order; loads issued
+// eight at a time (predicated) so that their latencies overlap.
+__device__ __forceinline__ float sum_splits(const float* p, size_t stride, int S) {
+  float acc = 0.f;
+  for (int ss = 0; ss < S; ss += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (ss + u < S) ? __ldcg(p + (size_t)(ss + u) * stride) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  return acc;
 }
 
 // Partial-sum floats per split for each mode.
@@ -62,6 +101,12 @@ __host__ __device__ inline size_t tile_part_floats(int mode, int F, int T, int M
     case MODE_G: return (size_t)2 * N * F * M;
     default: return (size_t)F * M * MAXM * MAXM;
   }
+}
+
+// 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cpa16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
 // ---------------------------------------------------------------------------------
@@ -207,14 +252,18 @@ __device__ bool warp_ip_bin(int M, const double* vs, double2* Q, double2* A, dou
 }
 
 // ---------------------------------------------------------------------------------
-// The tiled sweep.  grid = (n_own_tiles, S), block = 256, dynamic smem = tile_smem(...)
-// (or the IP scratch for MODE_Y, whichever is larger).
+// The tiled sweep.  grid = (n_own_tiles, S), block = 256, dynamic smem = tile_smem(...).
+// Per sub-chunk of the inner index: every operand the chunk needs is staged with
+// cp.async (all copies in flight at once), then
+//   phase 1: per point (2 own x 4 inner per item): lambda (unless MODE_W reads y~), y~,
+//            and the ratios the mode needs;
+//   phase 2: the contraction over the inner index into per-CTA accumulators.
 // ---------------------------------------------------------------------------------
 template <int MAXM, int MODE>
 __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, unsigned ctr_base) {
   extern __shared__ __align__(16) float sm[];
   constexpr bool F_OWN = (MODE != MODE_H);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = p.N, K = p.K, M = p.M, NK = N * K, F = p.F, T = p.T;
   const int SO = F_OWN ? F : T;
   const int SI = F_OWN ? T : F;
@@ -225,52 +274,105 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
   const int i_end = min(SI, i_begin + g.span);
   const int IC = g.IC, ICP = g.ICP;
   const TileSmem L = tile_smem(MODE, N, K, M, MAXM, IC);
-  float* own_s = sm + L.own;   // [NK][kOT]
-  float* oth_s = sm + L.oth;   // [NK][ICP]
-  float* g_s = sm + L.g;       // F_OWN: [N][kOT][M]   else [N][IC][M]
+  float* own_s = sm + L.own;
+  float* oth_s = sm + L.oth;
+  float* gw_s = sm + L.gw;
+  float* gi_s = sm + L.gi;
+  float* xs_s = sm + L.xs;
+  float* ys_s = sm + L.ys;
+  float2* xc_s = reinterpret_cast<float2*>(sm + L.xc);
   float* a_s = sm + L.a;
   float* b_s = sm + L.b;
   float* acc_s = sm + L.acc;
 
-  // factors: own = the factor indexed by the own index, oth = by the inner index
   const float* ownF = F_OWN ? p.W : p.H;
   const float* othF = F_OWN ? p.H : p.W;
 
-  for (int e = tid; e < NK * kOT; e += kThreads) {
-    int nk = e / kOT, o = e % kOT;
-    own_s[e] = (o < n_own) ? ownF[(size_t)nk * SO + o_base + o] : 0.f;
-  }
-  if (F_OWN) {
-    for (int e = tid; e < N * kOT * M; e += kThreads) {
-      int n = e / (kOT * M), o = (e / M) % kOT, m = e % M;
-      g_s[e] = (o < n_own) ? p.G[((size_t)n * F + o_base + o) * M + m] : 0.f;
+  // once per CTA: own factor tile, g~ of the own bins, zeroed accumulators
+  if (MODE != MODE_W)
+    for (int e = tid; e < NK * kOT; e += kThreads) {
+      const int nk = e / kOT, o = e % kOT;
+      cpa4(own_s + e, ownF + (size_t)nk * SO + o_base + min(o, n_own - 1), o < n_own);
     }
-  }
+  if (F_OWN)
+    for (int e = tid; e < N * kOT * M; e += kThreads) {
+      const int n = e / (kOT * M), r = e % (kOT * M), o = r / M;
+      cpa4(gw_s + e, p.G + ((size_t)n * F + o_base + min(o, n_own - 1)) * M + r % M, o < n_own);
+    }
   {
-    int accsz = (MODE == MODE_W || MODE == MODE_H) ? 2 * NK * kOT
-              : (MODE == MODE_G) ? 2 * N * kOT * M : kOT * M * MAXM * MAXM;
+    const int accsz = (MODE == MODE_W || MODE == MODE_H) ? 2 * NK * kOT
+                    : (MODE == MODE_G) ? 2 * N * kOT * M : kOT * M * MAXM * MAXM;
     for (int e = tid; e < accsz; e += kThreads) acc_s[e] = 0.f;
   }
 
-  // MODE_G without FLAG_UPDATE only normalises (launched with S = 1): no sweep.
-  const bool sweep = !(MODE == MODE_G && !(flags & FLAG_UPDATE));
-  for (int i0 = i_begin; sweep && i0 < i_end; i0 += IC) {
+  const bool do_v = (MODE == MODE_Y) && (flags & FLAG_DO_V);
+  for (int i0 = i_begin; i0 < i_end; i0 += IC) {
     const int icn = min(IC, i_end - i0);
     __syncthreads();  // previous sub-chunk fully consumed
-    // stage the other factor: one warp per row, lanes along the contiguous index
-    for (int row = tid >> 5; row < NK; row += kThreads / 32) {
-      const float* src = othF + (size_t)row * SI + i0;
-      float* dst = oth_s + row * ICP;
-      for (int i = tid & 31; i < IC; i += 32) dst[i] = (i < icn) ? src[i] : 0.f;
-    }
-    if (!F_OWN) {
-      // g~[n][i0 .. i0+icn)[0..M) is contiguous for each n
-      const int len = IC * M, valid = icn * M;
-      for (int n = 0; n < N; ++n) {
-        const float* src = p.G + ((size_t)n * F + i0) * M;
-        for (int j = tid; j < len; j += kThreads) g_s[n * len + j] = (j < valid) ? src[j] : 0.f;
+    // ---- stage the chunk (asynchronous copies, zero-filled past its end) ----
+    if ((SI & 3) == 0 && (icn & 3) == 0) {
+      // rows 16-byte aligned (SI, i0, IC multiples of 4): one 16-byte copy per 4 floats
+      const int q = IC >> 2, qn = icn >> 2;
+      for (int row = warp; row < NK; row += kThreads / 32) {
+        const float* src = othF + (size_t)row * SI + i0;
+        float* dst = oth_s + row * ICP;
+        for (int j = lane; j < q; j += 32) {
+          if (j < qn) cpa16(dst + 4 * j, src + 4 * j);
+          else st4(dst + 4 * j, make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+      }
+    } else {
+      for (int row = warp; row < NK; row += kThreads / 32) {
+        const float* src = othF + (size_t)row * SI + i0;
+        for (int i = lane; i < IC; i += 32) cpa4(oth_s + row * ICP + i, src + min(i, icn - 1), i < icn);
       }
     }
+    if (MODE == MODE_W || MODE == MODE_G) {
+      // x~ (and y~) of the own bins over the chunk frames, as [o][m][i]: one warp per
+      // (o, m) row, lanes along the frames
+      for (int row = warp; row < kOT * M; row += kThreads / 32) {
+        const int o = row / M, m = row - o * M;
+        const bool vo = o < n_own;
+        const size_t base = ((size_t)(o_base + min(o, n_own - 1)) * T + i0) * M + m;
+        float* dx = xs_s + row * ICP;
+        float* dy = ys_s + row * ICP;
+        for (int i = lane; i < IC; i += 32) {
+          const bool v = vo && (i < icn);
+          const size_t src = base + (size_t)min(i, icn - 1) * M;
+          cpa4(dx + i, p.xt + src, v);
+          if (MODE == MODE_W) cpa4(dy + i, p.yt + src, v);
+        }
+      }
+    }
+    if (MODE == MODE_H) {
+      // x~ of the chunk bins over the own frames as [o][m][i]: for one bin the kOT*M values
+      // of the own frames are contiguous; lanes along them, warps along the bins
+      const int rowlen = kOT * M;
+      for (int i = warp; i < IC; i += kThreads / 32) {
+        const bool vi = i < icn;
+        const size_t base = ((size_t)(i0 + min(i, icn - 1)) * T + o_base) * M;
+        const int lim = n_own * M;
+        for (int j = lane; j < rowlen; j += 32) cpa4(xs_s + j * ICP + i, p.xt + base + min(j, lim - 1), vi && j < lim);
+      }
+      // g~ of the chunk bins as [n][m][i]
+      for (int row = warp; row < N * M; row += kThreads / 32) {
+        const int n = row / M, m = row - n * M;
+        const float* src = p.G + ((size_t)n * F + i0) * M + m;
+        float* dst = gi_s + row * ICP;
+        for (int i = lane; i < IC; i += 32) cpa4(dst + i, src + (size_t)min(i, icn - 1) * M, i < icn);
+      }
+    }
+    if (do_v) {
+      // X of the own bins over the chunk frames, [o][i][m] (the global layout): one warp per bin
+      const int len = IC * M, lim = icn * M;
+      for (int o = warp; o < kOT; o += kThreads / 32) {
+        const bool vo = o < n_own;
+        const float2* src = p.X + ((size_t)(o_base + min(o, n_own - 1)) * T + i0) * M;
+        float2* dst = xc_s + o * len;
+        for (int j = lane; j < len; j += 32) cpa8(dst + j, src + min(j, lim - 1), vo && j < lim);
+      }
+    }
+    cpa_wait_all();
     __syncthreads();
 
     // ---------------- phase 1: per point quantities (2 own x 4 inner per item) -------
@@ -279,16 +381,13 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
       const int o0 = (it / nq) * 2;
       const int ii = (it % nq) * 4;
       float y[2][4][MAXM];
-      // model power y~ (read for MODE_W, formed from lambda otherwise)
       if (MODE == MODE_W) {
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const bool v = (o0 + a < n_own) && (ii + b < icn);
-            const size_t pt = (size_t)(o_base + o0 + a) * T + (i0 + ii + b);
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) y[a][b][m] = (v && m < M) ? p.yt[pt * M + m] : 1.f;
+          for (int m = 0; m < MAXM; ++m) {
+            const float4 v = (m < M) ? ld4(ys_s + ((o0 + a) * M + m) * ICP + ii) : make_float4(1.f, 1.f, 1.f, 1.f);
+            y[a][0][m] = v.x; y[a][1][m] = v.y; y[a][2][m] = v.z; y[a][3][m] = v.w;
           }
       } else {
 #pragma unroll
@@ -303,10 +402,12 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
           for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) lam[a][b] = 0.f;
+          const float* ow = own_s + n * K * kOT + o0;
+          const float* oh = oth_s + n * K * ICP + ii;
+#pragma unroll 4
           for (int k = 0; k < K; ++k) {
-            const int nk = n * K + k;
-            const float2 w = *reinterpret_cast<const float2*>(own_s + nk * kOT + o0);
-            const float4 h = ld4(oth_s + nk * ICP + ii);
+            const float2 w = *reinterpret_cast<const float2*>(ow + k * kOT);
+            const float4 h = ld4(oh + k * ICP);
             lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);
             lam[0][2] = fmaf(w.x, h.z, lam[0][2]); lam[0][3] = fmaf(w.x, h.w, lam[0][3]);
             lam[1][0] = fmaf(w.y, h.x, lam[1][0]); lam[1][1] = fmaf(w.y, h.y, lam[1][1]);
@@ -317,21 +418,30 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
             st4(a_s + (n * kOT + o0 + 1) * ICP + ii, make_float4(lam[1][0], lam[1][1], lam[1][2], lam[1][3]));
           }
 #pragma unroll
-          for (int a = 0; a < 2; ++a)
+          for (int m = 0; m < MAXM; ++m) {
+            if (m < M) {
+              if (F_OWN) {
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
+                for (int a = 0; a < 2; ++a) {
+                  const float gv = gw_s[(n * kOT + o0 + a) * M + m];
 #pragma unroll
-              for (int m = 0; m < MAXM; ++m) {
-                if (m < M) {
-                  const float gv = F_OWN ? g_s[(n * kOT + o0 + a) * M + m] : g_s[(n * IC + ii + b) * M + m];
-                  y[a][b][m] = fmaf(lam[a][b], gv, y[a][b][m]);
+                  for (int b = 0; b < 4; ++b) y[a][b][m] = fmaf(lam[a][b], gv, y[a][b][m]);
                 }
+              } else {
+                const float4 gv = ld4(gi_s + (n * M + m) * ICP + ii);
+                const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                  for (int b = 0; b < 4; ++b) y[a][b][m] = fmaf(lam[a][b], gg[b], y[a][b][m]);
               }
+            }
+          }
         }
       }
 
       if (MODE == MODE_Y) {
-        // write y~ (pre-normalisation) and 1/y~
+        // write y~ (before the phi normalisation) and 1/y~
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           float binv[4][MAXM];
@@ -348,32 +458,27 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
               }
             }
           }
-          if (flags & FLAG_DO_V) {
+          if (do_v) {
 #pragma unroll
             for (int m = 0; m < MAXM; ++m)
               if (m < M) st4(b_s + ((o0 + a) * M + m) * ICP + ii, make_float4(binv[0][m], binv[1][m], binv[2][m], binv[3][m]));
           }
         }
       } else {
-        // A = x~ / y~^2, B = 1 / y~
+        // A = x~ / y~^2, B = 1 / y~ (zero outside the chunk / tile)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           float A[4][MAXM], B[4][MAXM];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const bool v = (o0 + a < n_own) && (ii + b < icn);
-            const int f = F_OWN ? (o_base + o0 + a) : (i0 + ii + b);
-            const int t = F_OWN ? (i0 + ii + b) : (o_base + o0 + a);
-            const size_t pt = (size_t)f * T + t;
+          for (int m = 0; m < MAXM; ++m) {
+            const float4 xv = (m < M) ? ld4(xs_s + ((o0 + a) * M + m) * ICP + ii) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float xx[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              A[b][m] = 0.f; B[b][m] = 0.f;
-              if (v && m < M) {
-                const float bi = __fdividef(1.f, y[a][b][m]);
-                const float x = p.xt[pt * M + m];
-                B[b][m] = bi;
-                A[b][m] = x * bi * bi;
-              }
+            for (int b = 0; b < 4; ++b) {
+              const bool v = (o0 + a < n_own) && (ii + b < icn) && (m < M);
+              const float bi = v ? __fdividef(1.f, y[a][b][m]) : 0.f;
+              B[b][m] = bi;
+              A[b][m] = xx[b] * bi * bi;
             }
           }
           if (MODE == MODE_G) {
@@ -386,19 +491,21 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
           } else {
             // P_n = sum_m g~ A,  R_n = sum_m g~ B
             for (int n = 0; n < N; ++n) {
-              float P4[4], R4[4];
+              float P4[4] = {0.f, 0.f, 0.f, 0.f}, R4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                float pa = 0.f, ra = 0.f;
+              for (int m = 0; m < MAXM; ++m)
+                if (m < M) {
+                  if (F_OWN) {
+                    const float gv = gw_s[(n * kOT + o0 + a) * M + m];
 #pragma unroll
-                for (int m = 0; m < MAXM; ++m)
-                  if (m < M) {
-                    const float gv = F_OWN ? g_s[(n * kOT + o0 + a) * M + m] : g_s[(n * IC + ii + b) * M + m];
-                    pa = fmaf(gv, A[b][m], pa);
-                    ra = fmaf(gv, B[b][m], ra);
+                    for (int b = 0; b < 4; ++b) { P4[b] = fmaf(gv, A[b][m], P4[b]); R4[b] = fmaf(gv, B[b][m], R4[b]); }
+                  } else {
+                    const float4 gv = ld4(gi_s + (n * M + m) * ICP + ii);
+                    const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) { P4[b] = fmaf(gg[b], A[b][m], P4[b]); R4[b] = fmaf(gg[b], B[b][m], R4[b]); }
                   }
-                P4[b] = pa; R4[b] = ra;
-              }
+                }
               st4(a_s + ((0 * N + n) * kOT + o0 + a) * ICP + ii, make_float4(P4[0], P4[1], P4[2], P4[3]));
               st4(a_s + ((1 * N + n) * kOT + o0 + a) * ICP + ii, make_float4(R4[0], R4[1], R4[2], R4[3]));
             }
@@ -427,6 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
         const float* h0 = oth_s + (n * K + k0) * ICP;
         const float* h1 = oth_s + (n * K + k1) * ICP;
         float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
         for (int i = 0; i < icn4; i += 4) {
           const float4 p0 = ld4(P0 + i), p1 = ld4(P1 + i), r0 = ld4(R0 + i), r1 = ld4(R1 + i);
           const float4 x0 = ld4(h0 + i), x1 = ld4(h1 + i);
@@ -456,74 +564,54 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
         acc_s[((0 * N + n) * kOT + o) * M + m] += cn;
         acc_s[((1 * N + n) * kOT + o) * M + m] += cd;
       }
-    } else if (flags & FLAG_DO_V) {
-      // V_fm partial sums: warp w <-> own element o = w; lanes split (m-group, t-subset)
-      constexpr int MPG = (MAXM <= 4) ? MAXM : 2;
+    } else if (do_v) {
+      // V_fm partial sums: warp w <-> own bin o = w; lane = (m, t-subset), IS = 32 / MP
+      // lanes per channel (MP = MAXM rounded to a power of two), MAXM^2 accumulators each
       constexpr int MM = MAXM * MAXM;
-      const int warp = tid >> 5, lane = tid & 31;
+      constexpr int IS = 32 / MAXM;
       const int o = warp;
-      const int ngrp = (M + MPG - 1) / MPG;
-      const int IS = (ngrp == 1) ? 32 : (ngrp == 2 ? 16 : 8);
-      const int grp = lane / IS, isub = lane % IS;
-      float acc[MPG][MM];
+      const int m = lane / IS, isub = lane % IS;
+      float acc[MM];
 #pragma unroll
-      for (int mm = 0; mm < MPG; ++mm)
-#pragma unroll
-        for (int q = 0; q < MM; ++q) acc[mm][q] = 0.f;
-      if (o < n_own && grp < ngrp) {
-        const int f = o_base + o;
+      for (int q = 0; q < MM; ++q) acc[q] = 0.f;
+      if (o < n_own && m < M) {
+        const float* bp = b_s + (o * M + m) * ICP;
         for (int i = isub; i < icn; i += IS) {
-          const float2* xp = p.X + ((size_t)f * T + i0 + i) * M;
+          const float2* xp = xc_s + (o * IC + i) * M;
           float2 x[MAXM];
 #pragma unroll
           for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? xp[j] : make_float2(0.f, 0.f);
-          float pr[MM];
+          const float bv = bp[i];
 #pragma unroll
           for (int a = 0; a < MAXM; ++a)
 #pragma unroll
-            for (int b = 0; b < MAXM; ++b) {
-              if (a <= b) pr[a * MAXM + b] = x[a].x * x[b].x + x[a].y * x[b].y;        // Re(x_a conj x_b)
-              else        pr[a * MAXM + b] = x[b].y * x[a].x - x[b].x * x[a].y;        // Im(x_b conj x_a)
+            for (int c = 0; c < MAXM; ++c) {
+              const float pr = (a <= c) ? (x[a].x * x[c].x + x[a].y * x[c].y)     // Re(x_a conj x_c)
+                                        : (x[c].y * x[a].x - x[c].x * x[a].y);    // Im(x_c conj x_a)
+              acc[a * MAXM + c] = fmaf(bv, pr, acc[a * MAXM + c]);
             }
-#pragma unroll
-          for (int mm = 0; mm < MPG; ++mm) {
-            const int m = grp * MPG + mm;
-            const float bv = (m < M) ? b_s[(o * M + m) * ICP + i] : 0.f;
-#pragma unroll
-            for (int q = 0; q < MM; ++q) acc[mm][q] = fmaf(bv, pr[q], acc[mm][q]);
-          }
         }
       }
 #pragma unroll
-      for (int mm = 0; mm < MPG; ++mm)
+      for (int q = 0; q < MM; ++q) {
+        float v = acc[q];
 #pragma unroll
-        for (int q = 0; q < MM; ++q) {
-          float v = acc[mm][q];
-          for (int off = IS >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-          acc[mm][q] = v;
-        }
-      if (o < n_own && grp < ngrp && isub == 0) {
+        for (int off = IS >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        acc[q] = v;
+      }
+      if (o < n_own && m < M && isub == 0) {
 #pragma unroll
-        for (int mm = 0; mm < MPG; ++mm) {
-          const int m = grp * MPG + mm;
-          if (m < M) {
-#pragma unroll
-            for (int q = 0; q < MM; ++q) acc_s[(o * M + m) * MM + q] += acc[mm][q];
-          }
-        }
+        for (int q = 0; q < MM; ++q) acc_s[(o * M + m) * MM + q] += acc[q];
       }
     }
   }
   __syncthreads();
 
   // ---------------- write this split's partial sums ---------------------------------
-  const bool has_parts = sweep && (MODE != MODE_Y || (flags & FLAG_DO_V));
-  if (!has_parts) return;
+  if (MODE == MODE_Y && !do_v) return;
   const size_t psz = tile_part_floats(MODE, F, T, M, N, K, MAXM);
   float* part = p.part + (size_t)s * psz;
-  if (!has_parts) {
-    // nothing to write
-  } else if (MODE == MODE_W || MODE == MODE_H) {
+  if (MODE == MODE_W || MODE == MODE_H) {
     for (int e = tid; e < 2 * NK * kOT; e += kThreads) {
       const int o = e % kOT, r = e / kOT;  // r = pr*NK + nk
       if (o < n_own) part[(size_t)r * SO + o_base + o] = acc_s[e];
@@ -539,40 +627,46 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
       const int o = e / (M * MM);
       if (o < n_own) part[(size_t)(o_base)*M * MM + e] = acc_s[e];
     }
+    return;  // k_ip reduces the V_fm splits
   }
-  if (MODE == MODE_Y) return;  // k_ip reduces the V_fm splits
   // Every split must have finished reading the state before the last one rewrites it.
-  if (sweep && !arrive_last(p.counters + ctr_base + ot, g.S)) return;
+  if (!arrive_last(p.counters + ctr_base + ot, g.S)) return;
 
   // ---------------- last CTA of this own tile: reduce splits, apply the update -------
   if (MODE == MODE_W || MODE == MODE_H) {
-    float* fac = F_OWN ? p.W : p.H;
-    for (int e = tid; e < NK * kOT; e += kThreads) {
-      const int nk = e / kOT, o = e % kOT;
-      if (o >= n_own) continue;
-      float num = 0.f, den = 0.f;
-      for (int ss = 0; ss < g.S; ++ss) {
-        const float* pp = p.part + (size_t)ss * psz;
-        num += __ldcg(pp + (size_t)nk * SO + o_base + o);
-        den += __ldcg(pp + (size_t)(NK + nk) * SO + o_base + o);
+    float* __restrict__ fac = F_OWN ? p.W : p.H;
+    const float* __restrict__ pp = p.part;
+    for (int e0 = 0; e0 < NK * kOT; e0 += 4 * kThreads) {
+      float ratio[4], old[4];
+      size_t idx[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * kThreads + tid;
+        const int nk = e / kOT, o = e % kOT;
+        ok[u] = (e < NK * kOT) && (o < n_own);
+        idx[u] = ok[u] ? (size_t)nk * SO + o_base + o : 0;
+        const float num = ok[u] ? sum_splits(pp + idx[u], psz, g.S) : 1.f;
+        const float den = ok[u] ? sum_splits(pp + (size_t)NK * SO + idx[u], psz, g.S) : 1.f;
+        ratio[u] = num / den;
+        old[u] = ok[u] ? fac[idx[u]] : 0.f;
       }
-      const size_t idx = (size_t)nk * SO + o_base + o;
-      const float v = fac[idx] * sqrtf(num / den);
-      if (!finitef(v)) flag(p.status, ST_NONFINITE);
-      fac[idx] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ok[u]) {
+          const float v = old[u] * sqrtf(ratio[u]);
+          if (!finitef(v)) flag(p.status, ST_NONFINITE);
+          fac[idx[u]] = v;
+        }
     }
-  } else if (MODE == MODE_G) {
+  } else {
     // g~ <- g~ sqrt(num/den)
-    for (int e = tid; (flags & FLAG_UPDATE) && e < N * kOT * M; e += kThreads) {
+    for (int e = tid; e < N * kOT * M; e += kThreads) {
       const int m = e % M, o = (e / M) % kOT, n = e / (M * kOT);
       if (o >= n_own) continue;
-      float num = 0.f, den = 0.f;
-      for (int ss = 0; ss < g.S; ++ss) {
-        const float* pp = p.part + (size_t)ss * psz;
-        num += __ldcg(pp + ((size_t)n * F + o_base + o) * M + m);
-        den += __ldcg(pp + ((size_t)(N + n) * F + o_base + o) * M + m);
-      }
       const size_t idx = ((size_t)n * F + o_base + o) * M + m;
+      const float num = sum_splits(p.part + idx, psz, g.S);
+      const float den = sum_splits(p.part + (size_t)N * F * M + idx, psz, g.S);
       const float v = p.G[idx] * sqrtf(num / den);
       if (!finitef(v)) flag(p.status, ST_NONFINITE);
       p.G[idx] = v;
@@ -620,11 +714,8 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
   if (flags & FLAG_DO_V) {
     // packed split sums (float32, fixed order over the splits)
     const size_t psz = (size_t)F * M * MM;
-    for (int e = tid; e < M * MM; e += blockDim.x) {
-      float sum = 0.f;
-      for (int ss = 0; ss < S; ++ss) sum += __ldcg(p.part + (size_t)ss * psz + (size_t)f * M * MM + e);
-      vsum_s[e / MM][e % MM] = sum;
-    }
+    for (int e = tid; e < M * MM; e += blockDim.x)
+      vsum_s[e / MM][e % MM] = sum_splits(p.part + (size_t)f * M * MM + e, psz, S);
     __syncthreads();
     if (warp < M) {
       const int m = warp;
@@ -718,7 +809,9 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
     }
     __syncthreads();
   }
-  // phi normalisation, write-back (warp 0)
+  // phi normalisation and write-back
+  __shared__ double phi_s;
+  __shared__ float nu_s[64];
   if (warp == 0) {
     double phi = 1.0;
     df sq = df_make(1.f), isq = df_make(1.f);
@@ -740,24 +833,40 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
       p.Qf[(size_t)f * M * M + e] = make_float2(q.re.hi, q.im.hi);
       p.Qinv[(size_t)f * M * M + e] = make_float2(qi.re.hi, qi.im.hi);
     }
-    if (flags & FLAG_NORMALISE) {
-      // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
-      const float fphi = (float)phi;
-      for (int n = lane; n < N; n += 32) {
-        float* gp = p.G + ((size_t)n * F + f) * M;
-        float nu = 0.f;
-        for (int m = 0; m < M; ++m) { const float gv = gp[m] / fphi; gp[m] = gv; nu += gv; }
-        for (int m = 0; m < M; ++m) gp[m] /= nu;
-        for (int k = 0; k < K; ++k) p.W[((size_t)n * K + k) * F + f] *= nu;
-        if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
-      }
-    }
     if (lane == 0) {
+      phi_s = phi;
       const double ld = ld_s - (double)M * log(phi);
       p.logdet[f] = ld;
       p.phi[f] = (float)phi;
       if (bad_s) flag(p.status, ST_SINGULAR);
       if (!isfinite(ld)) flag(p.status, ST_NONFINITE);
+    }
+  }
+  if (flags & FLAG_NORMALISE) {
+    // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
+    __syncthreads();
+    const float fphi = (float)phi_s;
+    for (int n0 = 0; n0 < N; n0 += 64) {
+      const int nn = min(64, N - n0);
+      if (tid < nn) {
+        float* gp = p.G + ((size_t)(n0 + tid) * F + f) * M;
+        float gv[MAXM];
+        float nu = 0.f;
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) { gv[m] = gp[m] / fphi; nu += gv[m]; }
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) gp[m] = gv[m] / nu;
+        nu_s[tid] = nu;
+        if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
+      }
+      __syncthreads();
+      for (int e = tid; e < nn * K; e += blockDim.x) {
+        const int n = e / K, k = e - n * K;
+        p.W[((size_t)(n0 + n) * K + k) * F + f] *= nu_s[n];
+      }
+      __syncthreads();
     }
   }
 }
@@ -774,13 +883,13 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
   const int tid = threadIdx.x;
   const int M = p.M, T = p.T, F = p.F;
   if ((int)blockIdx.x < n_pt_blocks) {
-    const size_t npts = (size_t)F * T;
+    const unsigned npts = (unsigned)F * (unsigned)T;  // < 2^31 (checked at init)
     float part = 0.f;
     for (int r = 0; r < kPtsPerThread; ++r) {
-      const size_t pt = (size_t)blockIdx.x * (kThreads * kPtsPerThread) + (size_t)r * kThreads + tid;
+      const unsigned pt = blockIdx.x * (unsigned)(kThreads * kPtsPerThread) + (unsigned)(r * kThreads + tid);
       if (pt >= npts) break;
-      const int f = (int)(pt / T);
-      const float2* xp = p.X + pt * M;
+      const int f = (int)(pt / (unsigned)T);
+      const float2* xp = p.X + (size_t)pt * M;
       const float2* qp = p.Qf + (size_t)f * M * M;
       float2 x[MAXM];
 #pragma unroll
@@ -800,9 +909,9 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
             }
           }
           const float xv = re * re + im * im;
-          float yv = p.yt[pt * M + m];
-          if (apply_phi) { yv = yv / ph; p.yt[pt * M + m] = yv; }
-          p.xt[pt * M + m] = xv;
+          float yv = p.yt[(size_t)pt * M + m];
+          if (apply_phi) { yv = yv / ph; p.yt[(size_t)pt * M + m] = yv; }
+          p.xt[(size_t)pt * M + m] = xv;
           ls += -xv / yv - logf(yv);
         }
       }
@@ -839,20 +948,22 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
       if (!isfinite(ll)) flag(p.status, ST_NONFINITE);
     }
   } else if (do_mu) {
-    // mu_nk = sum_f w_nkf;  w_nk /= mu;  h_nk *= mu
-    const int NK = p.N * p.K;
-    const int wid = ((int)blockIdx.x - n_pt_blocks) * (kThreads / 32) + (tid >> 5);
-    const int lane = tid & 31;
-    if (wid >= NK) return;
-    float* w = p.W + (size_t)wid * F;
-    float* h = p.H + (size_t)wid * T;
-    float s = 0.f;
-    for (int f = lane; f < F; f += 32) s += w[f];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const float inv = 1.f / s;
-    for (int f = lane; f < F; f += 32) w[f] *= inv;
-    for (int t = lane; t < T; t += 32) h[t] *= s;
-    if (lane == 0 && !(s > 0.f && isfinite(s))) flag(p.status, ST_NONFINITE);
+    // mu_nk = sum_f w_nkf;  w_nk /= mu;  h_nk *= mu   (one CTA per (n, k) row)
+    const int nk = (int)blockIdx.x - n_pt_blocks;
+    float* __restrict__ w = p.W + (size_t)nk * F;
+    float* __restrict__ h = p.H + (size_t)nk * T;
+    float part = 0.f;
+    for (int f = tid; f < F; f += kThreads) part += w[f];
+    __shared__ float red[kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    float mu = 0.f;
+    for (int i = 0; i < kThreads / 32; ++i) mu += red[i];
+    const float inv = 1.f / mu;
+    for (int f = tid; f < F; f += kThreads) w[f] *= inv;
+    for (int t = tid; t < T; t += kThreads) h[t] *= mu;
+    if (tid == 0 && !(mu > 0.f && isfinite(mu))) flag(p.status, ST_NONFINITE);
   }
 }
 
