@@ -158,12 +158,14 @@ fmnmf_status fmnmf_destroy(fmnmf_ctx* ctx);
 const char* fmnmf_last_error(const fmnmf_ctx* ctx);
 
 /*
- * Kernel timing, for measurement only.  While enabled, every launch made by
- * fmnmf_iterate / fmnmf_separate is bracketed by CUDA events on the context stream.
- * fmnmf_kernel_times synchronises and returns, for each kernel class i < *n (names from
- * fmnmf_kernel_name), the summed milliseconds and launch count since the last reset.
+ * Kernel timing, for measurement only.  kinds is a bit mask of kernel classes (bit i =
+ * class i, named by fmnmf_kernel_name(i); -1 = all, 0 = off).  While it is non-zero, every
+ * launch of a selected class made by fmnmf_iterate / fmnmf_separate is bracketed by CUDA
+ * events on the context stream (inside the captured graphs as event-record nodes).
+ * fmnmf_kernel_times synchronises and returns, for each class i < *n, the summed
+ * milliseconds and launch count since the last call, then resets them.
  */
-fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int enable);
+fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int kinds);
 fmnmf_status fmnmf_kernel_times(fmnmf_ctx* ctx, double* ms, long long* launches, int* n);
 const char* fmnmf_kernel_name(int i);
 

@@ -58,9 +58,9 @@ struct fmnmf_ctx {
   float* H0 = nullptr;
   float* G0 = nullptr;
   float4* Q0 = nullptr;
-  std::map<std::pair<int, int>, GraphEntry> graphs;  // (chunk, timing) -> graph
+  std::map<std::pair<int, unsigned>, GraphEntry> graphs;  // (chunk, timing mask) -> graph
   std::string err;
-  bool timing = false;
+  unsigned timing = 0;  // bit i: bracket launches of kernel class i with events
   double ms[KK_COUNT] = {0};
   long long cnt[KK_COUNT] = {0};
   long long launches = 0;
@@ -275,7 +275,7 @@ struct Recorder {  // brackets launches with events when timing is on (works und
     return e;
   }
   cudaError_t run(KernelKind k, const LaunchArgs& a) {
-    if (!out) return launch(c, k, a);
+    if (!out || !((c->timing >> (int)k) & 1u)) return launch(c, k, a);
     cudaEvent_t e0 = take(), e1 = take();
     // under stream capture the records must be External to become event-record nodes
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -515,7 +515,7 @@ fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter) {
   if (n_iter < 0) return set_err(ctx, FMNMF_EINVAL, "n_iter < 0");
   while (n_iter > 0) {
     const int chunk = std::min(n_iter, kMaxChunk);
-    auto key = std::make_pair(chunk, ctx->timing ? 1 : 0);
+    auto key = std::make_pair(chunk, ctx->timing);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       GraphEntry ge;
@@ -650,9 +650,9 @@ fmnmf_status fmnmf_destroy(fmnmf_ctx* ctx) {
 
 const char* fmnmf_last_error(const fmnmf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_thread_err.c_str(); }
 
-fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int enable) {
+fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int kinds) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
-  ctx->timing = enable != 0;
+  ctx->timing = (unsigned)kinds & ((1u << KK_COUNT) - 1u);
   return FMNMF_OK;
 }
 

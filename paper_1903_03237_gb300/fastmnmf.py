@@ -199,8 +199,19 @@ class Context:
         _check(_lib.fmnmf_set_state(self._ctx, wp, hp, gp, qp), self._ctx)
 
     # -- measurement --------------------------------------------------------------------
-    def set_timing(self, enable: bool):
-        _check(_lib.fmnmf_set_timing(self._ctx, 1 if enable else 0), self._ctx)
+    def set_timing(self, kinds=True):
+        """True / False: time every kernel class or none; an int: bit mask of classes;
+        a list of names: those classes."""
+        if kinds is True:
+            mask = -1
+        elif kinds is False or kinds is None:
+            mask = 0
+        elif isinstance(kinds, int):
+            mask = kinds
+        else:
+            names = [_lib.fmnmf_kernel_name(i).decode() for i in range(16)]
+            mask = sum(1 << names.index(k) for k in kinds)
+        _check(_lib.fmnmf_set_timing(self._ctx, mask), self._ctx)
 
     def kernel_times(self) -> dict:
         """{kernel name: (total ms, launches)} since the last call (synchronises)."""
