@@ -31,12 +31,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FastMNMF TF-bin·iters/s vs plain FP32 on 1 GB300; serving p50/p99 latency"
 UNIT = "TF-bin·iters/s"
-WORKLOAD = dict(M=4, N=4, K=32, F=513, T=640, iters=100, diffuse=0.1)
+WORKLOADS = {
+    # paper-scale single mixture (the headline): 1024-point STFT at 16 kHz, ~10 s, 100 iterations
+    "c1": dict(M=4, N=4, K=32, F=513, T=640, iters=100, diffuse=0.1),
+    # large mixture (mixed-precision case): 2048-point STFT, ~65 s
+    "c2": dict(M=8, N=6, K=64, F=1025, T=4096, iters=10, diffuse=0.0),
+}
+WORKLOAD = WORKLOADS["c1"]
+PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock = 80.5 TFLOP/s
 
 
 def kernel_flops(kind: str, F, T, M, N, K) -> float:
-    """Algorithmic FLOPs of one launch of a kernel class (per TF bin x F*T)."""
+    """Algorithmic FLOPs of one launch of a plain-form kernel class (per TF bin x F*T)."""
     ft = F * T
     mm = M * M
     per_point = {
@@ -52,6 +59,36 @@ def kernel_flops(kind: str, F, T, M, N, K) -> float:
         "xt_loglik": 8 * mm + 7 * M,
     }
     return float(per_point.get(kind, 0)) * ft
+
+
+def kernel_bytes(kind: str, F, T, M, N, K) -> float:
+    """Algorithmic DRAM bytes of one launch of a mixed-form kernel class (operands read
+    once, results written once; float32 / complex64 storage)."""
+    ft = F * T
+    return float({
+        "gemm_lambda": 4 * N * ft + 4 * N * K * (F + T),         # lambda written, W and H read
+        "gemm_w": 8 * N * ft + 4 * N * K * T,                     # P, R and H read
+        "gemm_h": 8 * N * ft + 4 * N * K * F,                     # P, R and W read
+        "pr": 4 * ft * M + 2 * ft * M + 2 * N * ft + 8 * N * ft,  # x~, mean of (y~, lambda), P and R written
+        "g_update": 4 * N * ft + 4 * ft * M,                      # lambda and x~ read
+        "scm": 4 * N * ft + 8 * ft * M + 4 * ft * M,              # lambda, X read, y~ written
+        "xt_loglik": 20 * ft * M,                                 # X, y~ read; x~, y~ written
+    }.get(kind, 0))
+
+
+def roofline_for(dom, avg_ms, precision, F, T, M, N, K, workload):
+    peaks = read_peaks() or {}
+    if precision == "fp32" and kernel_flops(dom, F, T, M, N, K) > 0:
+        achieved = kernel_flops(dom, F, T, M, N, K) / (avg_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": read_traffic(dom, workload), "kernel": dom,
+                "avg_launch_us": avg_ms * 1e3,
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (max SM clock)"}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = kernel_bytes(dom, F, T, M, N, K) / (avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": read_traffic(dom, workload), "kernel": dom, "avg_launch_us": avg_ms * 1e3,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 
 
 def read_peaks():
@@ -181,12 +218,16 @@ def run_reference(args):
     }), flush=True)
 
 
-def _config():
+def _config(precision="fp32"):
     w = WORKLOAD
-    return {"workload": f"paper-scale single mixture M{w['M']} N{w['N']} K{w['K']} F{w['F']} T{w['T']}, "
+    prec = {"fp32": "plain FP32 (float-float IP solve)",
+            "bf16": "BF16 tensor-core contractions, FP32 accumulation (float-float IP solve)",
+            "tf32": "TF32 tensor-core contractions, FP32 accumulation (float-float IP solve)"}[precision]
+    name = "paper-scale single mixture" if WORKLOAD is WORKLOADS["c1"] else "large mixture"
+    return {"workload": f"{name} M{w['M']} N{w['N']} K{w['K']} F{w['F']} T{w['T']}, "
                         f"{w['iters']} iterations + Wiener separation per step",
             "M": w["M"], "N": w["N"], "K": w["K"], "F": w["F"], "T": w["T"], "iters_per_step": w["iters"],
-            "l2": "flushed between timed steps (512 MB write)", "precision": "plain FP32 (float64 IP solve)"}
+            "l2": "flushed between timed steps (512 MB write)", "precision": prec}
 
 
 def run_ours(args):
@@ -210,7 +251,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     Xd = torch.from_numpy(mix.X).cuda()
     torch.cuda.synchronize()
-    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream)
+    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream, precision=PRECISIONS[args.precision])
     out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
@@ -270,13 +311,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel, from its launches inside the timed region
     avg_ms = kt[dom][0] / kt[dom][1]
-    flops = kernel_flops(dom, F, T, M, N, K)
-    achieved = flops / (avg_ms / 1e3) / 1e12
-    traffic = read_traffic(dom, "c1")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
-                "avg_launch_us": avg_ms * 1e3, "launches_timed": kt[dom][1],
-                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (max SM clock)"}
+    roofline = roofline_for(dom, avg_ms, args.precision, F, T, M, N, K, args.workload)
+    roofline["launches_timed"] = kt[dom][1]
 
     # end to end through the C ABI with host buffers: H2D mixture, 100 iterations, D2H images
     ctx.set_timing(False)
@@ -302,17 +338,22 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        W0, H0, G0, Q0 = make_state(F, T, M, N, K, 0)
-        r, cores, secs = oracle_iteration_rate(mix, W0, H0, G0, Q0, 2)
+        # a bounded sample: all bins of c1 (2 iterations), the first 96 bins of larger mixtures
+        Fs = F if F * T <= 513 * 640 else 96
+        sub = type(mix)(X=mix.X[:Fs], W=None, H=None, G=None, Q=None, noisy_bins=None)
+        W0, H0, G0, Q0 = make_state(Fs, T, M, N, K, 0)
+        nit = 2 if Fs == F else 1
+        r, cores, secs = oracle_iteration_rate(sub, W0, H0, G0, Q0, nit)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"2 oracle iterations of the same {F}x{T} mixture ({secs:.1f} s)"}
+               "sample": f"{nit} oracle iteration(s) of {Fs} of the {F} bins x {T} frames of the same mixture ({secs:.1f} s)"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config() | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision],
+            "data": "synthetic",
+            "config": _config(args.precision) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": F * T * M * 8,
                     "d2h_bytes_per_step": N * F * T * M * 8},
@@ -348,7 +389,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu captures, no JSON line")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1",
+                    help="c1 (default, the headline line) or c2 (large mixture)")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.profile_run:
         profile_run()
     elif args.impl == "reference":

@@ -6,8 +6,8 @@ The product path (the CUDA library and its Python binding) never calls it, and t
 module imports nothing from the product package: the two share no code.
 
 What it computes, step by step in the paper's order and notation (NumPy float64 /
-complex128; plain ``einsum`` sums and explicit Python loops for the iterative
-projection).  Each function cites the passage it follows:
+complex128; plain ``einsum`` sums, with NumPy choosing the pairwise contraction order,
+and explicit Python loops for the iterative projection).  Each function cites the passage it follows:
 
 * source model        lambda_ftn = sum_k w_nkf h_nkt                      (Sec. II-B-2, Eq. 9)
 * diagonalised SCMs   Q_f G_nf Q_f^H = Diag(g~_nf),  Q_f = [q_f1..q_fM]^H   (Sec. III-A-1, Eq. 16)
@@ -98,18 +98,18 @@ def init_state(F: int, T: int, M: int, N: int, K: int, seed: int):
 # ---------------------------------------------------------------------------
 def source_psd(W, H):
     """lambda[f,t,n] = sum_k w_nkf h_nkt  (Sec. II-B-2, Eq. 9)."""
-    return np.einsum("nkf,nkt->ftn", W, H)
+    return np.einsum("nkf,nkt->ftn", W, H, optimize=True)
 
 
 def model_power(lam, G):
     """y~[f,t,m] = sum_n lambda_ftn g~_nfm  (Sec. III-A-2, definition below Eq. 17)."""
-    return np.einsum("ftn,nfm->ftm", lam, G)
+    return np.einsum("ftn,nfm->ftm", lam, G, optimize=True)
 
 
 def projected_power(Q, X):
     """x~[f,t,m] = |q_fm^H x_ft|^2 = |(Q_f x_ft)_m|^2  (Sec. III-A-2, below Eq. 17;
     row m of Q_f is q_fm^H, Eq. 16)."""
-    QX = np.einsum("fmj,ftj->ftm", Q, X)
+    QX = np.einsum("fmj,ftj->ftm", Q, X, optimize=True)
     return (QX.real ** 2) + (QX.imag ** 2)
 
 
@@ -145,8 +145,8 @@ def full_rank_covariances(W, H, G, Q):
     G_nf), and Y_ft = sum_n Y_ftn (Eq. 2).  Returns (Ysrc[f,t,n,M,M], Y[f,t,M,M])."""
     lam = source_psd(W, H)
     Qi = np.linalg.inv(Q)                                            # [F,M,M]
-    Gfull = np.einsum("fij,nfj,fkj->nfik", Qi, G, Qi.conj())         # Q^-1 Diag(g) Q^-H
-    Ysrc = np.einsum("ftn,nfik->ftnik", lam, Gfull)
+    Gfull = np.einsum("fij,nfj,fkj->nfik", Qi, G, Qi.conj(), optimize=True)         # Q^-1 Diag(g) Q^-H
+    Ysrc = np.einsum("ftn,nfik->ftnik", lam, Gfull, optimize=True)
     return Ysrc, Ysrc.sum(axis=2)
 
 
@@ -157,7 +157,7 @@ def loglik_fullrank(X, W, H, G, Q):
     _, Y = full_rank_covariances(W, H, G, Q)
     M = X.shape[2]
     sol = np.linalg.solve(Y, X[..., None])[..., 0]
-    quad = np.einsum("ftm,ftm->ft", X.conj(), sol).real
+    quad = np.einsum("ftm,ftm->ft", X.conj(), sol, optimize=True).real
     _, logabs = np.linalg.slogdet(Y)
     return float(-np.sum(quad) - np.sum(logabs) - X.shape[0] * X.shape[1] * M * np.log(np.pi))
 
@@ -174,8 +174,8 @@ def mu_W_terms(xt, W, H, G):
     """Numerator and denominator of the W rule (Sec. III-B-2, Eq. 23):
     num[n,k,f] = sum_{t,m} h_nkt g~_nfm x~/y~^2,  den[n,k,f] = sum_{t,m} h_nkt g~_nfm / y~."""
     A, B = _aux(xt, model_power(source_psd(W, H), G))
-    num = np.einsum("nkt,nfm,ftm->nkf", H, G, A)
-    den = np.einsum("nkt,nfm,ftm->nkf", H, G, B)
+    num = np.einsum("nkt,nfm,ftm->nkf", H, G, A, optimize=True)
+    den = np.einsum("nkt,nfm,ftm->nkf", H, G, B, optimize=True)
     return num, den
 
 
@@ -189,8 +189,8 @@ def mu_H_terms(xt, W, H, G):
     """Numerator and denominator of the H rule (Eq. 24): sums over f and m of
     w_nkf g~_nfm x~/y~^2 and of w_nkf g~_nfm / y~."""
     A, B = _aux(xt, model_power(source_psd(W, H), G))
-    num = np.einsum("nkf,nfm,ftm->nkt", W, G, A)
-    den = np.einsum("nkf,nfm,ftm->nkt", W, G, B)
+    num = np.einsum("nkf,nfm,ftm->nkt", W, G, A, optimize=True)
+    den = np.einsum("nkf,nfm,ftm->nkt", W, G, B, optimize=True)
     return num, den
 
 
@@ -205,8 +205,8 @@ def mu_G_terms(xt, W, H, G):
     num[n,f,m] = sum_t lambda_ftn x~/y~^2,  den[n,f,m] = sum_t lambda_ftn / y~."""
     lam = source_psd(W, H)
     A, B = _aux(xt, model_power(lam, G))
-    num = np.einsum("ftn,ftm->nfm", lam, A)
-    den = np.einsum("ftn,ftm->nfm", lam, B)
+    num = np.einsum("ftn,ftm->nfm", lam, A, optimize=True)
+    den = np.einsum("ftn,ftm->nfm", lam, B, optimize=True)
     return num, den
 
 
@@ -219,7 +219,7 @@ def update_G(xt, W, H, G):
 def weighted_scm(X, yt):
     """V_fm = (1/T) sum_t x_ft x_ft^H / y~_ftm  (Sec. III-A-2, Eq. 18).  Returns V[f,m,i,j]."""
     T = X.shape[1]
-    return np.einsum("fti,ftj,ftm->fmij", X, X.conj(), 1.0 / yt) / T
+    return np.einsum("fti,ftj,ftm->fmij", X, X.conj(), 1.0 / yt, optimize=True) / T
 
 
 def update_Q(X, W, H, G, Q, trace=None):
@@ -261,7 +261,7 @@ def normalise(W, H, G, Q):
     3. mu_nk = sum_f w_nkf;   w_nkf <- w_nkf/mu_nk;  h_nkt <- h_nkt mu_nk  (lambda fixed).
     """
     M = Q.shape[1]
-    phi = np.einsum("fij,fij->f", Q, Q.conj()).real / M
+    phi = np.einsum("fij,fij->f", Q, Q.conj(), optimize=True).real / M
     Q = Q / np.sqrt(phi)[:, None, None]
     G = G / phi[None, :, None]
     nu = G.sum(axis=2)                                               # [N,F]
@@ -325,10 +325,10 @@ def separate(X, W, H, G, Q):
     Returns out[n,f,t,m] (every channel of every source image)."""
     lam = source_psd(W, H)
     yt = model_power(lam, G)
-    QX = np.einsum("fmj,ftj->ftm", Q, X)
+    QX = np.einsum("fmj,ftj->ftm", Q, X, optimize=True)
     Qi = np.linalg.inv(Q)
-    gain = np.einsum("ftn,nfm->nftm", lam, G) / yt[None]
-    return np.einsum("fij,nftj->nfti", Qi, gain * QX[None])
+    gain = np.einsum("ftn,nfm->nftm", lam, G, optimize=True) / yt[None]
+    return np.einsum("fij,nftj->nfti", Qi, gain * QX[None], optimize=True)
 
 
 def separate_direct(X, W, H, G, Q):
@@ -336,4 +336,4 @@ def separate_direct(X, W, H, G, Q):
     matrices (pin of ``separate``)."""
     Ysrc, Y = full_rank_covariances(W, H, G, Q)
     sol = np.linalg.solve(Y, X[..., None])[..., 0]                   # Y_ft^-1 x_ft
-    return np.einsum("ftnij,ftj->nfti", Ysrc, sol)
+    return np.einsum("ftnij,ftj->nfti", Ysrc, sol, optimize=True)

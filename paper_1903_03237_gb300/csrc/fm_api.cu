@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fastmnmf.h"
+#include "fm_gemm.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
 
@@ -30,7 +31,15 @@ constexpr int kSmemTarget = 72 * 1024;   // bytes per CTA aimed for (three CTAs 
 constexpr int kSmemMax = 220 * 1024;     // hard ceiling (227 KB per CTA on sm_103a)
 
 const char* kKindNames[KK_COUNT] = {"w_update", "h_update", "g_update", "scm", "xt_loglik",
-                                    "prep_q", "wiener", "ip"};
+                                    "prep_q", "wiener", "ip", "gemm_lambda", "gemm_w", "gemm_h",
+                                    "pr", "apply"};
+
+// One tensor-core GEMM of the mixed form, planned once per context.
+struct GemmPlan {
+  GemmArgs g{};
+  dim3 grid;
+  int nt = 128;
+};
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
@@ -58,6 +67,13 @@ struct fmnmf_ctx {
   float* H0 = nullptr;
   float* G0 = nullptr;
   float4* Q0 = nullptr;
+  // mixed-precision form
+  bool mixed = false, tf32 = false;
+  float* lam = nullptr;   // [N][F][T]
+  float* PR = nullptr;    // [2][N][F][T]
+  float* Cg = nullptr;    // split GEMM sums
+  GemmPlan gpW, gpH, gpL;
+  int sms = 0;
   std::map<std::pair<int, unsigned>, GraphEntry> graphs;  // (chunk, timing mask) -> graph
   std::string err;
   unsigned timing = 0;  // bit i: bracket launches of kernel class i with events
@@ -192,6 +208,26 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   CK(configure(mx, (int)mx_cap_smem));
   ctx->gS = make_geom(F, T, sep_cap, sms * occupancy(mx, KK_SEP, sep_smem_bytes(N, K, M, mx, sep_cap)));
   ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC);
+  ctx->sms = sms;
+  if (ctx->mixed) {
+    CK(configure_gemm());
+    auto nt_for = [](int n) { return n <= 16 ? 16 : n <= 32 ? 32 : n <= 64 ? 64 : 128; };
+    auto plan_gemm = [&](GemmPlan& gp, int Mr, int Nc, int Kd, int batch, int nt, bool allow_split) {
+      gp.nt = nt;
+      gp.g.Mr = Mr; gp.g.Nc = Nc; gp.g.Kd = Kd; gp.g.batch = batch;
+      const int mt = (Mr + 127) / 128, ntl = (Nc + nt - 1) / nt;
+      const int kchunks = (Kd + kGemmKc - 1) / kGemmKc;
+      int S = 1;
+      if (allow_split) S = std::max(1, std::min(kchunks, (2 * sms + mt * ntl * batch - 1) / (mt * ntl * batch)));
+      const int kspan = ((kchunks + S - 1) / S) * kGemmKc;
+      S = (Kd + kspan - 1) / kspan;
+      gp.g.ksplit = S; gp.g.kspan = kspan;
+      gp.grid = dim3(mt, ntl, batch * S);
+    };
+    plan_gemm(ctx->gpW, F, K, T, 2 * N, nt_for(K), true);
+    plan_gemm(ctx->gpH, T, K, F, 2 * N, nt_for(K), true);
+    plan_gemm(ctx->gpL, F, T, K, N, 128, false);
+  }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
   return FMNMF_OK;
@@ -240,6 +276,13 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
       {(void**)&ctx->G0, N * F * M * 4},
       {(void**)&ctx->Q0, F * M * M * sizeof(float4)},
   };
+  if (ctx->mixed) {
+    const size_t cg = std::max((size_t)ctx->gpW.grid.z * ctx->gpW.g.Mr * ctx->gpW.g.Nc,
+                               (size_t)ctx->gpH.grid.z * ctx->gpH.g.Mr * ctx->gpH.g.Nc);
+    slots.push_back({(void**)&ctx->lam, N * F * T * 4});
+    slots.push_back({(void**)&ctx->PR, 2 * N * F * T * 4});
+    slots.push_back({(void**)&ctx->Cg, cg * 4});
+  }
   size_t total = 0;
   for (auto& s : slots) total += align256(s.bytes);
   if (ctx->opts.hbm_budget && total > ctx->opts.hbm_budget)
@@ -252,6 +295,25 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
   for (auto& s : slots) { *s.dst = base; base += align256(s.bytes); }
   p.X = (const float2*)X;
   p.F = ctx->F; p.T = ctx->T; p.M = ctx->M; p.N = ctx->N; p.K = ctx->K;
+  p.lam = nullptr;
+  if (ctx->mixed) {
+    const long long FT = (long long)F * T;
+    GemmArgs& w = ctx->gpW.g;   // [P;R]_n (f x t) . H_n (k x t)^T
+    w.A = ctx->PR; w.sAb = FT; w.sAi = T; w.sAk = 1;
+    w.B = p.H; w.sBb = (long long)K * T; w.sBj = T; w.sBk = 1; w.bmodB = (int)N;
+    w.C = ctx->Cg; w.sCs = 2LL * N * F * K; w.sCb = (long long)F * K; w.sCi = K; w.sCj = 1;
+    w.status = p.status;
+    GemmArgs& h = ctx->gpH.g;   // [P;R]_n^T (t x f) . W_n (k x f)^T
+    h.A = ctx->PR; h.sAb = FT; h.sAi = 1; h.sAk = T;
+    h.B = p.W; h.sBb = (long long)K * F; h.sBj = F; h.sBk = 1; h.bmodB = (int)N;
+    h.C = ctx->Cg; h.sCs = 2LL * N * T * K; h.sCb = (long long)T * K; h.sCi = K; h.sCj = 1;
+    h.status = p.status;
+    GemmArgs& l = ctx->gpL.g;   // W_n^T (f x k) . H_n^T (t x k)^T = lambda_n (f x t)
+    l.A = p.W; l.sAb = (long long)K * F; l.sAi = 1; l.sAk = F;
+    l.B = p.H; l.sBb = (long long)K * T; l.sBj = 1; l.sBk = T; l.bmodB = (int)N;
+    l.C = ctx->lam; l.sCs = 0; l.sCb = FT; l.sCi = T; l.sCj = 1;
+    l.status = p.status;
+  }
   CK(cudaMemsetAsync(p.counters, 0, (size_t)nctr * 4, ctx->st));
   CK(cudaMemsetAsync(p.status, 0, 4, ctx->st));
   return FMNMF_OK;
@@ -275,7 +337,11 @@ struct Recorder {  // brackets launches with events when timing is on (works und
     return e;
   }
   cudaError_t run(KernelKind k, const LaunchArgs& a) {
-    if (!out || !((c->timing >> (int)k) & 1u)) return launch(c, k, a);
+    return run_fn(k, [&] { return launch(c, k, a); });
+  }
+  template <class Fn>
+  cudaError_t run_fn(KernelKind k, Fn&& fn) {
+    if (!out || !((c->timing >> (int)k) & 1u)) return fn();
     cudaEvent_t e0 = take(), e1 = take();
     // under stream capture the records must be External to become event-record nodes
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -283,14 +349,17 @@ struct Recorder {  // brackets launches with events when timing is on (works und
     if (r != cudaSuccess) return r;
     const unsigned fl = (cs == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
     if ((r = cudaEventRecordWithFlags(e0, c->st, fl)) != cudaSuccess) return r;
-    if ((r = launch(c, k, a)) != cudaSuccess) return r;
+    if ((r = fn()) != cudaSuccess) return r;
     if ((r = cudaEventRecordWithFlags(e1, c->st, fl)) != cudaSuccess) return r;
     out->push_back({(int)k, {e0, e1}});
     return cudaSuccess;
   }
 };
 
+cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec);
+
 cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
+  if (c->mixed) return enqueue_mixed_iteration(c, rec);
   const unsigned mask = c->opts.update_mask;
   const int norm = c->opts.normalise ? FLAG_NORMALISE : 0;
   cudaError_t e;
@@ -302,6 +371,63 @@ cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
     if ((e = rec.run(KK_G, tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG))) != cudaSuccess) return e;
   const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
   if ((e = rec.run(KK_Y, tile_args(c, c->gY, c->smY, yflags, c->ctrY))) != cudaSuccess) return e;
+  if (yflags) {
+    LaunchArgs a;
+    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
+    a.grid = dim3(c->F);
+    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
+  }
+  LaunchArgs x;
+  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+  x.n_pt_blocks = c->n_pt_blocks;
+  x.apply_phi = (yflags != 0);
+  x.do_mu = norm ? 1 : 0;
+  x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
+  return rec.run(KK_XT, x);
+}
+
+// The mixed-precision iteration: tensor-core GEMMs for lambda and the W / H sums.
+cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
+  const unsigned mask = c->opts.update_mask;
+  const int norm = c->opts.normalise ? FLAG_NORMALISE : 0;
+  cudaError_t e;
+  auto gemm = [&](KernelKind k, const GemmPlan& gp) {
+    return rec.run_fn(k, [&] { c->launches++; return launch_gemm(gp.g, c->tf32, gp.nt, gp.grid, c->st); });
+  };
+  auto pr = [&](int mode) {
+    Prob q = c->p;
+    q.lam = c->lam;
+    return rec.run_fn(KK_PR, [&] { c->launches++; return launch_pr(c->maxm, q, c->PR, mode, c->st); });
+  };
+  auto apply = [&](float* fac, int S, int own) {
+    return rec.run_fn(KK_APPLY, [&] {
+      c->launches++;
+      return launch_apply(fac, c->Cg, S, c->N, c->K, own, c->p.status, c->st);
+    });
+  };
+  if (mask & FMNMF_UPDATE_W) {
+    if ((e = pr(0)) != cudaSuccess) return e;
+    if ((e = gemm(KK_GW, c->gpW)) != cudaSuccess) return e;
+    if ((e = apply(c->p.W, c->gpW.g.ksplit, c->F)) != cudaSuccess) return e;
+  }
+  if (mask & FMNMF_UPDATE_H) {
+    if ((e = gemm(KK_GL, c->gpL)) != cudaSuccess) return e;
+    if ((e = pr(1)) != cudaSuccess) return e;
+    if ((e = gemm(KK_GH, c->gpH)) != cudaSuccess) return e;
+    if ((e = apply(c->p.H, c->gpH.g.ksplit, c->T)) != cudaSuccess) return e;
+  }
+  if ((e = gemm(KK_GL, c->gpL)) != cudaSuccess) return e;
+  if (mask & FMNMF_UPDATE_G) {
+    LaunchArgs a = tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG);
+    a.p.lam = c->lam;
+    if ((e = rec.run(KK_G, a)) != cudaSuccess) return e;
+  }
+  const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
+  {
+    LaunchArgs a = tile_args(c, c->gY, c->smY, yflags, c->ctrY);
+    a.p.lam = c->lam;
+    if ((e = rec.run(KK_Y, a)) != cudaSuccess) return e;
+  }
   if (yflags) {
     LaunchArgs a;
     a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
@@ -463,11 +589,13 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
     return set_err(nullptr, FMNMF_EINVAL, "bad shape F=%d T=%d M=%d N=%d K=%d (need F,T,N,K >= 1, 1 <= M <= 8)", F, T, M, N, K);
   if ((double)F * T * M > 2.0e9) return set_err(nullptr, FMNMF_EINVAL, "F*T*M too large (> 2e9)");
   if (!X) return set_err(nullptr, FMNMF_EINVAL, "X is NULL");
-  if (opts && opts->precision != FMNMF_PREC_FP32)
-    return set_err(nullptr, FMNMF_EINVAL, "precision %d not available in this build", opts->precision);
+  if (opts && (opts->precision < FMNMF_PREC_FP32 || opts->precision > FMNMF_PREC_TF32))
+    return set_err(nullptr, FMNMF_EINVAL, "unknown precision %d", opts->precision);
   fmnmf_ctx* ctx = new fmnmf_ctx();
   ctx->F = F; ctx->T = T; ctx->M = M; ctx->N = N; ctx->K = K; ctx->maxm = bucket(M);
   if (opts) ctx->opts = *opts; else fmnmf_default_opts(&ctx->opts);
+  ctx->mixed = ctx->opts.precision != FMNMF_PREC_FP32;
+  ctx->tf32 = ctx->opts.precision == FMNMF_PREC_TF32;
   if (ctx->opts.update_mask & ~(unsigned)FMNMF_UPDATE_ALL) {
     const unsigned bad = ctx->opts.update_mask;
     delete ctx;

@@ -35,6 +35,7 @@ struct Prob {
   float* part;         // split-sum partials (sized by the host for the largest user)
   double* llpart;      // [ll_blocks] per-CTA log-likelihood partials
   unsigned* counters;  // arrival counters of the split reductions (zero between launches)
+  const float* lam;    // [N][F][T] lambda formed by the tensor-core GEMM (mixed form), or null
 };
 
 // Tiling of a launch over (own tile) x (inner split): own = the index the update writes

@@ -287,9 +287,11 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 
   const float* ownF = F_OWN ? p.W : p.H;
   const float* othF = F_OWN ? p.H : p.W;
+  // mixed form: lambda was formed by the tensor-core GEMM and is read, not recomputed
+  const bool lam_mem = (MODE == MODE_G || MODE == MODE_Y) && p.lam != nullptr;
 
   // once per CTA: own factor tile, g~ of the own bins, zeroed accumulators
-  if (MODE != MODE_W)
+  if (MODE != MODE_W && !lam_mem)
     for (int e = tid; e < NK * kOT; e += kThreads) {
       const int nk = e / kOT, o = e % kOT;
       cpa4(own_s + e, ownF + (size_t)nk * SO + o_base + min(o, n_own - 1), o < n_own);
@@ -310,7 +312,9 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
     const int icn = min(IC, i_end - i0);
     __syncthreads();  // previous sub-chunk fully consumed
     // ---- stage the chunk (asynchronous copies, zero-filled past its end) ----
-    if ((SI & 3) == 0 && (icn & 3) == 0) {
+    if (lam_mem) {
+      // the other factor is not needed: lambda is read below
+    } else if ((SI & 3) == 0 && (icn & 3) == 0) {
       // rows 16-byte aligned (SI, i0, IC multiples of 4): one 16-byte copy per 4 floats
       const int q = IC >> 2, qn = icn >> 2;
       for (int row = warp; row < NK; row += kThreads / 32) {
@@ -404,8 +408,17 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
             for (int b = 0; b < 4; ++b) lam[a][b] = 0.f;
           const float* ow = own_s + n * K * kOT + o0;
           const float* oh = oth_s + n * K * ICP + ii;
+          if (lam_mem) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+              const int f = min(o_base + o0 + a, F - 1);
+              const float* lp = p.lam + ((size_t)n * F + f) * T + i0 + ii;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) lam[a][b] = (ii + b < icn) ? __ldg(lp + b) : 0.f;
+            }
+          }
 #pragma unroll 4
-          for (int k = 0; k < K; ++k) {
+          for (int k = 0; !lam_mem && k < K; ++k) {
             const float2 w = *reinterpret_cast<const float2*>(ow + k * kOT);
             const float4 h = ld4(oh + k * ICP);
             lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);

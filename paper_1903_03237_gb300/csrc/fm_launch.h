@@ -15,7 +15,12 @@ enum KernelKind {
   KK_PREP = 5,   // per-bin float64 preparation (log-det, Q^-1)
   KK_SEP = 6,    // Wiener filter (Eq. 3)
   KK_IP = 7,     // IP solve (Eqs. 19-20) + per-bin normalisation
-  KK_COUNT = 8
+  KK_GL = 8,     // mixed form: lambda = W^T H on the tensor cores
+  KK_GW = 9,     // mixed form: W numerator / denominator GEMM
+  KK_GH = 10,    // mixed form: H numerator / denominator GEMM
+  KK_PR = 11,    // mixed form: P, R per TF bin
+  KK_APPLY = 12, // mixed form: multiplicative update from the split GEMM sums
+  KK_COUNT = 13
 };
 
 struct LaunchArgs {
@@ -44,6 +49,14 @@ int occupancy_m8(KernelKind k, size_t smem);
 cudaError_t configure_m2(int bytes);
 cudaError_t configure_m4(int bytes);
 cudaError_t configure_m8(int bytes);
+
+// Mixed-precision form (fm_mixed.cu).
+struct GemmArgs;
+cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStream_t st);
+cudaError_t configure_gemm();
+cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st);
+cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
+                         cudaStream_t st);
 
 // Sets the calling thread's message returned by fmnmf_last_error(NULL).
 void set_thread_error(const char* msg);

@@ -1,0 +1,142 @@
+// Mixed-precision form of the FastMNMF iteration: the dense contractions run on the
+// tensor cores (tcgen05, BF16 or TF32 operands, FP32 accumulation), the rest on the CUDA
+// cores in FP32, the IP in float-float.
+//
+//   lambda_n = W_n^T H_n                     (Eq. 9)      k_gemm_tc  [F x T] per source
+//   P, R per TF bin from x~ and y~           (Eqs. 23-24) k_pr
+//   num/den W_n = [P_n; R_n] H_n^T           (Eq. 23)     k_gemm_tc  sum over t, split-K
+//   num/den H_n = [P_n; R_n]^T W_n^T         (Eq. 24)     k_gemm_tc  sum over f, split-K
+//   W, H <- W, H * sqrt(num/den)                          k_apply (sums the splits in order)
+// The g~ update (Eq. 21) and V_fm (Eq. 18) read the materialised lambda in the tiled
+// sweeps; the IP, x~, log-likelihood and normalisation are those of the plain form.
+#include <cuda_runtime.h>
+
+#include "fm_gemm.cuh"
+#include "fm_kernels.cuh"
+#include "fm_launch.h"
+
+namespace fm {
+
+// P_n = sum_m g~_nfm x~/y~^2 and R_n = sum_m g~_nfm / y~ per TF bin, into PR[2][N][F][T].
+// y~ is read (mode 0, the W update: y~ of the current state is kept in p.yt) or formed from
+// the materialised lambda (mode 1, the H update).
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k_pr(Prob p, float* __restrict__ PR, int mode) {
+  const int F = p.F, T = p.T, M = p.M, N = p.N;
+  const unsigned npts = (unsigned)F * (unsigned)T;
+  const unsigned pt = blockIdx.x * (unsigned)kThreads + threadIdx.x;
+  if (pt >= npts) return;
+  const int f = (int)(pt / (unsigned)T);
+  float y[MAXM], x[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    x[m] = (m < M) ? p.xt[(size_t)pt * M + m] : 0.f;
+    y[m] = (mode == 0 && m < M) ? p.yt[(size_t)pt * M + m] : 0.f;
+  }
+  if (mode == 1) {
+    for (int n = 0; n < N; ++n) {
+      const float l = p.lam[(size_t)n * npts + pt];
+      const float* g = p.G + ((size_t)n * F + f) * M;
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m)
+        if (m < M) y[m] = fmaf(l, g[m], y[m]);
+    }
+  }
+  float A[MAXM], B[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    B[m] = (m < M) ? __fdividef(1.f, y[m]) : 0.f;
+    A[m] = x[m] * B[m] * B[m];
+  }
+  for (int n = 0; n < N; ++n) {
+    const float* g = p.G + ((size_t)n * F + f) * M;
+    float P = 0.f, R = 0.f;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m)
+      if (m < M) { P = fmaf(g[m], A[m], P); R = fmaf(g[m], B[m], R); }
+    PR[(size_t)n * npts + pt] = P;
+    PR[(size_t)(N + n) * npts + pt] = R;
+  }
+}
+
+// fac[n][k][o] *= sqrt(num/den) with num = sum_s C[s][n][o][k], den = sum_s C[s][N+n][o][k].
+__global__ void __launch_bounds__(kThreads) k_apply(float* __restrict__ fac, const float* __restrict__ C, int S,
+                                                    int N, int K, int own, unsigned* status) {
+  const size_t total = (size_t)N * K * own;
+  const size_t e = (size_t)blockIdx.x * kThreads + threadIdx.x;
+  if (e >= total) return;
+  const int o = (int)(e % own);
+  const int nk = (int)(e / own);
+  const int n = nk / K, k = nk - n * K;
+  const size_t split = (size_t)2 * N * own * K;
+  float num = 0.f, den = 0.f;
+  for (int s = 0; s < S; ++s) {
+    num += __ldg(C + s * split + ((size_t)n * own + o) * K + k);
+    den += __ldg(C + s * split + ((size_t)(N + n) * own + o) * K + k);
+  }
+  const float v = fac[e] * sqrtf(num / den);
+  if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+  fac[e] = v;
+}
+
+template <int NT, bool TF32>
+static cudaError_t gemm_launch(const GemmArgs& g, dim3 grid, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)gemm_stage_bytes(NT, TF32);
+  k_gemm_tc<NT, TF32><<<grid, kGemmThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+template <int NT, bool TF32>
+static cudaError_t gemm_configure() {
+  return cudaFuncSetAttribute(k_gemm_tc<NT, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              2 * gemm_stage_bytes(NT, TF32));
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStream_t st) {
+  if (tf32) {
+    switch (nt) {
+      case 16: return gemm_launch<16, true>(g, grid, st);
+      case 32: return gemm_launch<32, true>(g, grid, st);
+      case 64: return gemm_launch<64, true>(g, grid, st);
+      default: return gemm_launch<128, true>(g, grid, st);
+    }
+  }
+  switch (nt) {
+    case 16: return gemm_launch<16, false>(g, grid, st);
+    case 32: return gemm_launch<32, false>(g, grid, st);
+    case 64: return gemm_launch<64, false>(g, grid, st);
+    default: return gemm_launch<128, false>(g, grid, st);
+  }
+}
+
+cudaError_t configure_gemm() {
+  cudaError_t e;
+  if ((e = gemm_configure<16, true>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<32, true>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<64, true>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<128, true>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<16, false>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<32, false>()) != cudaSuccess) return e;
+  if ((e = gemm_configure<64, false>()) != cudaSuccess) return e;
+  return gemm_configure<128, false>();
+}
+
+cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st) {
+  const unsigned npts = (unsigned)p.F * (unsigned)p.T;
+  const dim3 grid((npts + kThreads - 1) / kThreads);
+  switch (maxm) {
+    case 2: k_pr<2><<<grid, kThreads, 0, st>>>(p, PR, mode); break;
+    case 4: k_pr<4><<<grid, kThreads, 0, st>>>(p, PR, mode); break;
+    default: k_pr<8><<<grid, kThreads, 0, st>>>(p, PR, mode); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
+                         cudaStream_t st) {
+  const size_t total = (size_t)N * K * own;
+  k_apply<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(fac, C, S, N, K, own, status);
+  return cudaGetLastError();
+}
+
+}  // namespace fm

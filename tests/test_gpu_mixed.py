@@ -1,0 +1,83 @@
+"""Mixed-precision form (BF16 / TF32 tensor-core contractions, FP32 elsewhere, float-float
+IP) against the float64 oracle.
+
+Bar: after one iteration from the same state, the relative error of W, H, g~, Q, the
+log-likelihood and the separated images is at most 1e-3 (||a - b|| / ||b|| per result,
+|dLL| / sum |terms| for the log-likelihood); the errors are printed per result.
+"""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import fastmnmf_oracle as O
+from paper_1903_03237_gb300.synth import make_mixture, make_state, CONFIGS
+
+from tests._parity import rel, maxrel, ll_rel, as64
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-3
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf
+    return fastmnmf
+
+
+def _mixed_errors(fm, F, T, M, N, K, precision, seed=1, diffuse=0.0):
+    mix = make_mixture(F, T, M, N, K, seed, diffuse_frac=diffuse)
+    W, H, G, Q = make_state(F, T, M, N, K, seed)
+    ctx = fm.Context(mix.X, N, K, precision=precision)
+    ctx.set_state(W, H, G, Q)
+    ctx.iterate(1)
+    ll = ctx.loglik()
+    Wg, Hg, Gg, Qg = ctx.get_state()
+    S = ctx.separate()
+    ctx.close()
+    X64 = mix.X.astype(np.complex128)
+    Wr, Hr, Gr, Qr, tr = O.iterate(X64, *as64(W, H, G, Q), n_iter=1)
+    Sr = O.separate(X64, Wr, Hr, Gr, Qr)
+    return {"W": rel(Wg, Wr), "H": rel(Hg, Hr), "G": rel(Gg, Gr), "Q": rel(Qg, Qr),
+            "LL": ll_rel(ll, tr[-1], X64, Wr, Hr, Gr, Qr), "separated": rel(S, Sr),
+            "W_max": maxrel(Wg, Wr), "H_max": maxrel(Hg, Hr), "G_max": maxrel(Gg, Gr), "Q_max": maxrel(Qg, Qr),
+            "separated_max": maxrel(S, Sr)}
+
+
+SHAPES = [(37, 150, 3, 3, 5), (70, 260, 4, 4, 32), (33, 200, 8, 6, 20), (40, 90, 2, 2, 8)]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in SHAPES])
+def test_mixed_one_iteration(fm, shape, precision):
+    prec = fm.PREC_BF16 if precision == "bf16" else fm.PREC_TF32
+    err = _mixed_errors(fm, *shape, prec)
+    print(precision, shape, json.dumps({k: f"{v:.2e}" for k, v in err.items()}))
+    assert max(err[k] for k in ("W", "H", "G", "Q", "LL", "separated")) < TOL_MIXED, err
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_mixed_c2_full_size(fm, precision):
+    c = CONFIGS["c2"]
+    prec = fm.PREC_BF16 if precision == "bf16" else fm.PREC_TF32
+    err = _mixed_errors(fm, c["F"], c["T"], c["M"], c["N"], c["K"], prec, seed=0)
+    print("c2", precision, json.dumps({k: f"{v:.2e}" for k, v in err.items()}))
+    assert max(err[k] for k in ("W", "H", "G", "Q", "LL", "separated")) < TOL_MIXED, err
+
+
+def test_mixed_trajectory_monotone(fm):
+    mix = make_mixture(70, 260, 4, 4, 32, 3)
+    ctx = fm.Context(mix.X, 4, 32, seed=1, precision=fm.PREC_BF16)
+    lls = [ctx.loglik()]
+    for _ in range(15):
+        ctx.iterate(1)
+        lls.append(ctx.loglik())
+    d = np.diff(lls)
+    # rounding of the BF16 contractions may cost a tiny decrease; the trend must rise
+    assert lls[-1] > lls[0] and d.min() > -1e-4 * abs(lls[0]), (d.min(), lls)
