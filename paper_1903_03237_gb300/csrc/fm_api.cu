@@ -73,6 +73,7 @@ struct fmnmf_ctx {
   float* PR = nullptr;    // [2][N][F][T]
   float* Cg = nullptr;    // split GEMM sums
   GemmPlan gpW, gpH, gpL;
+  int scmS = 1, scmSpan = 64;  // tensor-core V_fm: T splits and frames per split
   int sms = 0;
   std::map<std::pair<int, unsigned>, GraphEntry> graphs;  // (chunk, timing mask) -> graph
   std::string err;
@@ -149,16 +150,16 @@ Geom make_geom(int SO, int SI, int ic_cap, int slots) {
 }
 
 // Largest sub-chunk (multiple of 4, <= 256) whose shared memory fits `limit` bytes.
-int ic_cap_for(int mode, int N, int K, int M, int maxm, int limit) {
+int ic_cap_for(int mode, int N, int K, int M, int maxm, int limit, bool lam_mem = false) {
   for (int ic = 256; ic >= 4; ic -= 4) {
-    size_t bytes = (size_t)tile_smem(mode, N, K, M, maxm, ic).total * 4;
+    size_t bytes = (size_t)tile_smem(mode, N, K, M, maxm, ic, lam_mem).total * 4;
     if (bytes <= (size_t)limit) return ic;
   }
   return 0;
 }
 
-size_t smem_bytes(int mode, int N, int K, int M, int maxm, int ic) {
-  size_t b = (size_t)tile_smem(mode, N, K, M, maxm, ic).total * 4;
+size_t smem_bytes(int mode, int N, int K, int M, int maxm, int ic, bool lam_mem = false) {
+  size_t b = (size_t)tile_smem(mode, N, K, M, maxm, ic, lam_mem).total * 4;
   return b;
 }
 
@@ -175,19 +176,21 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int caps[4];
+  // the mixed form reads lambda in the g~ and y~ sweeps: no factor tiles there
+  auto lm = [&](int mode) { return ctx->mixed && (mode == MODE_G || mode == MODE_Y); };
   for (int mode = 0; mode < 4; ++mode) {
-    int cap = ic_cap_for(mode, N, K, M, mx, kSmemTarget);
-    if (cap == 0) cap = ic_cap_for(mode, N, K, M, mx, kSmemMax);
+    int cap = ic_cap_for(mode, N, K, M, mx, kSmemTarget, lm(mode));
+    if (cap == 0) cap = ic_cap_for(mode, N, K, M, mx, kSmemMax, lm(mode));
     if (cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K = %d too large for the shared-memory tiles", N * K);
     caps[mode] = cap;
   }
   size_t mx_cap_smem = 48 * 1024;
   for (int mode = 0; mode < 4; ++mode)
-    mx_cap_smem = std::max(mx_cap_smem, smem_bytes(mode, N, K, M, mx, caps[mode]));
+    mx_cap_smem = std::max(mx_cap_smem, smem_bytes(mode, N, K, M, mx, caps[mode], lm(mode)));
   CK(configure(mx, (int)mx_cap_smem));
   const KernelKind kinds[4] = {KK_W, KK_H, KK_G, KK_Y};
   auto slots = [&](int mode) {
-    return sms * occupancy(mx, kinds[mode], smem_bytes(mode, N, K, M, mx, caps[mode]));
+    return sms * occupancy(mx, kinds[mode], smem_bytes(mode, N, K, M, mx, caps[mode], lm(mode)));
   };
   ctx->gW = make_geom(F, T, caps[MODE_W], slots(MODE_W));
   ctx->gH = make_geom(T, F, caps[MODE_H], slots(MODE_H));
@@ -195,8 +198,8 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   ctx->gY = make_geom(F, T, caps[MODE_Y], slots(MODE_Y));
   ctx->smW = smem_bytes(MODE_W, N, K, M, mx, ctx->gW.IC);
   ctx->smH = smem_bytes(MODE_H, N, K, M, mx, ctx->gH.IC);
-  ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC);
-  ctx->smY = smem_bytes(MODE_Y, N, K, M, mx, ctx->gY.IC);
+  ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC, lm(MODE_G));
+  ctx->smY = smem_bytes(MODE_Y, N, K, M, mx, ctx->gY.IC, lm(MODE_Y));
   int sep_cap = 0;
   for (int ic = 256; ic >= 4; ic -= 4)
     if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemTarget) { sep_cap = ic; break; }
@@ -219,6 +222,9 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
       const int kchunks = (Kd + kGemmKc - 1) / kGemmKc;
       int S = 1;
       if (allow_split) S = std::max(1, std::min(kchunks, (2 * sms + mt * ntl * batch - 1) / (mt * ntl * batch)));
+      // a TMEM accumulator sums its split sequentially in FP32: at most 512 terms per split
+      // (the splits are then summed in a fixed order), which bounds the rounding growth
+      S = std::max(S, (Kd + 511) / 512);
       const int kspan = ((kchunks + S - 1) / S) * kGemmKc;
       S = (Kd + kspan - 1) / kspan;
       gp.g.ksplit = S; gp.g.kspan = kspan;
@@ -227,6 +233,12 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     plan_gemm(ctx->gpW, F, K, T, 2 * N, nt_for(K), true);
     plan_gemm(ctx->gpH, T, K, F, 2 * N, nt_for(K), true);
     plan_gemm(ctx->gpL, F, T, K, N, 128, false);
+    const int nb = (F + scm_bins_per_cta(mx) - 1) / scm_bins_per_cta(mx);
+    const int tch = (T + 31) / 32;  // chunks of 32 frames
+    int S = std::max(1, std::min(tch, (2 * sms) / nb));
+    S = std::max(S, (T + 127) / 128);  // at most 128 frames summed per TMEM accumulator
+    ctx->scmSpan = ((tch + S - 1) / S) * 32;
+    ctx->scmS = (T + ctx->scmSpan - 1) / ctx->scmSpan;
   }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
@@ -243,6 +255,7 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
   part = std::max(part, (size_t)ctx->gH.S * tile_part_floats(MODE_H, F, T, M, N, K, mx));
   part = std::max(part, (size_t)ctx->gG.S * tile_part_floats(MODE_G, F, T, M, N, K, mx));
   part = std::max(part, (size_t)ctx->gY.S * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
+  if (ctx->mixed) part = std::max(part, (size_t)ctx->scmS * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   const unsigned nctr = ctx->gW.n_own_tiles + ctx->gH.n_own_tiles + ctx->gG.n_own_tiles +
                         ctx->gY.n_own_tiles + 1;
   ctx->ctrW = 0;
@@ -418,19 +431,28 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
   }
   if ((e = gemm(KK_GL, c->gpL)) != cudaSuccess) return e;
   if (mask & FMNMF_UPDATE_G) {
-    LaunchArgs a = tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG);
+    LaunchArgs a = tile_args(c, c->gG, c->smG, FLAG_UPDATE | FLAG_LAM_MEM, c->ctrG);
     a.p.lam = c->lam;
     if ((e = rec.run(KK_G, a)) != cudaSuccess) return e;
   }
   const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
-  {
-    LaunchArgs a = tile_args(c, c->gY, c->smY, yflags, c->ctrY);
+  int ipS = c->gY.S;
+  if (mask & FMNMF_UPDATE_Q) {
+    // y~ and the V_fm split sums on the tensor cores
+    Prob q = c->p;
+    q.lam = c->lam;
+    // V_fm always in TF32: with BF16 operands the IP update misses the 1e-3 bar at M = 8
+    if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, true, q, c->scmS, c->scmSpan, c->st); })) != cudaSuccess)
+      return e;
+    ipS = c->scmS;
+  } else {
+    LaunchArgs a = tile_args(c, c->gY, c->smY, yflags | FLAG_LAM_MEM, c->ctrY);
     a.p.lam = c->lam;
     if ((e = rec.run(KK_Y, a)) != cudaSuccess) return e;
   }
   if (yflags) {
     LaunchArgs a;
-    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
+    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = ipS;
     a.grid = dim3(c->F);
     if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
   }
@@ -449,7 +471,16 @@ fmnmf_status refresh_state(fmnmf_ctx* ctx) {
   a.p = ctx->p; a.st = ctx->st;
   a.grid = dim3((ctx->F + 7) / 8);
   CK(launch(ctx, KK_PREP, a));
-  CK(launch(ctx, KK_Y, tile_args(ctx, ctx->gY, ctx->smY, 0, ctx->ctrY)));
+  if (ctx->mixed) {
+    // lambda on the tensor cores, then y~ from it (the launch geometry of the mixed form)
+    ctx->launches++;
+    CK(launch_gemm(ctx->gpL.g, ctx->tf32, ctx->gpL.nt, ctx->gpL.grid, ctx->st));
+    LaunchArgs y = tile_args(ctx, ctx->gY, ctx->smY, FLAG_LAM_MEM, ctx->ctrY);
+    y.p.lam = ctx->lam;
+    CK(launch(ctx, KK_Y, y));
+  } else {
+    CK(launch(ctx, KK_Y, tile_args(ctx, ctx->gY, ctx->smY, 0, ctx->ctrY)));
+  }
   LaunchArgs x;
   x.p = ctx->p; x.st = ctx->st; x.ctr = ctx->ctrLL; x.n_pt_blocks = ctx->n_pt_blocks;
   x.apply_phi = 0; x.do_mu = 0; x.grid = dim3(ctx->n_pt_blocks);

@@ -22,7 +22,9 @@ namespace fm {
 enum { MODE_W = 0, MODE_H = 1, MODE_G = 2, MODE_Y = 3 };
 // FLAG_DO_V (MODE_Y): form V_fm and run the IP update.  FLAG_UPDATE (MODE_G): apply the
 // g~ rule (without it the launch only normalises).  FLAG_NORMALISE: scale normalisation.
-enum { FLAG_DO_V = 1, FLAG_NORMALISE = 2, FLAG_UPDATE = 4 };
+// FLAG_LAM_MEM (MODE_G / MODE_Y): lambda is read from p.lam (mixed form) and the shared
+// memory holds no factor tiles; the host sizes the launch's shared memory the same way.
+enum { FLAG_DO_V = 1, FLAG_NORMALISE = 2, FLAG_UPDATE = 4, FLAG_LAM_MEM = 8 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -38,13 +40,14 @@ struct TileSmem {
   int own, oth, gw, gi, xs, ys, xc, a, b, acc, total;
 };
 __host__ __device__ inline int r4(int x) { return (x + 3) & ~3; }
-__host__ __device__ inline TileSmem tile_smem(int mode, int N, int K, int M, int MAXM, int IC) {
+// lam_mem: lambda is read from memory (mixed form, MODE_G / MODE_Y): no factor tiles.
+__host__ __device__ inline TileSmem tile_smem(int mode, int N, int K, int M, int MAXM, int IC, bool lam_mem = false) {
   const int ICP = IC + 4, NK = N * K;
   const bool f_own = (mode != MODE_H);
   TileSmem s;
   int o = 0;
-  s.own = o; o += (mode != MODE_W) ? NK * kOT : 0;           // own factor tile [NK][kOT]
-  s.oth = o; o += NK * ICP;                                   // other factor chunk [NK][ICP]
+  s.own = o; o += (mode != MODE_W && !lam_mem) ? NK * kOT : 0;  // own factor tile [NK][kOT]
+  s.oth = o; o += lam_mem ? 0 : NK * ICP;                        // other factor chunk [NK][ICP]
   s.gw = o;  o += f_own ? r4(N * kOT * M) : 0;                // g~ of the own bins [N][kOT][M]
   s.gi = o;  o += (mode == MODE_H) ? N * M * ICP : 0;         // g~ of the chunk bins [N][M][ICP]
   s.xs = o;  o += (mode != MODE_Y) ? kOT * M * ICP : 0;       // x~ [kOT][M][ICP]
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
   const int i_begin = s * g.span;
   const int i_end = min(SI, i_begin + g.span);
   const int IC = g.IC, ICP = g.ICP;
-  const TileSmem L = tile_smem(MODE, N, K, M, MAXM, IC);
+  const bool lam_mem = (MODE == MODE_G || MODE == MODE_Y) && (flags & FLAG_LAM_MEM);
+  const TileSmem L = tile_smem(MODE, N, K, M, MAXM, IC, lam_mem);
   float* own_s = sm + L.own;
   float* oth_s = sm + L.oth;
   float* gw_s = sm + L.gw;
@@ -287,8 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 
   const float* ownF = F_OWN ? p.W : p.H;
   const float* othF = F_OWN ? p.H : p.W;
-  // mixed form: lambda was formed by the tensor-core GEMM and is read, not recomputed
-  const bool lam_mem = (MODE == MODE_G || MODE == MODE_Y) && p.lam != nullptr;
+  // mixed form (lam_mem): lambda was formed by the tensor-core GEMM and is read, not recomputed
 
   // once per CTA: own factor tile, g~ of the own bins, zeroed accumulators
   if (MODE != MODE_W && !lam_mem)

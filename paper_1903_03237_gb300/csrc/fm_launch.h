@@ -55,6 +55,9 @@ struct GemmArgs;
 cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStream_t st);
 cudaError_t configure_gemm();
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st);
+// V_fm split sums on the tensor cores (and y~), grid (ceil(F / bins per CTA), S).
+cudaError_t launch_scm_tc(int maxm, bool tf32, const Prob& p, int S, int span, cudaStream_t st);
+int scm_bins_per_cta(int maxm);
 cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
                          cudaStream_t st);
 

@@ -14,6 +14,7 @@
 #include "fm_gemm.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
+#include "fm_scm_tc.cuh"
 
 namespace fm {
 
@@ -109,8 +110,27 @@ cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStr
   }
 }
 
+template <int MAXM, bool TF32>
+static cudaError_t scm_launch(const Prob& p, int S, int span, cudaStream_t st) {
+  using C = ScmCfg<MAXM, TF32>;
+  const dim3 grid((p.F + C::FG - 1) / C::FG, S);
+  k_scm_tc<MAXM, TF32><<<grid, kScmThreads, C::SMEM, st>>>(p, S, span);
+  return cudaGetLastError();
+}
+template <int MAXM, bool TF32>
+static cudaError_t scm_configure() {
+  return cudaFuncSetAttribute(k_scm_tc<MAXM, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              ScmCfg<MAXM, TF32>::SMEM);
+}
+
 cudaError_t configure_gemm() {
   cudaError_t e;
+  if ((e = scm_configure<2, false>()) != cudaSuccess) return e;
+  if ((e = scm_configure<4, false>()) != cudaSuccess) return e;
+  if ((e = scm_configure<8, false>()) != cudaSuccess) return e;
+  if ((e = scm_configure<2, true>()) != cudaSuccess) return e;
+  if ((e = scm_configure<4, true>()) != cudaSuccess) return e;
+  if ((e = scm_configure<8, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<16, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<32, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<64, true>()) != cudaSuccess) return e;
@@ -120,6 +140,19 @@ cudaError_t configure_gemm() {
   if ((e = gemm_configure<64, false>()) != cudaSuccess) return e;
   return gemm_configure<128, false>();
 }
+
+cudaError_t launch_scm_tc(int maxm, bool tf32, const Prob& p, int S, int span, cudaStream_t st) {
+  if (tf32) {
+    if (maxm == 2) return scm_launch<2, true>(p, S, span, st);
+    if (maxm == 4) return scm_launch<4, true>(p, S, span, st);
+    return scm_launch<8, true>(p, S, span, st);
+  }
+  if (maxm == 2) return scm_launch<2, false>(p, S, span, st);
+  if (maxm == 4) return scm_launch<4, false>(p, S, span, st);
+  return scm_launch<8, false>(p, S, span, st);
+}
+
+int scm_bins_per_cta(int maxm) { return 128 / (maxm * maxm); }
 
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st) {
   const unsigned npts = (unsigned)p.F * (unsigned)p.T;
