@@ -366,6 +366,136 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def c3_instances(n=64, seed=0):
+    """Batched workload: n mixtures, T ~ U{200..4000}, M in {2,4,8} with N = M, K = 16,
+    F = 513, per-instance seeds 1000 + i (same generative model as the other configs)."""
+    rng = np.random.default_rng(seed)
+    Ts = rng.integers(200, 4001, size=n)
+    Ms = rng.choice([2, 4, 8], size=n)
+    return [(513, int(T), int(M), int(M), 16, 1000 + i) for i, (T, M) in enumerate(zip(Ts, Ms))]
+
+
+def run_batched(args):
+    """One step = every instance restarted from its seeded state and iterated 50 times, all
+    members of one batch (one graph launch per step).  Also times the same step with the
+    instances run one after another (sequential), for comparison."""
+    import torch
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    from paper_1903_03237_gb300.synth import make_mixture
+    iters = 50
+    inst = c3_instances(args.instances)
+    prec = PRECISIONS[args.precision]
+    ctxs = []
+    for (F, T, M, N, K, sd) in inst:
+        mix = make_mixture(F, T, M, N, K, sd)
+        ctxs.append(fm.Context(mix.X, N, K, seed=sd, precision=prec))
+    units = sum(F * T * iters for (F, T, M, N, K, sd) in inst)
+    batch = fm.Batch(ctxs)
+
+    def step_batched():
+        for c in ctxs:
+            c.restart()
+        batch.iterate(iters)
+
+    def step_sequential():
+        for c in ctxs:
+            c.restart()
+            c.iterate(iters)
+
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            tot += time.perf_counter() - t0
+        return tot
+    l0 = sum(c.launch_count() for c in ctxs)
+    t_b = timed(step_batched)
+    launches = sum(c.launch_count() for c in ctxs) - l0
+    batch.sync()
+    t_s = timed(step_sequential)
+    for c in ctxs:
+        c.sync()
+    value = units * args.steps / t_b
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"batched: {len(inst)} mixtures, T ~ U{{200..4000}}, M in {{2,4,8}}, N = M, K 16, "
+                               f"F 513, {iters} iterations each, one graph launch per step",
+                   "l2": "flushed between timed steps (512 MB write)", "precision": args.precision},
+        "sequential_value": units * args.steps / t_s, "batched_over_sequential": t_s / t_b,
+        "gpu_launches": launches,
+    }), flush=True)
+    batch.close()
+
+
+def run_serving(args):
+    """Serving workload: Poisson arrivals at 20 requests/s (arrival seed 7); each request
+    M 4, N 3, K 16, F 513, T = min(6000, round(exp(ln 375 + 0.6 Z))), per-request seed
+    2000 + i, 50 iterations then the Wiener separation.  Requests are submitted at their
+    arrival times; latency = completion - arrival.  Runs the continuous-batching server and,
+    for comparison, the same arrivals served one request at a time (FIFO, max_active 1)."""
+    import torch
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    from paper_1903_03237_gb300.synth import make_mixture
+    R = args.requests
+    rng = np.random.default_rng(7)
+    gaps = rng.exponential(1.0 / 20.0, size=R)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    Ts = np.minimum(6000, np.round(np.exp(np.log(375.0) + 0.6 * rng.standard_normal(R)))).astype(int)
+    Ts = np.maximum(Ts, 8)
+    # mixtures: slices of a few long seeded draws (the generator's cost stays out of the loop)
+    pool = [make_mixture(513, int(Ts.max()), 4, 3, 16, 2000 + i).X for i in range(4)]
+    reqs = [np.ascontiguousarray(pool[i % 4][:, :T, :]) for i, T in enumerate(Ts)]
+    units = float(sum(513 * int(T) * 50 for T in Ts))
+
+    def serve(max_active):
+        with fm.Server(max_active=max_active, iters_per_step=10, precision=PRECISIONS[args.precision]) as srv:
+            ids = []
+            t0 = time.perf_counter()
+            for i in range(R):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                ids.append(srv.submit(reqs[i], 3, 16, 50, seed=2000 + i))
+            lat = []
+            for j in ids:
+                srv.wait(j, 600.0)
+                st, l = srv.poll(j)
+                lat.append(l)
+                srv.result(j)
+            wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "throughput": units / wall, "wall_s": wall}
+
+    cb = serve(args.max_active)
+    fifo = serve(1)
+    print(json.dumps({
+        "metric": METRIC, "value": cb["throughput"], "unit": UNIT, "n_gpus": 1, "steps": R, "warmup": 0,
+        "ms_per_step": 1e3 * cb["wall_s"] / R, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"serving: {R} requests, Poisson 20/s, M4 N3 K16 F513, T lognormal (median 375, "
+                               "sigma 0.6, cap 6000), 50 iterations + Wiener each",
+                   "max_active": args.max_active, "iters_per_step": 10, "precision": args.precision},
+        "latency_p50_ms": cb["p50_ms"], "latency_p99_ms": cb["p99_ms"],
+        "fifo": fifo,
+    }), flush=True)
+
+
 def profile_run():
     """A short run of the same workload for ncu captures: context, 2 iterations, separation."""
     import torch
@@ -389,14 +519,21 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu captures, no JSON line")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1",
-                    help="c1 (default, the headline line) or c2 (large mixture)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c3", "c4"], default="c1",
+                    help="c1 (default, the headline line), c2 (large mixture), c3 (batched mixtures), c4 (serving)")
+    ap.add_argument("--requests", type=int, default=2000, help="c4: number of requests")
+    ap.add_argument("--max-active", type=int, default=16, help="c4: resident requests")
+    ap.add_argument("--instances", type=int, default=64, help="c3: number of mixtures")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
     args = ap.parse_args()
     global WORKLOAD
-    WORKLOAD = WORKLOADS[args.workload]
+    WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])
     if args.profile_run:
         profile_run()
+    elif args.workload == "c3":
+        run_batched(args)
+    elif args.workload == "c4":
+        run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -98,6 +98,11 @@ fmnmf_status fmnmf_default_opts(fmnmf_opts* opts);
 fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, int T, int M,
                         int N, int K, uint64_t seed, const fmnmf_opts* opts);
 
+/* Device bytes a context of this shape and options occupies (its arena, plus the Wiener
+ * output buffer fmnmf_separate allocates for a host destination).  No device memory is
+ * touched; the current device's properties are used for the tiling. */
+fmnmf_status fmnmf_footprint(int F, int T, int M, int N, int K, const fmnmf_opts* opts, size_t* bytes);
+
 /* Replaces the mixture of an existing context (same F, T, M) and re-initialises the state
  * from `seed` as fmnmf_init does, reusing the context's device memory. */
 fmnmf_status fmnmf_reset(fmnmf_ctx* ctx, const void* X, int x_on_device, uint64_t seed);
@@ -168,6 +173,61 @@ const char* fmnmf_last_error(const fmnmf_ctx* ctx);
 fmnmf_status fmnmf_set_timing(fmnmf_ctx* ctx, int kinds);
 fmnmf_status fmnmf_kernel_times(fmnmf_ctx* ctx, double* ms, long long* launches, int* n);
 const char* fmnmf_kernel_name(int i);
+
+/*
+ * Batches: several contexts (independent mixtures, any shapes and precisions) iterated by
+ * one CUDA graph launch.  fmnmf_batch_create captures nothing yet; the first
+ * fmnmf_batch_iterate for a given chunk length captures every member's iteration into
+ * one graph with one branch per context (forked from and joined to the batch's own
+ * stream), so the members' kernels overlap on the device; later calls replay it.  Each
+ * member computes exactly what fmnmf_iterate would (same kernels, same results).  The
+ * contexts must use distinct streams (the default private streams do), stay alive while
+ * the batch exists, and not be iterated on their own while a batch call is in flight.
+ * fmnmf_batch_sync waits for the batch and reports the first member error.
+ */
+typedef struct fmnmf_batch fmnmf_batch;
+fmnmf_status fmnmf_batch_create(fmnmf_ctx* const* ctxs, int n, fmnmf_batch** out);
+fmnmf_status fmnmf_batch_iterate(fmnmf_batch* batch, int n_iter);
+fmnmf_status fmnmf_batch_sync(fmnmf_batch* batch);
+fmnmf_status fmnmf_batch_destroy(fmnmf_batch* batch);
+
+/*
+ * Serving (continuous batching).  A server accepts separation requests of any shape from
+ * any thread and returns each one's separated images.  Its scheduler thread:
+ *  - admits queued requests in arrival order while fewer than max_active are resident
+ *    and their footprint (fmnmf_footprint) fits the HBM budget; the context and state of
+ *    an admitted request stay resident on the device until it completes;
+ *  - advances every resident request by iters_per_step iterations per step, each on its
+ *    own stream so their kernels overlap, and admits new arrivals at step boundaries;
+ *  - separates a request that has run its iterations (Eq. 3) into a host buffer, frees
+ *    its device memory and marks it done.
+ * A request's results equal those of a context running it alone (fmnmf_init,
+ * fmnmf_iterate, fmnmf_separate with the same seed).  Latency = completion - submission.
+ *  hbm_budget      device bytes for admitted requests (0 = 70 % of the free memory at
+ *                  creation); a request larger than it is rejected with FMNMF_ENOMEM.
+ *  max_active      resident requests (0 = 16); iters_per_step (0 = 10); precision FMNMF_PREC_*.
+ * submit copies X (host, complex64 [F][T][M]) and returns at once; wait blocks up to
+ * timeout_s; result copies the images ([N][F][T][M] complex64, host) and the final
+ * log-likelihood and forgets the request (a failed request returns its error).  destroy
+ * drops queued requests, finishes the resident ones and frees everything.
+ */
+typedef struct fmnmf_server fmnmf_server;
+enum { FMNMF_JOB_QUEUED = 0, FMNMF_JOB_RUNNING = 1, FMNMF_JOB_DONE = 2, FMNMF_JOB_FAILED = 3 };
+typedef struct {
+  size_t hbm_budget;
+  int max_active;
+  int iters_per_step;
+  int precision;
+} fmnmf_server_opts;
+fmnmf_status fmnmf_server_create(const fmnmf_server_opts* opts, fmnmf_server** out);
+fmnmf_status fmnmf_server_submit(fmnmf_server* server, const void* X, int F, int T, int M, int N, int K,
+                                 int n_iter, uint64_t seed, uint64_t* job);
+fmnmf_status fmnmf_server_poll(fmnmf_server* server, uint64_t job, int* state, double* latency_s);
+fmnmf_status fmnmf_server_wait(fmnmf_server* server, uint64_t job, double timeout_s, int* state);
+fmnmf_status fmnmf_server_result(fmnmf_server* server, uint64_t job, void* out, double* loglik);
+fmnmf_status fmnmf_server_stats(fmnmf_server* server, long long* queued, long long* active,
+                                long long* completed, long long* failed, size_t* bytes_in_use);
+fmnmf_status fmnmf_server_destroy(fmnmf_server* server);
 
 /* Number of kernel launches this context has enqueued since creation. */
 long long fmnmf_launch_count(const fmnmf_ctx* ctx);

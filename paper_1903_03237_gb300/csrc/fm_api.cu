@@ -86,6 +86,16 @@ struct fmnmf_ctx {
   std::vector<cudaEvent_t> evpool;
 };
 
+// A batch: several contexts iterated by one CUDA graph with one branch per context.
+struct fmnmf_batch {
+  std::vector<fmnmf_ctx*> ctxs;
+  cudaStream_t st = nullptr;  // origin stream: fork and join point of the branches
+  std::map<int, cudaGraphExec_t> graphs;  // chunk length -> executable graph
+  std::map<int, long long> graph_launches;
+  std::vector<cudaEvent_t> events;
+  std::string err;
+};
+
 namespace {
 
 fmnmf_status set_err(fmnmf_ctx* c, fmnmf_status s, const char* fmt, ...) {
@@ -247,7 +257,8 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-fmnmf_status allocate(fmnmf_ctx* ctx) {
+// Lays out (dry_run: only sizes, into ctx->arena_bytes) or allocates the context arena.
+fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
   const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
   const int mx = ctx->maxm;
   size_t part = 0;
@@ -298,6 +309,10 @@ fmnmf_status allocate(fmnmf_ctx* ctx) {
   }
   size_t total = 0;
   for (auto& s : slots) total += align256(s.bytes);
+  if (dry_run) {
+    ctx->arena_bytes = total;
+    return FMNMF_OK;
+  }
   if (ctx->opts.hbm_budget && total > ctx->opts.hbm_budget)
     return set_err(ctx, FMNMF_ENOMEM, "needs %zu bytes of device memory, budget %zu", total,
                    ctx->opts.hbm_budget);
@@ -651,6 +666,23 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
   return FMNMF_OK;
 }
 
+fmnmf_status fmnmf_footprint(int F, int T, int M, int N, int K, const fmnmf_opts* opts, size_t* bytes) {
+  if (!bytes) return set_err(nullptr, FMNMF_EINVAL, "bytes is NULL");
+  if (F < 1 || T < 1 || M < 1 || M > kMaxM || N < 1 || K < 1)
+    return set_err(nullptr, FMNMF_EINVAL, "bad shape F=%d T=%d M=%d N=%d K=%d", F, T, M, N, K);
+  fmnmf_ctx tmp;
+  tmp.F = F; tmp.T = T; tmp.M = M; tmp.N = N; tmp.K = K; tmp.maxm = bucket(M);
+  if (opts) tmp.opts = *opts; else fmnmf_default_opts(&tmp.opts);
+  tmp.mixed = tmp.opts.precision != FMNMF_PREC_FP32;
+  tmp.tf32 = tmp.opts.precision == FMNMF_PREC_TF32;
+  fmnmf_status s = plan(&tmp);
+  if (s == FMNMF_OK) s = allocate(&tmp, true);
+  if (s != FMNMF_OK) { g_thread_err = tmp.err; return s; }
+  // the Wiener filter's output buffer when the result goes to the host
+  *bytes = tmp.arena_bytes + (size_t)N * F * T * M * sizeof(float2);
+  return FMNMF_OK;
+}
+
 fmnmf_status fmnmf_reset(fmnmf_ctx* ctx, const void* X, int x_on_device, uint64_t seed) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
   fmnmf_status s;
@@ -835,5 +867,107 @@ fmnmf_status fmnmf_kernel_times(fmnmf_ctx* ctx, double* ms, long long* launches,
 const char* fmnmf_kernel_name(int i) { return (i >= 0 && i < KK_COUNT) ? kKindNames[i] : ""; }
 
 long long fmnmf_launch_count(const fmnmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ---- batches ---------------------------------------------------------------------------
+fmnmf_status fmnmf_batch_create(fmnmf_ctx* const* ctxs, int n, fmnmf_batch** out) {
+  if (!out || !ctxs || n < 1) return set_err(nullptr, FMNMF_EINVAL, "batch_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return set_err(nullptr, FMNMF_EINVAL, "batch_create: context %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->st == ctxs[i]->st)
+        return set_err(nullptr, FMNMF_EINVAL, "batch_create: contexts %d and %d share a stream", j, i);
+  }
+  fmnmf_batch* b = new fmnmf_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete b; return set_err(nullptr, FMNMF_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+  *out = b;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_batch_iterate(fmnmf_batch* b, int n_iter) {
+  if (!b || n_iter < 0) return set_err(nullptr, FMNMF_EINVAL, "batch_iterate: bad arguments");
+  fmnmf_ctx* ctx = nullptr;  // for CK
+  while (n_iter > 0) {
+    const int chunk = std::min(n_iter, kMaxChunk);
+    auto it = b->graphs.find(chunk);
+    if (it == b->graphs.end()) {
+      // capture: fork every context stream off the origin stream, enqueue its iterations,
+      // join back; the result is one graph whose branches run concurrently
+      const int n = (int)b->ctxs.size();
+      while ((int)b->events.size() < n + 1) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->events.push_back(ev);
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaEventRecord(b->events[n], b->st);
+      long long launches = 0;
+      for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        fmnmf_ctx* c = b->ctxs[i];
+        if ((e = cudaStreamWaitEvent(c->st, b->events[n], 0)) != cudaSuccess) break;
+        Recorder rec{c, nullptr};
+        const long long before = c->launches;
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_iteration(c, rec);
+        launches += c->launches - before;
+        c->launches = before;
+        if (e == cudaSuccess) e = cudaEventRecord(b->events[i], c->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->events[i], 0);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        b->err = std::string("batch graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+        return set_err(nullptr, FMNMF_ECUDA, "%s", b->err.c_str());
+      }
+      cudaGraphExec_t ex = nullptr;
+      CK(cudaGraphInstantiate(&ex, g, 0));
+      cudaGraphDestroy(g);
+      it = b->graphs.emplace(chunk, ex).first;
+      b->graph_launches[chunk] = launches;
+    }
+    // the origin stream must follow the work already queued on every member stream
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+      CK(cudaEventRecord(b->events[i], b->ctxs[i]->st));
+      CK(cudaStreamWaitEvent(b->st, b->events[i], 0));
+    }
+    CK(cudaGraphLaunch(it->second, b->st));
+    // and every member stream must follow the graph before its own next work
+    CK(cudaEventRecord(b->events[b->ctxs.size()], b->st));
+    for (auto* c : b->ctxs) {
+      CK(cudaStreamWaitEvent(c->st, b->events[b->ctxs.size()], 0));
+    }
+    // launch accounting: spread over the member contexts in proportion
+    const long long per = b->graph_launches[chunk] / (long long)b->ctxs.size();
+    for (auto* c : b->ctxs) c->launches += per;
+    n_iter -= chunk;
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_batch_sync(fmnmf_batch* b) {
+  if (!b) return set_err(nullptr, FMNMF_EINVAL, "batch is NULL");
+  fmnmf_status worst = FMNMF_OK;
+  for (auto* c : b->ctxs) {
+    fmnmf_status s = check_status(c);
+    if (s != FMNMF_OK && worst == FMNMF_OK) {
+      worst = s;
+      set_err(nullptr, s, "%s", c->err.c_str());
+    }
+  }
+  return worst;
+}
+
+fmnmf_status fmnmf_batch_destroy(fmnmf_batch* b) {
+  if (!b) return FMNMF_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto ev : b->events) cudaEventDestroy(ev);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+  return FMNMF_OK;
+}
 
 }  // extern "C"

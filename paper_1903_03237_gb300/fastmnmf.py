@@ -32,7 +32,10 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
 EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "fmnmf_iterate", "fmnmf_sync",
            "fmnmf_loglik", "fmnmf_separate", "fmnmf_get_state", "fmnmf_set_state", "fmnmf_shape",
            "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
-           "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc"]
+           "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc",
+           "fmnmf_batch_create", "fmnmf_batch_iterate", "fmnmf_batch_sync", "fmnmf_batch_destroy",
+           "fmnmf_footprint", "fmnmf_server_create", "fmnmf_server_submit", "fmnmf_server_poll",
+           "fmnmf_server_wait", "fmnmf_server_result", "fmnmf_server_stats", "fmnmf_server_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -62,6 +65,18 @@ _sig = {
     "fmnmf_kernel_name": (ctypes.c_char_p, [_I]),
     "fmnmf_launch_count": (ctypes.c_longlong, [_P]),
     "fmnmf_loglik_noalloc": (_S, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "fmnmf_batch_create": (_S, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "fmnmf_batch_iterate": (_S, [_P, _I]),
+    "fmnmf_batch_sync": (_S, [_P]),
+    "fmnmf_batch_destroy": (_S, [_P]),
+    "fmnmf_footprint": (_S, [_I, _I, _I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "fmnmf_server_create": (_S, [_P, ctypes.POINTER(_P)]),
+    "fmnmf_server_submit": (_S, [_P, _P, _I, _I, _I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "fmnmf_server_poll": (_S, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_server_wait": (_S, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_I)]),
+    "fmnmf_server_result": (_S, [_P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_server_stats": (_S, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 4 + [ctypes.POINTER(ctypes.c_size_t)]),
+    "fmnmf_server_destroy": (_S, [_P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -223,3 +238,109 @@ class Context:
 
     def launch_count(self) -> int:
         return int(_lib.fmnmf_launch_count(self._ctx))
+
+
+class Batch:
+    """Several contexts iterated by one graph launch (one concurrent branch per context)."""
+
+    def __init__(self, contexts):
+        self._members = list(contexts)
+        arr = (_P * len(self._members))(*[c.handle for c in self._members])
+        self._b = _P()
+        _check(_lib.fmnmf_batch_create(arr, len(self._members), ctypes.byref(self._b)), None)
+
+    def iterate(self, n: int = 1):
+        _check(_lib.fmnmf_batch_iterate(self._b, n), None)
+
+    def sync(self):
+        _check(_lib.fmnmf_batch_sync(self._b), None)
+
+    def close(self):
+        if self._b:
+            _lib.fmnmf_batch_destroy(self._b)
+            self._b = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("iters_per_step", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+def footprint(F, T, M, N, K, precision=PREC_FP32) -> int:
+    o = default_opts()
+    o.precision = precision
+    b = ctypes.c_size_t()
+    _check(_lib.fmnmf_footprint(F, T, M, N, K, ctypes.byref(o), ctypes.byref(b)))
+    return b.value
+
+
+class Server:
+    """Continuous-batching separation server (wraps fmnmf_server)."""
+
+    def __init__(self, hbm_budget=0, max_active=16, iters_per_step=10, precision=PREC_FP32):
+        o = ServerOpts(hbm_budget, max_active, iters_per_step, precision)
+        self._s = _P()
+        _check(_lib.fmnmf_server_create(ctypes.byref(o), ctypes.byref(self._s)))
+        self._shapes = {}
+
+    def submit(self, X, N, K, n_iter, seed=0) -> int:
+        Xh, ptr = _host_ptr(X, np.complex64)
+        F, T, M = Xh.shape
+        job = ctypes.c_uint64()
+        _check(_lib.fmnmf_server_submit(self._s, ptr, F, T, M, N, K, n_iter, seed, ctypes.byref(job)))
+        self._shapes[job.value] = (N, F, T, M)
+        return job.value
+
+    def poll(self, job):
+        st, lat = _I(), ctypes.c_double()
+        _check(_lib.fmnmf_server_poll(self._s, job, ctypes.byref(st), ctypes.byref(lat)))
+        return st.value, lat.value
+
+    def wait(self, job, timeout=600.0) -> int:
+        st = _I()
+        _check(_lib.fmnmf_server_wait(self._s, job, timeout, ctypes.byref(st)))
+        return st.value
+
+    def result(self, job):
+        out = np.empty(self._shapes.pop(job), np.complex64)
+        ll = ctypes.c_double()
+        _check(_lib.fmnmf_server_result(self._s, job, out.ctypes.data, ctypes.byref(ll)))
+        return out, ll.value
+
+    def stats(self) -> dict:
+        q, a, c, f = (ctypes.c_longlong() for _ in range(4))
+        b = ctypes.c_size_t()
+        _check(_lib.fmnmf_server_stats(self._s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(c), ctypes.byref(f), ctypes.byref(b)))
+        return {"queued": q.value, "active": a.value, "completed": c.value, "failed": f.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if self._s:
+            _lib.fmnmf_server_destroy(self._s)
+            self._s = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
