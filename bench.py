@@ -455,12 +455,15 @@ def run_serving(args):
     rng = np.random.default_rng(7)
     gaps = rng.exponential(1.0 / 20.0, size=R)
     arrivals = np.cumsum(gaps) - gaps[0]
+    if args.rate > 0:
+        arrivals = arrivals * (20.0 / args.rate)
+    else:  # capacity: every request queued at once
+        arrivals = np.zeros(R)
     Ts = np.minimum(6000, np.round(np.exp(np.log(375.0) + 0.6 * rng.standard_normal(R)))).astype(int)
     Ts = np.maximum(Ts, 8)
     # mixtures: slices of a few long seeded draws (the generator's cost stays out of the loop)
     pool = [make_mixture(513, int(Ts.max()), 4, 3, 16, 2000 + i).X for i in range(4)]
     reqs = [np.ascontiguousarray(pool[i % 4][:, :T, :]) for i, T in enumerate(Ts)]
-    units = float(sum(513 * int(T) * 50 for T in Ts))
 
     def serve(max_active):
         with fm.Server(max_active=max_active, iters_per_step=10, precision=PRECISIONS[args.precision]) as srv:
@@ -471,16 +474,22 @@ def run_serving(args):
                 if arrivals[i] > now:
                     time.sleep(arrivals[i] - now)
                 ids.append(srv.submit(reqs[i], 3, 16, 50, seed=2000 + i))
-            lat = []
-            for j in ids:
+            lat, done_units, failed = [], 0.0, {}
+            for i, j in enumerate(ids):
                 srv.wait(j, 600.0)
                 st, l = srv.poll(j)
+                try:
+                    srv.result(j)
+                except fm.FastMNMFError as e:  # e.g. a very short request whose model degenerates
+                    name = fm.STATUS_NAMES.get(e.status, str(e.status))
+                    failed[name] = failed.get(name, 0) + 1
+                    continue
                 lat.append(l)
-                srv.result(j)
+                done_units += 513 * int(Ts[i]) * 50
             wall = time.perf_counter() - t0
         lat = np.array(lat)
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "throughput": units / wall, "wall_s": wall}
+                "throughput": done_units / wall, "wall_s": wall, "completed": int(len(lat)), "failed": failed}
 
     cb = serve(args.max_active)
     fifo = serve(1)
@@ -488,24 +497,27 @@ def run_serving(args):
         "metric": METRIC, "value": cb["throughput"], "unit": UNIT, "n_gpus": 1, "steps": R, "warmup": 0,
         "ms_per_step": 1e3 * cb["wall_s"] / R, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
-        "config": {"workload": f"serving: {R} requests, Poisson 20/s, M4 N3 K16 F513, T lognormal (median 375, "
+        "config": {"workload": f"serving: {R} requests, Poisson {args.rate:g}/s, M4 N3 K16 F513, T lognormal (median 375, "
                                "sigma 0.6, cap 6000), 50 iterations + Wiener each",
                    "max_active": args.max_active, "iters_per_step": 10, "precision": args.precision},
         "latency_p50_ms": cb["p50_ms"], "latency_p99_ms": cb["p99_ms"],
+        "completed": cb["completed"], "failed": cb["failed"],
         "fifo": fifo,
     }), flush=True)
 
 
-def profile_run():
-    """A short run of the same workload for ncu captures: context, 2 iterations, separation."""
+def profile_run(args):
+    """A short run of the same workload for ncu captures: context, 2 iterations, separation
+    (``--bins`` overrides F to keep the device footprint of a capture small)."""
     import torch
     from paper_1903_03237_gb300.build import build
     build()
     from paper_1903_03237_gb300 import fastmnmf as fm
     from paper_1903_03237_gb300.synth import make_mixture
     w = WORKLOAD
-    mix = make_mixture(w["F"], w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
-    with fm.Context(mix.X, w["N"], w["K"], seed=0) as ctx:
+    F = args.bins or w["F"]
+    mix = make_mixture(F, w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
+    with fm.Context(mix.X, w["N"], w["K"], seed=0, precision=PRECISIONS[args.precision]) as ctx:
         ctx.iterate(2)
         ctx.separate()
         print("profile run ok, log-likelihood", ctx.loglik())
@@ -519,17 +531,20 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu captures, no JSON line")
+    ap.add_argument("--bins", type=int, default=0, help="--profile-run: number of frequency bins (default: the workload's)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c3", "c4"], default="c1",
                     help="c1 (default, the headline line), c2 (large mixture), c3 (batched mixtures), c4 (serving)")
     ap.add_argument("--requests", type=int, default=2000, help="c4: number of requests")
     ap.add_argument("--max-active", type=int, default=16, help="c4: resident requests")
+    ap.add_argument("--rate", type=float, default=20.0,
+                    help="c4: arrival rate in requests/s (the same arrival pattern, rescaled); 0 = all at once")
     ap.add_argument("--instances", type=int, default=64, help="c3: number of mixtures")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])
     if args.profile_run:
-        profile_run()
+        profile_run(args)
     elif args.workload == "c3":
         run_batched(args)
     elif args.workload == "c4":

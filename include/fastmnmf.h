@@ -133,6 +133,10 @@ fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter);
 /* Waits for the context stream and reports any device-side error. */
 fmnmf_status fmnmf_sync(fmnmf_ctx* ctx);
 
+/* Non-blocking: FMNMF_EBUSY while work enqueued on the context stream is still running;
+ * otherwise what fmnmf_sync returns (without waiting). */
+fmnmf_status fmnmf_query(fmnmf_ctx* ctx);
+
 /* Synchronises and returns the log-likelihood of the current state: Eq. 17 including the
  * constant -F T M log(pi) that the paper's "=c" drops (the true log-density of Eq. 2). */
 fmnmf_status fmnmf_loglik(fmnmf_ctx* ctx, double* ll);
@@ -197,8 +201,10 @@ fmnmf_status fmnmf_batch_destroy(fmnmf_batch* batch);
  *  - admits queued requests in arrival order while fewer than max_active are resident
  *    and their footprint (fmnmf_footprint) fits the HBM budget; the context and state of
  *    an admitted request stay resident on the device until it completes;
- *  - advances every resident request by iters_per_step iterations per step, each on its
- *    own stream so their kernels overlap, and admits new arrivals at step boundaries;
+ *  - advances every resident request in steps of iters_per_step iterations on its own
+ *    stream, so the kernels of resident requests overlap; a request's next step is
+ *    enqueued as soon as its previous one has finished (no request waits for another's
+ *    step), and new arrivals are admitted between steps;
  *  - separates a request that has run its iterations (Eq. 3) into a host buffer, frees
  *    its device memory and marks it done.
  * A request's results equal those of a context running it alone (fmnmf_init,

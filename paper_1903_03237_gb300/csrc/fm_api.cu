@@ -243,11 +243,24 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     plan_gemm(ctx->gpW, F, K, T, 2 * N, nt_for(K), true);
     plan_gemm(ctx->gpH, T, K, F, 2 * N, nt_for(K), true);
     plan_gemm(ctx->gpL, F, T, K, N, 128, false);
+    // V_fm: bin groups x T splits.  Enough splits for two waves, then the split count (up
+    // to twice that) whose last wave is fullest; spans are whole stages.
     const int nb = (F + scm_bins_per_cta(mx) - 1) / scm_bins_per_cta(mx);
-    const int tch = (T + 31) / 32;  // chunks of 32 frames
-    int S = std::max(1, std::min(tch, (2 * sms) / nb));
-    S = std::max(S, (T + 127) / 128);  // at most 128 frames summed per TMEM accumulator
-    ctx->scmSpan = ((tch + S - 1) / S) * 32;
+    if (scm_smem(mx, N) > 227 * 1024)
+      return set_err(ctx, FMNMF_EINVAL, "N=%d is too large for the mixed-precision form (use FP32)", N);
+    CK(scm_prepare(mx, N));
+    const int kc = scm_frames_per_stage(mx);
+    const int nst = (T + kc - 1) / kc;
+    const int slots = sms * scm_occupancy(mx, N);
+    const int S0 = std::max(1, std::min(nst, (2 * slots + nb - 1) / nb));
+    int best = S0;
+    double best_fill = 0.0;
+    for (int S = S0; S <= std::min(nst, 2 * S0); ++S) {
+      const double w = (double)nb * S / slots;
+      const double fill = w / std::ceil(w);
+      if (fill > best_fill + 1e-9) { best_fill = fill; best = S; }
+    }
+    ctx->scmSpan = ((nst + best - 1) / best) * kc;
     ctx->scmS = (T + ctx->scmSpan - 1) / ctx->scmSpan;
   }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
@@ -316,8 +329,9 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
   if (ctx->opts.hbm_budget && total > ctx->opts.hbm_budget)
     return set_err(ctx, FMNMF_ENOMEM, "needs %zu bytes of device memory, budget %zu", total,
                    ctx->opts.hbm_budget);
-  cudaError_t e = cudaMalloc(&ctx->arena, total);
-  if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+  // stream-ordered: neither the allocation nor the release waits for other contexts' work
+  cudaError_t e = cudaMallocAsync(&ctx->arena, total, ctx->st);
+  if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "cudaMallocAsync(%zu): %s", total, cudaGetErrorString(e));
   ctx->arena_bytes = total;
   char* base = (char*)ctx->arena;
   for (auto& s : slots) { *s.dst = base; base += align256(s.bytes); }
@@ -457,7 +471,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     Prob q = c->p;
     q.lam = c->lam;
     // V_fm always in TF32: with BF16 operands the IP update misses the 1e-3 bar at M = 8
-    if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, true, q, c->scmS, c->scmSpan, c->st); })) != cudaSuccess)
+    if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, q, c->scmS, c->scmSpan, c->st); })) != cudaSuccess)
       return e;
     ipS = c->scmS;
   } else {
@@ -516,9 +530,9 @@ fmnmf_status snapshot(fmnmf_ctx* ctx, bool restore) {
 }
 
 fmnmf_status check_status(fmnmf_ctx* ctx) {
-  CK(cudaStreamSynchronize(ctx->st));
   unsigned st = 0;
-  CK(cudaMemcpy(&st, ctx->p.status, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&st, ctx->p.status, 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   if (st & ST_SINGULAR) return set_err(ctx, FMNMF_ESINGULAR, "singular IP system or diagonaliser (device status 0x%x)", st);
   if (st & ST_NONFINITE) return set_err(ctx, FMNMF_ENONFINITE, "non-finite value produced on the device (status 0x%x)", st);
   if (st & ST_TIMEOUT) return set_err(ctx, FMNMF_ETIMEOUT, "device wait timed out (status 0x%x)", st);
@@ -601,7 +615,10 @@ void free_ctx(fmnmf_ctx* ctx) {
   }
   for (auto& e : ctx->pending) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
   for (auto e : ctx->evpool) cudaEventDestroy(e);
-  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->arena) {
+    cudaFreeAsync(ctx->arena, ctx->st);
+    cudaStreamSynchronize(ctx->st);
+  }
   if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
   delete ctx;
 }
@@ -651,7 +668,7 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
   if (ctx->opts.stream) {
     ctx->st = (cudaStream_t)ctx->opts.stream;
   } else {
-    cudaError_t e = cudaStreamCreate(&ctx->st);
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete ctx; return set_err(nullptr, FMNMF_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
     ctx->own_stream = true;
   }
@@ -748,11 +765,20 @@ fmnmf_status fmnmf_sync(fmnmf_ctx* ctx) {
   return check_status(ctx);
 }
 
+fmnmf_status fmnmf_query(fmnmf_ctx* ctx) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  const cudaError_t e = cudaStreamQuery(ctx->st);
+  if (e == cudaErrorNotReady) return FMNMF_EBUSY;
+  if (e != cudaSuccess) return set_err(ctx, FMNMF_ECUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+  return check_status(ctx);  // the stream is idle: this does not wait
+}
+
 fmnmf_status fmnmf_loglik(fmnmf_ctx* ctx, double* ll) {
   if (!ctx || !ll) return set_err(ctx, FMNMF_EINVAL, "NULL argument");
   fmnmf_status s = check_status(ctx);
   if (s != FMNMF_OK) return s;
-  CK(cudaMemcpy(ll, ctx->p.ll, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(ll, ctx->p.ll, 8, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   return FMNMF_OK;
 }
 
@@ -788,10 +814,10 @@ fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void*
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
   CK(cudaStreamSynchronize(ctx->st));
   const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
-  if (W) CK(cudaMemcpy(W, ctx->p.W, N * K * F * 4, cudaMemcpyDeviceToHost));
-  if (H) CK(cudaMemcpy(H, ctx->p.H, N * K * T * 4, cudaMemcpyDeviceToHost));
-  if (G) CK(cudaMemcpy(G, ctx->p.G, N * F * M * 4, cudaMemcpyDeviceToHost));
-  if (Q) CK(cudaMemcpy(Q, ctx->p.Qf, F * M * M * sizeof(float2), cudaMemcpyDeviceToHost));
+  if (W) CK(cudaMemcpyAsync(W, ctx->p.W, N * K * F * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (H) CK(cudaMemcpyAsync(H, ctx->p.H, N * K * T * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (G) CK(cudaMemcpyAsync(G, ctx->p.G, N * F * M * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (Q) CK(cudaMemcpyAsync(Q, ctx->p.Qf, F * M * M * sizeof(float2), cudaMemcpyDeviceToHost, ctx->st));
   return check_status(ctx);
 }
 
@@ -812,11 +838,12 @@ fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, con
     Qx[i] = make_float4(q[2 * i], 0.f, q[2 * i + 1], 0.f);
   }
   CK(cudaStreamSynchronize(ctx->st));
-  CK(cudaMemcpy(ctx->p.W, W, N * K * F * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->p.H, H, N * K * T * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->p.G, G, N * F * M * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->p.Qx, Qx.data(), Qx.size() * sizeof(float4), cudaMemcpyHostToDevice));
-  CK(cudaMemset(ctx->p.status, 0, 4));
+  CK(cudaMemcpyAsync(ctx->p.W, W, N * K * F * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.H, H, N * K * T * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.G, G, N * F * M * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.Qx, Qx.data(), Qx.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // the host vector Qx goes out of scope
   fmnmf_status s = snapshot(ctx, false);
   if (s != FMNMF_OK) return s;
   s = refresh_state(ctx);

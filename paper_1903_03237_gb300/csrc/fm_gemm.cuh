@@ -4,9 +4,10 @@
 //
 // A and B are read from global memory (float32) through arbitrary element strides, rounded
 // to the MMA operand type and staged by the CTA's threads into shared memory in the
-// K-major core-matrix layout (fm_tc.cuh); a transposed source is therefore as cheap as a
-// contiguous one.  One CTA computes a 128 x NT tile of C (MMA M = 128, N = NT), looping
-// over its split of the K dimension in chunks of 64; two shared-memory stages let the
+// K-major core-matrix layout (k-groups outermost); a transposed source is therefore as
+// cheap as a contiguous one.  The epilogue goes through shared memory so that every store
+// instruction writes whole row segments of C.  One CTA computes a 128 x NT tile of C
+// (MMA M = 128, N = NT), looping over its split of the K dimension in chunks of 64; two shared-memory stages let the
 // threads fill one stage while the tensor core works on the other.  One thread issues the
 // MMAs and commits them to an mbarrier per stage; every wait is bounded and reports
 // ST_TIMEOUT instead of hanging.
@@ -35,6 +36,47 @@ __host__ __device__ inline int gemm_stage_bytes(int nt, bool tf32) {
   return (128 + nt) * kGemmKc * es;
 }
 
+// Stages a rows x kGemmKc tile of src(r0 + r, k0 + k) (zero outside [rlim) x [kn)) as BF16 or
+// TF32 into the K-major core-matrix layout with the 16-byte k-groups outermost: core row
+// (r, kg) at byte (kg * rows + r) * 16.  A thread builds whole 16-byte rows (8 BF16 or 4
+// TF32 values); consecutive threads take consecutive r, so the stores fill all banks.  The
+// loads are float4 when the tile rows are contiguous in k and 16-byte aligned (vec), else
+// scalar (consecutive threads then read consecutive r, which is the stride-1 index when
+// the rows are not contiguous in k).
+template <bool TF32>
+__device__ __forceinline__ void gemm_stage_tile(const float* __restrict__ src, long long sr, long long sk, int rows,
+                                                int r0, int rlim, int k0, int kn, bool vec, unsigned char* dst) {
+  constexpr int EPG = TF32 ? 4 : 8;
+  constexpr int KG = kGemmKc / EPG;
+  for (int e = threadIdx.x; e < rows * KG; e += kGemmThreads) {
+    const int r = e % rows, kg = e / rows, kk = kg * EPG;
+    const bool rok = r0 + r < rlim;
+    const float* p = src + (long long)(r0 + r) * sr + (long long)(k0 + kk) * sk;
+    float v[EPG];
+    if (rok && vec && kk + EPG <= kn) {
+#pragma unroll
+      for (int q = 0; q < EPG / 4; ++q) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p) + q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPG; ++j) v[j] = (rok && kk + j < kn) ? __ldg(p + (long long)j * sk) : 0.f;
+    }
+    uint4 o;
+    if (TF32) {
+      o = make_uint4(__float_as_uint(to_tf32(v[0])), __float_as_uint(to_tf32(v[1])), __float_as_uint(to_tf32(v[2])),
+                     __float_as_uint(to_tf32(v[3])));
+    } else {
+      const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4 % EPG], v[5 % EPG]), h3 = __floats2bfloat162_rn(v[6 % EPG], v[7 % EPG]);
+      o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
+                     *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+    }
+    *reinterpret_cast<uint4*>(dst + (kg * rows + r) * 16) = o;
+  }
+}
+
 template <int NT, bool TF32>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char gsm[];
@@ -51,6 +93,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   const int kbeg = s * g.kspan, kend = min(g.Kd, kbeg + g.kspan);
   const float* A = g.A + (long long)b * g.sAb;
   const float* B = g.B + (long long)(b % g.bmodB) * g.sBb;
+  // float4 operand loads: rows contiguous in k, row starts 16-byte aligned (k0 is a
+  // multiple of kGemmKc and the k-groups of 4)
+  const bool vecA = g.sAk == 1 && (g.sAi & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const bool vecB = g.sBk == 1 && (g.sBj & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
 
   if (warp == 0) { tmem_alloc(&tbase, TCOLS); tmem_relinquish(); }
   if (tid == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
@@ -59,7 +105,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   tc_fence_after();
   const uint32_t tacc = tbase;
   constexpr uint32_t idesc = TF32 ? idesc_tf32_f32(128, NT) : idesc_bf16_f32(128, NT);
-  constexpr uint32_t kMaxTries = 1u << 20;
+  constexpr uint32_t kMaxTries = 1u << 22;
 
   bool ok = true;
   int c = 0;
@@ -69,39 +115,19 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       if (!mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
     }
     const int kn = min(kGemmKc, kend - k0);
-    // stage A (128 x kn) and B (NT x kn): the stride-1 index runs along the lanes
-    auto stage = [&](const float* src, long long sr, long long sk, int rows, int r0, int rlim, unsigned char* dst) {
-      if (sk == 1) {
-        for (int e = tid; e < rows * kGemmKc; e += kGemmThreads) {
-          const int r = e / kGemmKc, k = e % kGemmKc;
-          float v = 0.f;
-          if (r0 + r < rlim && k < kn) v = src[(long long)(r0 + r) * sr + (k0 + k)];
-          if (TF32) *reinterpret_cast<float*>(dst + cm_offset(r, k, KB, 4)) = to_tf32(v);
-          else *reinterpret_cast<__nv_bfloat16*>(dst + cm_offset(r, k, KB, 2)) = __float2bfloat16_rn(v);
-        }
-      } else {
-        for (int e = tid; e < rows * kGemmKc; e += kGemmThreads) {
-          const int k = e / rows, r = e % rows;
-          float v = 0.f;
-          if (r0 + r < rlim && k < kn) v = src[(long long)(r0 + r) * sr + (long long)(k0 + k) * sk];
-          if (TF32) *reinterpret_cast<float*>(dst + cm_offset(r, k, KB, 4)) = to_tf32(v);
-          else *reinterpret_cast<__nv_bfloat16*>(dst + cm_offset(r, k, KB, 2)) = __float2bfloat16_rn(v);
-        }
-      }
-    };
-    stage(A, g.sAi, g.sAk, 128, i0, g.Mr, st);
-    stage(B, g.sBj, g.sBk, NT, j0, g.Nc, st + A_BYTES);
+    gemm_stage_tile<TF32>(A, g.sAi, g.sAk, 128, i0, g.Mr, k0, kn, vecA, st);
+    gemm_stage_tile<TF32>(B, g.sBj, g.sBk, NT, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
       const uint32_t sa = smem_u32(st), sb = smem_u32(st + A_BYTES);
-      constexpr int KSTEP = 32;  // bytes of K per MMA (16 BF16 or 8 TF32 elements)
+      constexpr uint32_t ALBO = 128 * 16, BLBO = NT * 16;
 #pragma unroll
-      for (int q = 0; q < KB / KSTEP; ++q) {
-        const uint64_t da = umma_desc(sa + q * 2 * 128, 128, (KB / 16) * 128);
-        const uint64_t db = umma_desc(sb + q * 2 * 128, 128, (KB / 16) * 128);
+      for (int q = 0; q < KB / 32; ++q) {  // 32 bytes of K per MMA (16 BF16 or 8 TF32)
+        const uint64_t da = umma_desc(sa + q * 2 * ALBO, ALBO, 128);
+        const uint64_t db = umma_desc(sb + q * 2 * BLBO, BLBO, 128);
         if (TF32) umma_tf32(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);
         else umma_f16(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);
       }
@@ -113,12 +139,36 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   if (ok && nchunks >= 2 && !mbar_wait(&mbar[(nchunks - 2) & 1], (uint32_t)(((nchunks - 2) >> 1) & 1), kMaxTries)) ok = false;
   if (ok && nchunks >= 1 && !mbar_wait(&mbar[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1), kMaxTries)) ok = false;
   tc_fence_after();
+  float* Cb = g.C + (long long)s * g.sCs + (long long)b * g.sCb;
   if (!ok) {
     if (lane == 0) atomicOr(g.status, ST_TIMEOUT);
+  } else if (nchunks > 0 && g.sCj == 1) {
+    // epilogue through shared memory (free: every MMA has completed): warp w holds rows
+    // 32w..32w+31 of the tile; it writes CW columns of its 32 rows at a time, each store
+    // instruction covering whole row segments (each warp uses its own scratch rows)
+    constexpr int CW = NT < 32 ? NT : 32;
+    constexpr int RPI = 32 / CW;  // rows per store instruction
+    float* scr = reinterpret_cast<float*>(gsm) + warp * (32 * 33);
+    const int lc = lane % CW, lr = lane / CW;
+#pragma unroll 1
+    for (int cc = 0; cc < NT; cc += CW) {
+      float v[CW];
+      tmem_ld16(tacc + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc, v);
+      if (CW == 32) tmem_ld16(tacc + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc + 16), v + (CW == 32 ? 16 : 0));
+#pragma unroll
+      for (int q = 0; q < CW; ++q) scr[lane * 33 + q] = v[q];
+      __syncwarp();
+      const int j = j0 + cc + lc;
+#pragma unroll 4
+      for (int rr = lr; rr < 32; rr += RPI) {
+        const int i = i0 + 32 * warp + rr;
+        if (i < g.Mr && j < g.Nc) Cb[(long long)i * g.sCi + j] = scr[rr * 33 + lc];
+      }
+      __syncwarp();
+    }
   } else if (nchunks > 0) {
     // epilogue: warp w holds rows 32w..32w+31 of the tile
     const int i = i0 + 32 * warp + lane;
-    float* Cb = g.C + (long long)s * g.sCs + (long long)b * g.sCb;
 #pragma unroll
     for (int cc = 0; cc < NT; cc += 16) {
       float v[16];
@@ -134,7 +184,6 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   } else {
     // empty split: zero output
     const int i = i0 + 32 * warp + lane;
-    float* Cb = g.C + (long long)s * g.sCs + (long long)b * g.sCb;
     if (i < g.Mr)
       for (int j = j0; j < min(g.Nc, j0 + NT); ++j) Cb[(long long)i * g.sCi + (long long)j * g.sCj] = 0.f;
   }

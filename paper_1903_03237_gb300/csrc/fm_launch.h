@@ -56,8 +56,12 @@ cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStr
 cudaError_t configure_gemm();
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st);
 // V_fm split sums on the tensor cores (and y~), grid (ceil(F / bins per CTA), S).
-cudaError_t launch_scm_tc(int maxm, bool tf32, const Prob& p, int S, int span, cudaStream_t st);
+cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, cudaStream_t st);
 int scm_bins_per_cta(int maxm);
+int scm_frames_per_stage(int maxm);
+int scm_smem(int maxm, int N);             // dynamic shared memory of k_scm_tc for N sources
+cudaError_t scm_prepare(int maxm, int N);  // allow that much shared memory
+int scm_occupancy(int maxm, int N);        // resident k_scm_tc CTAs per SM
 cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
                          cudaStream_t st);
 

@@ -11,6 +11,8 @@
 // sweeps; the IP, x~, log-likelihood and normalisation are those of the plain form.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "fm_gemm.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
@@ -110,27 +112,39 @@ cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStr
   }
 }
 
-template <int MAXM, bool TF32>
+template <int MAXM>
 static cudaError_t scm_launch(const Prob& p, int S, int span, cudaStream_t st) {
-  using C = ScmCfg<MAXM, TF32>;
+  using C = ScmCfg<MAXM>;
   const dim3 grid((p.F + C::FG - 1) / C::FG, S);
-  k_scm_tc<MAXM, TF32><<<grid, kScmThreads, C::SMEM, st>>>(p, S, span);
+  if (p.M == MAXM) k_scm_tc<MAXM, true><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span);
+  else k_scm_tc<MAXM, false><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span);
   return cudaGetLastError();
 }
-template <int MAXM, bool TF32>
-static cudaError_t scm_configure() {
-  return cudaFuncSetAttribute(k_scm_tc<MAXM, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              ScmCfg<MAXM, TF32>::SMEM);
+// The kernel's shared memory grows with N (lambda rows and g~ staged per bin): raise the
+// function's limit to what this N needs (never lower it: contexts share the function).
+template <int MAXM>
+static cudaError_t scm_configure(int N) {
+  static std::mutex mu;
+  static int configured = 0;
+  const int need = ScmCfg<MAXM>::smem(N);
+  std::lock_guard<std::mutex> lk(mu);
+  if (need <= configured) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_scm_tc<MAXM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_scm_tc<MAXM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  if (e == cudaSuccess) configured = need;
+  return e;
+}
+template <int MAXM>
+static int scm_occ(int N) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scm_tc<MAXM, true>, kScmThreads + 32, ScmCfg<MAXM>::smem(N)) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
 }
 
 cudaError_t configure_gemm() {
   cudaError_t e;
-  if ((e = scm_configure<2, false>()) != cudaSuccess) return e;
-  if ((e = scm_configure<4, false>()) != cudaSuccess) return e;
-  if ((e = scm_configure<8, false>()) != cudaSuccess) return e;
-  if ((e = scm_configure<2, true>()) != cudaSuccess) return e;
-  if ((e = scm_configure<4, true>()) != cudaSuccess) return e;
-  if ((e = scm_configure<8, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<16, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<32, true>()) != cudaSuccess) return e;
   if ((e = gemm_configure<64, true>()) != cudaSuccess) return e;
@@ -141,18 +155,21 @@ cudaError_t configure_gemm() {
   return gemm_configure<128, false>();
 }
 
-cudaError_t launch_scm_tc(int maxm, bool tf32, const Prob& p, int S, int span, cudaStream_t st) {
-  if (tf32) {
-    if (maxm == 2) return scm_launch<2, true>(p, S, span, st);
-    if (maxm == 4) return scm_launch<4, true>(p, S, span, st);
-    return scm_launch<8, true>(p, S, span, st);
-  }
-  if (maxm == 2) return scm_launch<2, false>(p, S, span, st);
-  if (maxm == 4) return scm_launch<4, false>(p, S, span, st);
-  return scm_launch<8, false>(p, S, span, st);
+cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, cudaStream_t st) {
+  if (maxm == 2) return scm_launch<2>(p, S, span, st);
+  if (maxm == 4) return scm_launch<4>(p, S, span, st);
+  return scm_launch<8>(p, S, span, st);
 }
 
 int scm_bins_per_cta(int maxm) { return 128 / (maxm * maxm); }
+int scm_frames_per_stage(int maxm) { return maxm == 2 ? ScmCfg<2>::KC : maxm == 4 ? ScmCfg<4>::KC : ScmCfg<8>::KC; }
+int scm_smem(int maxm, int N) {
+  return maxm == 2 ? ScmCfg<2>::smem(N) : maxm == 4 ? ScmCfg<4>::smem(N) : ScmCfg<8>::smem(N);
+}
+cudaError_t scm_prepare(int maxm, int N) {
+  return maxm == 2 ? scm_configure<2>(N) : maxm == 4 ? scm_configure<4>(N) : scm_configure<8>(N);
+}
+int scm_occupancy(int maxm, int N) { return maxm == 2 ? scm_occ<2>(N) : maxm == 4 ? scm_occ<4>(N) : scm_occ<8>(N); }
 
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st) {
   const unsigned npts = (unsigned)p.F * (unsigned)p.T;

@@ -4,10 +4,11 @@
 // A scheduler thread admits queued requests in arrival order while a slot is free and
 // their device footprint (fmnmf_footprint: the context arena plus the Wiener output) fits
 // the server's HBM budget, and keeps every admitted request's state resident in its own
-// context (and stream).  It then advances all admitted requests in steps of
-// iters_per_step iterations: each step enqueues every active request's iterations on its
-// stream, so their kernels overlap on the device, and waits for them; requests that
-// arrived meanwhile join at the next step boundary.  A request that has run its
+// context (and stream).  Each admitted request advances in steps of iters_per_step
+// iterations on its own stream, so the kernels of resident requests overlap on the
+// device; the scheduler polls the streams (fmnmf_query) and enqueues a request's next
+// step as soon as its previous one has finished, so no request waits for another's step,
+// and requests that arrived meanwhile are admitted between polls.  A request that has run its
 // iterations is separated (Eq. 3) into a host buffer, its context is destroyed, and its
 // memory returns to the budget.  Each request computes exactly what a context running it
 // alone computes: the kernels and their reduction orders do not depend on the mix.
@@ -44,6 +45,7 @@ struct Job {
   fmnmf_status status = FMNMF_OK;
   std::string err;
   int iters_done = 0;
+  int pending = 0;          // iterations of the step in flight
   size_t bytes = 0;
   fmnmf_ctx* ctx = nullptr;
   Clock::time_point t_submit, t_done;
@@ -89,14 +91,45 @@ struct fmnmf_server {
     done_cv.notify_all();
   }
 
+  void fail(Job* j, fmnmf_status st) {
+    std::string msg = fmnmf_last_error(j->ctx);
+    fmnmf_destroy(j->ctx);
+    j->ctx = nullptr;
+    finish(j, FMNMF_JOB_FAILED, st, msg);
+  }
+
+  // Enqueues the next step of j on its stream (asynchronous).
+  void launch_step(Job* j) {
+    const int k = std::min(o.iters_per_step, j->n_iter - j->iters_done);
+    j->pending = k;
+    fmnmf_status st = k > 0 ? fmnmf_iterate(j->ctx, k) : FMNMF_OK;
+    if (st != FMNMF_OK) fail(j, st);
+  }
+
+  // The step of j has finished: account for it, and either separate and retire the
+  // request or enqueue its next step.
+  void step_done(Job* j, fmnmf_status st) {
+    if (st != FMNMF_OK) { fail(j, st); return; }
+    j->iters_done += j->pending;
+    j->pending = 0;
+    if (j->iters_done < j->n_iter) { launch_step(j); return; }
+    j->out.resize((size_t)2 * j->N * j->F * j->T * j->M);
+    st = fmnmf_separate(j->ctx, j->out.data(), 0);
+    if (st == FMNMF_OK) st = fmnmf_loglik(j->ctx, &j->ll);
+    if (st != FMNMF_OK) { fail(j, st); return; }
+    fmnmf_destroy(j->ctx);
+    j->ctx = nullptr;
+    finish(j, FMNMF_JOB_DONE, FMNMF_OK, "");
+  }
+
   void run() {
     cudaSetDevice(device);
     for (;;) {
-      std::vector<Job*> admit;
-      std::vector<Job*> step;
+      std::vector<Job*> admit, live;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop || !queue.empty() || !active.empty(); });
+        if (active.empty())
+          cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop || !queue.empty(); });
         if (stop && active.empty()) break;
         while (!stop && !queue.empty() && (int)(active.size() + admit.size()) < o.max_active) {
           Job* j = jobs[queue.front()].get();
@@ -117,45 +150,28 @@ struct fmnmf_server {
           continue;
         }
         std::vector<float>().swap(j->X);
-        std::lock_guard<std::mutex> lk(mu);
-        j->state = FMNMF_JOB_RUNNING;
-        active.push_back(j);
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          j->state = FMNMF_JOB_RUNNING;
+          active.push_back(j);
+        }
+        launch_step(j);
       }
       {
         std::lock_guard<std::mutex> lk(mu);
-        step = active;
+        live = active;
       }
-      if (step.empty()) continue;
-      // one step for every admitted request, each on its own stream: their work overlaps
-      std::vector<fmnmf_status> enq(step.size(), FMNMF_OK);
-      for (size_t i = 0; i < step.size(); ++i) {
-        Job* j = step[i];
-        const int k = std::min(o.iters_per_step, j->n_iter - j->iters_done);
-        if (k > 0) {
-          enq[i] = fmnmf_iterate(j->ctx, k);
-          if (enq[i] == FMNMF_OK) j->iters_done += k;
-        }
+      bool progressed = !admit.empty();
+      for (Job* j : live) {
+        const fmnmf_status st = fmnmf_query(j->ctx);
+        if (st == FMNMF_EBUSY) continue;
+        progressed = true;
+        step_done(j, st);
       }
-      for (size_t i = 0; i < step.size(); ++i) {
-        Job* j = step[i];
-        fmnmf_status st = fmnmf_sync(j->ctx);
-        if (st == FMNMF_OK) st = enq[i];
-        if (st != FMNMF_OK) {
-          std::string msg = fmnmf_last_error(j->ctx);
-          fmnmf_destroy(j->ctx);
-          j->ctx = nullptr;
-          finish(j, FMNMF_JOB_FAILED, st, msg);
-          continue;
-        }
-        if (j->iters_done >= j->n_iter) {
-          j->out.resize((size_t)2 * j->N * j->F * j->T * j->M);
-          st = fmnmf_separate(j->ctx, j->out.data(), 0);
-          if (st == FMNMF_OK) st = fmnmf_loglik(j->ctx, &j->ll);
-          std::string msg = st == FMNMF_OK ? "" : fmnmf_last_error(j->ctx);
-          fmnmf_destroy(j->ctx);
-          j->ctx = nullptr;
-          finish(j, st == FMNMF_OK ? FMNMF_JOB_DONE : FMNMF_JOB_FAILED, st, msg);
-        }
+      if (!progressed) {
+        // nothing finished: sleep briefly unless a request arrives
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait_for(lk, std::chrono::microseconds(50), [&] { return stop || !queue.empty(); });
       }
     }
   }

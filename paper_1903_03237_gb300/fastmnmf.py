@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
 
 # every symbol include/fastmnmf.h declares
 EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "fmnmf_iterate", "fmnmf_sync",
+           "fmnmf_query",
            "fmnmf_loglik", "fmnmf_separate", "fmnmf_get_state", "fmnmf_set_state", "fmnmf_shape",
            "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
            "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc",
@@ -53,6 +54,7 @@ _sig = {
     "fmnmf_restart": (_S, [_P]),
     "fmnmf_iterate": (_S, [_P, _I]),
     "fmnmf_sync": (_S, [_P]),
+    "fmnmf_query": (_S, [_P]),
     "fmnmf_loglik": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
     "fmnmf_separate": (_S, [_P, _P, _I]),
     "fmnmf_get_state": (_S, [_P, _P, _P, _P, _P]),
@@ -178,6 +180,14 @@ class Context:
 
     def sync(self):
         _check(_lib.fmnmf_sync(self._ctx), self._ctx)
+
+    def busy(self) -> bool:
+        """True while work enqueued on the context stream is still running (non-blocking)."""
+        st = _lib.fmnmf_query(self._ctx)
+        if st == EBUSY:
+            return True
+        _check(st, self._ctx)
+        return False
 
     def loglik(self) -> float:
         v = ctypes.c_double()

@@ -50,7 +50,10 @@ def _mixed_errors(fm, F, T, M, N, K, precision, seed=1, diffuse=0.0):
             "separated_max": maxrel(S, Sr)}
 
 
-SHAPES = [(37, 150, 3, 3, 5), (70, 260, 4, 4, 32), (33, 200, 8, 6, 20), (40, 90, 2, 2, 8)]
+# (29, 151, 3): T*M odd, so the X rows are not 16-byte aligned and load without TMA;
+# (21, 77, 5) the same in the 8-channel bucket; (40, 700, 2) spans several TMEM blocks
+SHAPES = [(37, 150, 3, 3, 5), (70, 260, 4, 4, 32), (33, 200, 8, 6, 20), (40, 90, 2, 2, 8),
+          (29, 151, 3, 2, 6), (21, 77, 5, 3, 7), (40, 700, 2, 2, 8)]
 
 
 @pytest.mark.parametrize("precision", ["bf16", "tf32"])
