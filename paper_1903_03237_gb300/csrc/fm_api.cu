@@ -74,6 +74,7 @@ struct fmnmf_ctx {
   float* Cg = nullptr;    // split GEMM sums
   GemmPlan gpW, gpH, gpL;
   int scmS = 1, scmSpan = 64;  // tensor-core V_fm: T splits and frames per split
+  int gtcNP = 0, gtcS = 1, gtcSpan = 16;  // tensor-core g~ update (NP = 0: the CUDA-core sweep)
   int sms = 0;
   std::map<std::pair<int, unsigned>, GraphEntry> graphs;  // (chunk, timing mask) -> graph
   std::string err;
@@ -173,10 +174,12 @@ size_t smem_bytes(int mode, int N, int K, int M, int maxm, int ic, bool lam_mem 
   return b;
 }
 
-size_t sep_smem_bytes(int N, int K, int M, int maxm, int ic) {
+// k_separate: Q and Q^-1 of the tile's bins, g~; unless lambda is read from memory, the W
+// tile, an H chunk and the lambda chunk.
+size_t sep_smem_bytes(int N, int K, int M, int maxm, int ic, bool lam_mem = false) {
   const int NK = N * K, ICP = ic + 4;
-  size_t fl = (size_t)NK * kOT + (size_t)NK * ICP + (((size_t)N * kOT * M + 3) & ~(size_t)3) +
-              (size_t)N * kOT * ICP;
+  size_t fl = (((size_t)N * kOT * M + 3) & ~(size_t)3);
+  if (!lam_mem) fl += (size_t)NK * kOT + (size_t)NK * ICP + (size_t)N * kOT * ICP;
   return fl * 4 + 2 * (size_t)kOT * maxm * maxm * sizeof(float2);
 }
 
@@ -210,17 +213,19 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   ctx->smH = smem_bytes(MODE_H, N, K, M, mx, ctx->gH.IC);
   ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC, lm(MODE_G));
   ctx->smY = smem_bytes(MODE_Y, N, K, M, mx, ctx->gY.IC, lm(MODE_Y));
+  // the Wiener filter reads the materialised lambda in the mixed form
+  const bool sep_lm = ctx->mixed;
   int sep_cap = 0;
   for (int ic = 256; ic >= 4; ic -= 4)
-    if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemTarget) { sep_cap = ic; break; }
+    if (sep_smem_bytes(N, K, M, mx, ic, sep_lm) <= (size_t)kSmemTarget) { sep_cap = ic; break; }
   if (sep_cap == 0)
     for (int ic = 256; ic >= 4; ic -= 4)
-      if (sep_smem_bytes(N, K, M, mx, ic) <= (size_t)kSmemMax) { sep_cap = ic; break; }
+      if (sep_smem_bytes(N, K, M, mx, ic, sep_lm) <= (size_t)kSmemMax) { sep_cap = ic; break; }
   if (sep_cap == 0) return set_err(ctx, FMNMF_EINVAL, "N*K too large for the Wiener tiles");
-  mx_cap_smem = std::max(mx_cap_smem, sep_smem_bytes(N, K, M, mx, sep_cap));
+  mx_cap_smem = std::max(mx_cap_smem, sep_smem_bytes(N, K, M, mx, sep_cap, sep_lm));
   CK(configure(mx, (int)mx_cap_smem));
-  ctx->gS = make_geom(F, T, sep_cap, sms * occupancy(mx, KK_SEP, sep_smem_bytes(N, K, M, mx, sep_cap)));
-  ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC);
+  ctx->gS = make_geom(F, T, sep_cap, sms * occupancy(mx, KK_SEP, sep_smem_bytes(N, K, M, mx, sep_cap, sep_lm)));
+  ctx->smS = sep_smem_bytes(N, K, M, mx, ctx->gS.IC, sep_lm);
   ctx->sms = sms;
   if (ctx->mixed) {
     CK(configure_gemm());
@@ -262,6 +267,27 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     }
     ctx->scmSpan = ((nst + best - 1) / best) * kc;
     ctx->scmS = (T + ctx->scmSpan - 1) / ctx->scmSpan;
+    // g~ update: the same split choice for its bin groups
+    ctx->gtcNP = gtc_np(mx, N);
+    if (ctx->gtcNP > 0 && gtc_smem(mx, ctx->gtcNP, N) <= 227 * 1024) {
+      CK(gtc_prepare(mx, ctx->gtcNP, N));
+      const int gnb = (F + gtc_bins_per_cta(mx) - 1) / gtc_bins_per_cta(mx);
+      const int gkc = gtc_frames_per_stage();
+      const int gst = (T + gkc - 1) / gkc;
+      const int gslots = sms * gtc_occupancy(mx, ctx->gtcNP, N);
+      const int G0 = std::max(1, std::min(gst, (2 * gslots + gnb - 1) / gnb));
+      int gbest = G0;
+      double gfill = 0.0;
+      for (int S = G0; S <= std::min(gst, 2 * G0); ++S) {
+        const double w = (double)gnb * S / gslots;
+        const double fill = w / std::ceil(w);
+        if (fill > gfill + 1e-9) { gfill = fill; gbest = S; }
+      }
+      ctx->gtcSpan = ((gst + gbest - 1) / gbest) * gkc;
+      ctx->gtcS = (T + ctx->gtcSpan - 1) / ctx->gtcSpan;
+    } else {
+      ctx->gtcNP = 0;
+    }
   }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
@@ -280,6 +306,7 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
   part = std::max(part, (size_t)ctx->gG.S * tile_part_floats(MODE_G, F, T, M, N, K, mx));
   part = std::max(part, (size_t)ctx->gY.S * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   if (ctx->mixed) part = std::max(part, (size_t)ctx->scmS * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
+  if (ctx->mixed && ctx->gtcNP > 0) part = std::max(part, (size_t)ctx->gtcS * tile_part_floats(MODE_G, F, T, M, N, K, mx));
   const unsigned nctr = ctx->gW.n_own_tiles + ctx->gH.n_own_tiles + ctx->gG.n_own_tiles +
                         ctx->gY.n_own_tiles + 1;
   ctx->ctrW = 0;
@@ -460,9 +487,19 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
   }
   if ((e = gemm(KK_GL, c->gpL)) != cudaSuccess) return e;
   if (mask & FMNMF_UPDATE_G) {
-    LaunchArgs a = tile_args(c, c->gG, c->smG, FLAG_UPDATE | FLAG_LAM_MEM, c->ctrG);
-    a.p.lam = c->lam;
-    if ((e = rec.run(KK_G, a)) != cudaSuccess) return e;
+    if (c->gtcNP > 0) {
+      Prob q = c->p;
+      q.lam = c->lam;
+      if ((e = rec.run_fn(KK_G, [&] {
+             c->launches++;
+             return launch_g_tc(c->maxm, c->gtcNP, q, c->gtcS, c->gtcSpan, c->ctrG, c->st);
+           })) != cudaSuccess)
+        return e;
+    } else {
+      LaunchArgs a = tile_args(c, c->gG, c->smG, FLAG_UPDATE | FLAG_LAM_MEM, c->ctrG);
+      a.p.lam = c->lam;
+      if ((e = rec.run(KK_G, a)) != cudaSuccess) return e;
+    }
   }
   const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
   int ipS = c->gY.S;
@@ -470,7 +507,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     // y~ and the V_fm split sums on the tensor cores
     Prob q = c->p;
     q.lam = c->lam;
-    // V_fm always in TF32: with BF16 operands the IP update misses the 1e-3 bar at M = 8
+    // V_fm in split BF16 in either mixed form: single BF16 or TF32 operands miss the 1e-3 bar
     if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, q, c->scmS, c->scmSpan, c->st); })) != cudaSuccess)
       return e;
     ipS = c->scmS;
@@ -796,6 +833,19 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
   Recorder rec{ctx, ctx->timing ? &ctx->pending : nullptr};
   LaunchArgs a;
   a.p = ctx->p; a.g = ctx->gS; a.smem = ctx->smS; a.st = ctx->st; a.out = dst;
+  if (ctx->mixed) {
+    // lambda of the current W and H (the normalisation rescaled W after the last GEMM),
+    // with TF32 operands in either mixed form: the images scale with lambda directly
+    cudaError_t el = rec.run_fn(KK_GL, [&] {
+      ctx->launches++;
+      return launch_gemm(ctx->gpL.g, true, ctx->gpL.nt, ctx->gpL.grid, ctx->st);
+    });
+    if (el != cudaSuccess) {
+      if (tmp) cudaFreeAsync(tmp, ctx->st);
+      return set_err(ctx, FMNMF_ECUDA, "lambda GEMM launch: %s", cudaGetErrorString(el));
+    }
+    a.p.lam = ctx->lam;
+  }
   a.grid = dim3(ctx->gS.n_own_tiles, ctx->gS.S);
   cudaError_t e = rec.run(KK_SEP, a);
   if (e != cudaSuccess) {

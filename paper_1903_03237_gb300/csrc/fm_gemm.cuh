@@ -42,38 +42,54 @@ __host__ __device__ inline int gemm_stage_bytes(int nt, bool tf32) {
 // TF32 values); consecutive threads take consecutive r, so the stores fill all banks.  The
 // loads are float4 when the tile rows are contiguous in k and 16-byte aligned (vec), else
 // scalar (consecutive threads then read consecutive r, which is the stride-1 index when
-// the rows are not contiguous in k).
-template <bool TF32>
-__device__ __forceinline__ void gemm_stage_tile(const float* __restrict__ src, long long sr, long long sk, int rows,
-                                                int r0, int rlim, int k0, int kn, bool vec, unsigned char* dst) {
+// the rows are not contiguous in k).  A thread issues the loads of up to 8 rows before
+// converting and storing any of them, so that many loads are in flight.
+template <bool TF32, int ROWS>
+__device__ __forceinline__ void gemm_stage_tile(const float* __restrict__ src, long long sr, long long sk, int r0,
+                                                int rlim, int k0, int kn, bool vec, unsigned char* dst) {
   constexpr int EPG = TF32 ? 4 : 8;
   constexpr int KG = kGemmKc / EPG;
-  for (int e = threadIdx.x; e < rows * KG; e += kGemmThreads) {
-    const int r = e % rows, kg = e / rows, kk = kg * EPG;
-    const bool rok = r0 + r < rlim;
-    const float* p = src + (long long)(r0 + r) * sr + (long long)(k0 + kk) * sk;
-    float v[EPG];
-    if (rok && vec && kk + EPG <= kn) {
+  constexpr int ITEMS = ROWS * KG / kGemmThreads;  // 16-byte rows per thread
+  constexpr int BATCH = ITEMS < 8 ? ITEMS : 8;     // loads issued together (in flight at once)
+  static_assert(ITEMS * kGemmThreads == ROWS * KG, "whole rows per thread");
+#pragma unroll 1
+  for (int i0 = 0; i0 < ITEMS; i0 += BATCH) {
+    float v[BATCH][EPG];
 #pragma unroll
-      for (int q = 0; q < EPG / 4; ++q) {
-        const float4 x = __ldg(reinterpret_cast<const float4*>(p) + q);
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    for (int u = 0; u < BATCH; ++u) {
+      const int e = (i0 + u) * kGemmThreads + threadIdx.x;
+      const int r = e % ROWS, kk = (e / ROWS) * EPG;
+      const bool rok = r0 + r < rlim;
+      const float* p = src + (long long)(r0 + r) * sr + (long long)(k0 + kk) * sk;
+      if (rok && vec && kk + EPG <= kn) {
+#pragma unroll
+        for (int q = 0; q < EPG / 4; ++q) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(p) + q);
+          v[u][4 * q] = x.x; v[u][4 * q + 1] = x.y; v[u][4 * q + 2] = x.z; v[u][4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < EPG; ++j) v[u][j] = (rok && kk + j < kn) ? __ldg(p + (long long)j * sk) : 0.f;
       }
-    } else {
+    }
 #pragma unroll
-      for (int j = 0; j < EPG; ++j) v[j] = (rok && kk + j < kn) ? __ldg(p + (long long)j * sk) : 0.f;
+    for (int u = 0; u < BATCH; ++u) {
+      const int e = (i0 + u) * kGemmThreads + threadIdx.x;
+      const int r = e % ROWS, kg = e / ROWS;
+      uint4 o;
+      if (TF32) {
+        o = make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
+                       __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
+      } else {
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]);
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4 % EPG], v[u][5 % EPG]);
+        const __nv_bfloat162 h3 = __floats2bfloat162_rn(v[u][6 % EPG], v[u][7 % EPG]);
+        o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
+                       *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+      }
+      *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = o;
     }
-    uint4 o;
-    if (TF32) {
-      o = make_uint4(__float_as_uint(to_tf32(v[0])), __float_as_uint(to_tf32(v[1])), __float_as_uint(to_tf32(v[2])),
-                     __float_as_uint(to_tf32(v[3])));
-    } else {
-      const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4 % EPG], v[5 % EPG]), h3 = __floats2bfloat162_rn(v[6 % EPG], v[7 % EPG]);
-      o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
-                     *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
-    }
-    *reinterpret_cast<uint4*>(dst + (kg * rows + r) * 16) = o;
   }
 }
 
@@ -115,8 +131,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       if (!mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
     }
     const int kn = min(kGemmKc, kend - k0);
-    gemm_stage_tile<TF32>(A, g.sAi, g.sAk, 128, i0, g.Mr, k0, kn, vecA, st);
-    gemm_stage_tile<TF32>(B, g.sBj, g.sBk, NT, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
+    gemm_stage_tile<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, st);
+    gemm_stage_tile<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();

@@ -900,20 +900,59 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
   const int M = p.M, T = p.T, F = p.F;
   if ((int)blockIdx.x < n_pt_blocks) {
     const unsigned npts = (unsigned)F * (unsigned)T;  // < 2^31 (checked at init)
+    const unsigned pt0 = blockIdx.x * (unsigned)(kThreads * kPtsPerThread);
+    const unsigned pt_end = min(npts, pt0 + (unsigned)(kThreads * kPtsPerThread));
+    // Q_f (and phi_f) of the block's bins in shared memory when they fit: the per-point
+    // loads then go to the shared-memory pipe instead of the global load queue
+    constexpr int kQs = 2048;
+    __shared__ float2 qs[kQs];
+    __shared__ float phs[kQs / 4];
+    const int fa = (int)(pt0 / (unsigned)T), nfb = (int)((pt_end - 1) / (unsigned)T) - fa + 1;
+    const bool q_smem = nfb * M * M <= kQs && nfb <= kQs / 4;
+    if (q_smem) {
+      for (int e = tid; e < nfb * M * M; e += kThreads) qs[e] = __ldg(p.Qf + (size_t)fa * M * M + e);
+      for (int e = tid; e < nfb; e += kThreads) phs[e] = apply_phi ? __ldg(p.phi + fa + e) : 1.f;
+    }
+    __syncthreads();
+    const bool exact = (M == MAXM);  // vector loads and stores of whole points
     float part = 0.f;
     for (int r = 0; r < kPtsPerThread; ++r) {
-      const unsigned pt = blockIdx.x * (unsigned)(kThreads * kPtsPerThread) + (unsigned)(r * kThreads + tid);
-      if (pt >= npts) break;
+      const unsigned pt = pt0 + (unsigned)(r * kThreads + tid);
+      if (pt >= pt_end) break;
       const int f = (int)(pt / (unsigned)T);
       const float2* xp = p.X + (size_t)pt * M;
-      const float2* qp = p.Qf + (size_t)f * M * M;
+      const float2* qp = q_smem ? qs + (f - fa) * M * M : p.Qf + (size_t)f * M * M;
       float2 x[MAXM];
+      float yv[MAXM], xv[MAXM];
+      if (exact) {
 #pragma unroll
-      for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? xp[j] : make_float2(0.f, 0.f);
-      const float ph = apply_phi ? p.phi[f] : 1.f;
+        for (int q = 0; q < MAXM / 2; ++q) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(xp) + q);
+          x[2 * q] = make_float2(v.x, v.y);
+          x[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if (MAXM % 4 == 0) {
+#pragma unroll
+          for (int q = 0; q < MAXM / 4; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(p.yt + (size_t)pt * MAXM + 4 * q);
+            yv[4 * q] = v.x; yv[4 * q + 1] = v.y; yv[4 * q + 2] = v.z; yv[4 * q + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) yv[m] = p.yt[(size_t)pt * MAXM + m];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+          x[j] = (j < M) ? __ldg(xp + j) : make_float2(0.f, 0.f);
+          yv[j] = (j < M) ? p.yt[(size_t)pt * M + j] : 1.f;
+        }
+      }
+      const float ph = q_smem ? phs[f - fa] : (apply_phi ? p.phi[f] : 1.f);
       float ls = 0.f;
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
+        xv[m] = 0.f;
         if (m < M) {
           float re = 0.f, im = 0.f;
 #pragma unroll
@@ -924,12 +963,27 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
               im = fmaf(q.x, x[j].y, fmaf(q.y, x[j].x, im));
             }
           }
-          const float xv = re * re + im * im;
-          float yv = p.yt[(size_t)pt * M + m];
-          if (apply_phi) { yv = yv / ph; p.yt[(size_t)pt * M + m] = yv; }
-          p.xt[(size_t)pt * M + m] = xv;
-          ls += -xv / yv - logf(yv);
+          xv[m] = re * re + im * im;
+          if (apply_phi) yv[m] = yv[m] / ph;
+          ls += -xv[m] / yv[m] - logf(yv[m]);
         }
+      }
+      if (exact && MAXM % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < MAXM / 4; ++q) {
+          *reinterpret_cast<float4*>(p.xt + (size_t)pt * MAXM + 4 * q) =
+              make_float4(xv[4 * q], xv[4 * q + 1], xv[4 * q + 2], xv[4 * q + 3]);
+          if (apply_phi)
+            *reinterpret_cast<float4*>(p.yt + (size_t)pt * MAXM + 4 * q) =
+                make_float4(yv[4 * q], yv[4 * q + 1], yv[4 * q + 2], yv[4 * q + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) {
+            p.xt[(size_t)pt * M + m] = xv[m];
+            if (apply_phi) p.yt[(size_t)pt * M + m] = yv[m];
+          }
       }
       part += ls;
     }
@@ -1047,51 +1101,58 @@ __global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* _
   const int i_begin = blockIdx.y * g.span;
   const int i_end = min(T, i_begin + g.span);
   const int IC = g.IC, ICP = g.ICP;
-  float* own_s = sm;                       // [NK][kOT]
-  float* oth_s = own_s + NK * kOT;         // [NK][ICP]
-  float* g_s = oth_s + NK * ICP;           // [N][kOT][M]
-  float* lam_s = g_s + ((N * kOT * M + 3) & ~3);   // [N][kOT][ICP]
-  float2* q_s = reinterpret_cast<float2*>(lam_s + N * kOT * ICP);   // [kOT][M*M]
-  float2* qi_s = q_s + kOT * MAXM * MAXM;                            // [kOT][M*M]
+  // lambda materialised (mixed form): read per point instead of formed from W and H tiles
+  const bool lam_mem = p.lam != nullptr;
+  const int MM = MAXM * MAXM;
+  float2* q_s = reinterpret_cast<float2*>(sm);   // [kOT][MAXM*MAXM] (rows padded to MAXM)
+  float2* qi_s = q_s + kOT * MM;                  // [kOT][MAXM*MAXM]
+  float* g_s = reinterpret_cast<float*>(qi_s + kOT * MM);   // [N][kOT][M]
+  float* own_s = g_s + ((N * kOT * M + 3) & ~3);  // [NK][kOT]        (W, H tiles: not lam_mem)
+  float* oth_s = own_s + NK * kOT;                 // [NK][ICP]
+  float* lam_s = oth_s + NK * ICP;                 // [N][kOT][ICP]
 
-  for (int e = tid; e < NK * kOT; e += kThreads) {
-    const int nk = e / kOT, o = e % kOT;
-    own_s[e] = (o < n_own) ? p.W[(size_t)nk * F + o_base + o] : 0.f;
-  }
   for (int e = tid; e < N * kOT * M; e += kThreads) {
     const int n = e / (kOT * M), o = (e / M) % kOT, m = e % M;
     g_s[e] = (o < n_own) ? p.G[((size_t)n * F + o_base + o) * M + m] : 0.f;
   }
-  for (int e = tid; e < kOT * M * M; e += kThreads) {
-    const int o = e / (M * M);
-    q_s[e] = (o < n_own) ? p.Qf[(size_t)o_base * M * M + e] : make_float2(0.f, 0.f);
-    qi_s[e] = (o < n_own) ? p.Qinv[(size_t)o_base * M * M + e] : make_float2(0.f, 0.f);
+  for (int e = tid; e < kOT * MM; e += kThreads) {
+    const int o = e / MM, r = (e % MM) / MAXM, c = e % MAXM;
+    const bool v = o < n_own && r < M && c < M;
+    q_s[e] = v ? p.Qf[((size_t)(o_base + o) * M + r) * M + c] : make_float2(0.f, 0.f);
+    qi_s[e] = v ? p.Qinv[((size_t)(o_base + o) * M + r) * M + c] : make_float2(0.f, 0.f);
   }
+  if (!lam_mem)
+    for (int e = tid; e < NK * kOT; e += kThreads) {
+      const int nk = e / kOT, o = e % kOT;
+      own_s[e] = (o < n_own) ? p.W[(size_t)nk * F + o_base + o] : 0.f;
+    }
   for (int i0 = i_begin; i0 < i_end; i0 += IC) {
     const int icn = min(IC, i_end - i0);
     __syncthreads();
-    for (int row = tid >> 5; row < NK; row += kThreads / 32) {
-      const float* src = p.H + (size_t)row * T + i0;
-      float* dst = oth_s + row * ICP;
-      for (int i = tid & 31; i < IC; i += 32) dst[i] = (i < icn) ? src[i] : 0.f;
-    }
-    __syncthreads();
-    const int nq = IC / 4;
-    for (int it = tid; it < (kOT / 2) * nq; it += kThreads) {
-      const int o0 = (it / nq) * 2, ii = (it % nq) * 4;
-      for (int n = 0; n < N; ++n) {
-        float lam[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-        for (int k = 0; k < K; ++k) {
-          const int nk = n * K + k;
-          const float2 w = *reinterpret_cast<const float2*>(own_s + nk * kOT + o0);
-          const float4 h = ld4(oth_s + nk * ICP + ii);
-          lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);
-          lam[0][2] = fmaf(w.x, h.z, lam[0][2]); lam[0][3] = fmaf(w.x, h.w, lam[0][3]);
-          lam[1][0] = fmaf(w.y, h.x, lam[1][0]); lam[1][1] = fmaf(w.y, h.y, lam[1][1]);
-          lam[1][2] = fmaf(w.y, h.z, lam[1][2]); lam[1][3] = fmaf(w.y, h.w, lam[1][3]);
+    if (!lam_mem) {
+      for (int row = tid >> 5; row < NK; row += kThreads / 32) {
+        const float* src = p.H + (size_t)row * T + i0;
+        float* dst = oth_s + row * ICP;
+        for (int i = tid & 31; i < IC; i += 32) dst[i] = (i < icn) ? src[i] : 0.f;
+      }
+      __syncthreads();
+      const int nq = IC / 4;
+      for (int it = tid; it < (kOT / 2) * nq; it += kThreads) {
+        const int o0 = (it / nq) * 2, ii = (it % nq) * 4;
+        for (int n = 0; n < N; ++n) {
+          float lam[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+          for (int k = 0; k < K; ++k) {
+            const int nk = n * K + k;
+            const float2 w = *reinterpret_cast<const float2*>(own_s + nk * kOT + o0);
+            const float4 h = ld4(oth_s + nk * ICP + ii);
+            lam[0][0] = fmaf(w.x, h.x, lam[0][0]); lam[0][1] = fmaf(w.x, h.y, lam[0][1]);
+            lam[0][2] = fmaf(w.x, h.z, lam[0][2]); lam[0][3] = fmaf(w.x, h.w, lam[0][3]);
+            lam[1][0] = fmaf(w.y, h.x, lam[1][0]); lam[1][1] = fmaf(w.y, h.y, lam[1][1]);
+            lam[1][2] = fmaf(w.y, h.z, lam[1][2]); lam[1][3] = fmaf(w.y, h.w, lam[1][3]);
+          }
+          st4(lam_s + (n * kOT + o0) * ICP + ii, make_float4(lam[0][0], lam[0][1], lam[0][2], lam[0][3]));
+          st4(lam_s + (n * kOT + o0 + 1) * ICP + ii, make_float4(lam[1][0], lam[1][1], lam[1][2], lam[1][3]));
         }
-        st4(lam_s + (n * kOT + o0) * ICP + ii, make_float4(lam[0][0], lam[0][1], lam[0][2], lam[0][3]));
-        st4(lam_s + (n * kOT + o0 + 1) * ICP + ii, make_float4(lam[1][0], lam[1][1], lam[1][2], lam[1][3]));
       }
     }
     __syncthreads();
@@ -1101,26 +1162,43 @@ __global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* _
       if (o >= n_own || i >= icn) continue;
       const int f = o_base + o, t = i0 + i;
       const size_t pt = (size_t)f * T + t;
+      const bool exact = (M == MAXM);
       float2 x[MAXM], y[MAXM];
+      if (exact) {
 #pragma unroll
-      for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? p.X[pt * M + j] : make_float2(0.f, 0.f);
-      const float2* Qo = q_s + o * M * M;
-      const float2* Qi = qi_s + o * M * M;
+        for (int q = 0; q < MAXM / 2; ++q) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(p.X + pt * MAXM) + q);
+          x[2 * q] = make_float2(v.x, v.y);
+          x[2 * q + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) x[j] = (j < M) ? __ldg(p.X + pt * M + j) : make_float2(0.f, 0.f);
+      }
+      // y = Q_f x (rows of Q read two entries at a time)
+      const float4* Qo = reinterpret_cast<const float4*>(q_s + o * MM);
+      const float4* Qi = reinterpret_cast<const float4*>(qi_s + o * MM);
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
-        float2 s = make_float2(0.f, 0.f);
-        if (m < M) {
+        float sr = 0.f, si = 0.f;
 #pragma unroll
-          for (int j = 0; j < MAXM; ++j)
-            if (j < M) { const float2 c = cmulf(Qo[m * M + j], x[j]); s.x += c.x; s.y += c.y; }
+        for (int j = 0; j < MAXM; j += 2) {
+          const float4 q = Qo[(m * MAXM + j) >> 1];
+          sr = fmaf(q.x, x[j].x, fmaf(-q.y, x[j].y, sr));
+          si = fmaf(q.x, x[j].y, fmaf(q.y, x[j].x, si));
+          sr = fmaf(q.z, x[j + 1].x, fmaf(-q.w, x[j + 1].y, sr));
+          si = fmaf(q.z, x[j + 1].y, fmaf(q.w, x[j + 1].x, si));
         }
-        y[m] = s;
+        y[m] = make_float2(sr, si);
       }
+      auto lam_of = [&](int n) {
+        return lam_mem ? __ldg(p.lam + ((size_t)n * F + f) * T + t) : lam_s[(n * kOT + o) * ICP + i];
+      };
       float ytot[MAXM];
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) ytot[m] = 0.f;
       for (int n = 0; n < N; ++n) {
-        const float l = lam_s[(n * kOT + o) * ICP + i];
+        const float l = lam_of(n);
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
           if (m < M) ytot[m] = fmaf(l, g_s[(n * kOT + o) * M + m], ytot[m]);
@@ -1129,23 +1207,36 @@ __global__ void __launch_bounds__(kThreads) k_separate(Prob p, Geom g, float2* _
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) yinv[m] = (m < M) ? __fdividef(1.f, ytot[m]) : 0.f;
       for (int n = 0; n < N; ++n) {
-        const float l = lam_s[(n * kOT + o) * ICP + i];
+        const float l = lam_of(n);
         float2 z[MAXM];
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) {
           const float gain = (m < M) ? l * g_s[(n * kOT + o) * M + m] * yinv[m] : 0.f;
           z[m] = make_float2(gain * y[m].x, gain * y[m].y);
         }
-        float2* op = out + (((size_t)n * F + f) * T + t) * M;
+        float2 r[MAXM];
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) {
-          if (m < M) {
-            float2 s = make_float2(0.f, 0.f);
+          float sr = 0.f, si = 0.f;
 #pragma unroll
-            for (int j = 0; j < MAXM; ++j)
-              if (j < M) { const float2 c = cmulf(Qi[m * M + j], z[j]); s.x += c.x; s.y += c.y; }
-            op[m] = s;
+          for (int j = 0; j < MAXM; j += 2) {
+            const float4 q = Qi[(m * MAXM + j) >> 1];
+            sr = fmaf(q.x, z[j].x, fmaf(-q.y, z[j].y, sr));
+            si = fmaf(q.x, z[j].y, fmaf(q.y, z[j].x, si));
+            sr = fmaf(q.z, z[j + 1].x, fmaf(-q.w, z[j + 1].y, sr));
+            si = fmaf(q.z, z[j + 1].y, fmaf(q.w, z[j + 1].x, si));
           }
+          r[m] = make_float2(sr, si);
+        }
+        float2* op = out + (((size_t)n * F + f) * T + t) * M;
+        if (exact) {
+#pragma unroll
+          for (int q = 0; q < MAXM / 2; ++q)
+            reinterpret_cast<float4*>(op)[q] = make_float4(r[2 * q].x, r[2 * q].y, r[2 * q + 1].x, r[2 * q + 1].y);
+        } else {
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m)
+            if (m < M) op[m] = r[m];
         }
       }
     }

@@ -62,6 +62,14 @@ int scm_frames_per_stage(int maxm);
 int scm_smem(int maxm, int N);             // dynamic shared memory of k_scm_tc for N sources
 cudaError_t scm_prepare(int maxm, int N);  // allow that much shared memory
 int scm_occupancy(int maxm, int N);        // resident k_scm_tc CTAs per SM
+// tensor-core g~ update (N padded to np sources; np = 0: N unsupported)
+int gtc_np(int maxm, int N);
+cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, cudaStream_t st);
+cudaError_t gtc_prepare(int maxm, int np, int N);
+int gtc_occupancy(int maxm, int np, int N);
+int gtc_smem(int maxm, int np, int N);
+int gtc_bins_per_cta(int maxm);
+int gtc_frames_per_stage();
 cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
                          cudaStream_t st);
 

@@ -12,7 +12,9 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
+#include "fm_g_tc.cuh"
 #include "fm_gemm.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
@@ -63,23 +65,34 @@ __global__ void __launch_bounds__(kThreads) k_pr(Prob p, float* __restrict__ PR,
 }
 
 // fac[n][k][o] *= sqrt(num/den) with num = sum_s C[s][n][o][k], den = sum_s C[s][N+n][o][k].
+// Threads run along the split buffer's layout (k fastest), so the split loads coalesce.
 __global__ void __launch_bounds__(kThreads) k_apply(float* __restrict__ fac, const float* __restrict__ C, int S,
                                                     int N, int K, int own, unsigned* status) {
   const size_t total = (size_t)N * K * own;
   const size_t e = (size_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= total) return;
-  const int o = (int)(e % own);
-  const int nk = (int)(e / own);
-  const int n = nk / K, k = nk - n * K;
+  const int k = (int)(e % K);
+  const size_t no = e / K;
+  const int o = (int)(no % own), n = (int)(no / own);
   const size_t split = (size_t)2 * N * own * K;
+  // the splits summed in order; their loads issued eight at a time
   float num = 0.f, den = 0.f;
-  for (int s = 0; s < S; ++s) {
-    num += __ldg(C + s * split + ((size_t)n * own + o) * K + k);
-    den += __ldg(C + s * split + ((size_t)(N + n) * own + o) * K + k);
+  const float* cn = C + e;
+  const float* cd = C + (size_t)N * own * K + e;
+  for (int s0 = 0; s0 < S; s0 += 8) {
+    float a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a[u] = (s0 + u < S) ? __ldg(cn + (size_t)(s0 + u) * split) : 0.f;
+      b[u] = (s0 + u < S) ? __ldg(cd + (size_t)(s0 + u) * split) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { num += a[u]; den += b[u]; }
   }
-  const float v = fac[e] * sqrtf(num / den);
+  float* fp = fac + ((size_t)n * K + k) * own + o;
+  const float v = *fp * sqrtf(num / den);
   if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
-  fac[e] = v;
+  *fp = v;
 }
 
 template <int NT, bool TF32>
@@ -170,6 +183,69 @@ cudaError_t scm_prepare(int maxm, int N) {
   return maxm == 2 ? scm_configure<2>(N) : maxm == 4 ? scm_configure<4>(N) : scm_configure<8>(N);
 }
 int scm_occupancy(int maxm, int N) { return maxm == 2 ? scm_occ<2>(N) : maxm == 4 ? scm_occ<4>(N) : scm_occ<8>(N); }
+
+// ---- g~ update on the tensor cores ----
+template <int MAXM, int NP>
+static cudaError_t gtc_launch(const Prob& p, int S, int span, unsigned ctr, cudaStream_t st) {
+  using C = GtcCfg<MAXM, NP>;
+  const dim3 grid((p.F + C::FG - 1) / C::FG, S);
+  k_g_tc<MAXM, NP><<<grid, kGtcThreads + 32, C::smem(p.N), st>>>(p, S, span, ctr);
+  return cudaGetLastError();
+}
+template <int MAXM, int NP>
+static cudaError_t gtc_configure(int N) {
+  static std::mutex mu;
+  static int configured = 0;
+  const int need = GtcCfg<MAXM, NP>::smem(N);
+  std::lock_guard<std::mutex> lk(mu);
+  if (need <= configured) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_g_tc<MAXM, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  if (e == cudaSuccess) configured = need;
+  return e;
+}
+template <int MAXM, int NP>
+static int gtc_occ(int N) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g_tc<MAXM, NP>, kGtcThreads + 32, GtcCfg<MAXM, NP>::smem(N)) !=
+      cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+// The source padding of the kernel for (MAXM, N): a power of two >= N and >= MAXM / 2 (a
+// warp reads whole 16-column groups), at most 8; 0 when N is too large for it.
+int gtc_np(int maxm, int N) {
+  int np = 2;
+  while (np < N) np *= 2;
+  np = std::max(np, maxm / 2);
+  return np <= 8 ? np : 0;
+}
+template <typename Fn>
+static auto gtc_dispatch(int maxm, int np, Fn&& fn) {
+  switch (maxm * 16 + np) {
+    case 8 * 16 + 4: return fn(std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
+    case 8 * 16 + 8: return fn(std::integral_constant<int, 8>(), std::integral_constant<int, 8>());
+    case 4 * 16 + 2: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
+    case 4 * 16 + 4: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 4>());
+    case 4 * 16 + 8: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 8>());
+    case 2 * 16 + 2: return fn(std::integral_constant<int, 2>(), std::integral_constant<int, 2>());
+    case 2 * 16 + 4: return fn(std::integral_constant<int, 2>(), std::integral_constant<int, 4>());
+    default: return fn(std::integral_constant<int, 2>(), std::integral_constant<int, 8>());
+  }
+}
+cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, cudaStream_t st) {
+  return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return gtc_launch<decltype(mx)::value, decltype(n)::value>(p, S, span, ctr, st); });
+}
+cudaError_t gtc_prepare(int maxm, int np, int N) {
+  return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return gtc_configure<decltype(mx)::value, decltype(n)::value>(N); });
+}
+int gtc_occupancy(int maxm, int np, int N) {
+  return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return gtc_occ<decltype(mx)::value, decltype(n)::value>(N); });
+}
+int gtc_smem(int maxm, int np, int N) {
+  return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return GtcCfg<decltype(mx)::value, decltype(n)::value>::smem(N); });
+}
+int gtc_bins_per_cta(int maxm) { return 64 / maxm; }
+int gtc_frames_per_stage() { return kGtcKc; }
 
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st) {
   const unsigned npts = (unsigned)p.F * (unsigned)p.T;

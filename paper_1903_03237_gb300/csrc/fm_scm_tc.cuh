@@ -33,8 +33,6 @@
 // g = gq*GL + gl, GL = 8 / MAXM.
 // Split sums go to part[S][F][M][MAXM^2] for k_ip.
 #pragma once
-#include <cuda_bf16.h>
-
 #include "fm_common.cuh"
 #include "fm_tc.cuh"
 
@@ -75,44 +73,6 @@ struct ScmCfg {
   }
 };
 
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-      : "memory");
-}
-
-// (hi, lo) BF16 pairs of two floats, packed two per 32-bit word (first value in the low half).
-__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
-  split2(v[0], v[1], hi.x, lo.x);
-  split2(v[2], v[3], hi.y, lo.y);
-  split2(v[4], v[5], hi.z, lo.z);
-  split2(v[6], v[7], hi.w, lo.w);
-}
-
-// 32 lanes x 32 bits, 8 consecutive columns (tcgen05.ld 32x32b.x8).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Products of 8 frames of one (bin, c) with x_a for the a-range [a0, a0 + AR): hi and lo
 // rows into the A tiles.  FULL: all 8 frames valid (no per-frame test).
 template <int MAXM, int AR, bool FULL>
@@ -145,9 +105,6 @@ __device__ __forceinline__ void form_products(const float2* __restrict__ xg, int
   }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
-}
 // barrier 1 over the formation warps only (the MMA warp does not take part)
 __device__ __forceinline__ void formation_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kScmThreads) : "memory"); }
 

@@ -2,24 +2,20 @@
 //
 // Operand tiles live in shared memory in the canonical K-major layout without swizzle:
 // an R x Kb-byte tile is a grid of 8-row x 16-byte "core matrices", each stored as 128
-// contiguous bytes (row r of the core matrix at byte 16 r).  Core matrices adjacent along
-// K are 128 bytes apart (leading byte offset), groups of 8 rows are kb/16 * 128 bytes
-// apart (stride byte offset).  The accumulator lives in tensor memory (TMEM): for an
-// M = 128 MMA, row i of D is TMEM lane i and column j is TMEM column base + j.
+// contiguous bytes (row r of the core matrix at byte 16 r).  The descriptor gives the
+// distance between core matrices adjacent along K (leading byte offset) and along the
+// rows (stride byte offset).  The kernels here put the 16-byte k-groups outermost: the core
+// row (r, kg) sits at byte (kg * R + r) * 16, so the leading byte offset is R * 16 and the
+// stride byte offset 128.  The accumulator lives in tensor memory (TMEM): for an M = 128
+// MMA, row i of D is TMEM lane i and column j is TMEM column base + j.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace fm {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Byte offset of element (row, k) of a K-major tile with kb bytes per row, elements of
-// esize bytes, in the core-matrix layout above.
-__host__ __device__ __forceinline__ uint32_t cm_offset(int row, int k, int kb, int esize) {
-  const int kbyte = k * esize;
-  return (uint32_t)(((row >> 3) * (kb >> 4) + (kbyte >> 4)) * 128 + (row & 7) * 16 + (kbyte & 15));
-}
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading / stride byte offsets
 // (16-byte units), descriptor version 1 (bits 46-47), no swizzle (bits 61-63 = 0).
@@ -124,6 +120,48 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+// (hi, lo) BF16 pairs of two floats, packed two per 32-bit word (first value in the low half).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  split2(v[0], v[1], hi.x, lo.x);
+  split2(v[2], v[3], hi.y, lo.y);
+  split2(v[4], v[5], hi.z, lo.z);
+  split2(v[6], v[7], hi.w, lo.w);
+}
+
+// 32 lanes x 32 bits, 8 consecutive columns (tcgen05.ld 32x32b.x8).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 }  // namespace fm
