@@ -73,6 +73,10 @@ def kernel_bytes(kind: str, F, T, M, N, K) -> float:
         "g_update": 4 * N * ft + 4 * ft * M,                      # lambda and x~ read
         "scm": 4 * N * ft + 8 * ft * M + 4 * ft * M,              # lambda, X read, y~ written
         "xt_loglik": 20 * ft * M,                                 # X, y~ read; x~, y~ written
+        "wiener": 8 * ft * M + 4 * N * ft + 8 * N * ft * M,       # X, lambda read; images written
+        # one V_fm set read; Q, Q^-1 read and written; X, y~ read, x~, y~ written (fused x~ / LL)
+        "ip": 4 * F * M ** 4 + 64 * F * M * M + 20 * ft * M,
+        "apply": 8 * N * K * (F + T),                               # num/den (one split) read, W or H updated
     }.get(kind, 0))
 
 
@@ -221,13 +225,119 @@ def run_reference(args):
 def _config(precision="fp32"):
     w = WORKLOAD
     prec = {"fp32": "plain FP32 (float-float IP solve)",
-            "bf16": "BF16 tensor-core contractions, FP32 accumulation (float-float IP solve)",
-            "tf32": "TF32 tensor-core contractions, FP32 accumulation (float-float IP solve)"}[precision]
+            "bf16": "mixed: BF16 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
+                    "and g~ sums, FP32 accumulation, float-float IP solve",
+            "tf32": "mixed: TF32 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
+                    "and g~ sums, FP32 accumulation, float-float IP solve"}[precision]
     name = "paper-scale single mixture" if WORKLOAD is WORKLOADS["c1"] else "large mixture"
     return {"workload": f"{name} M{w['M']} N{w['N']} K{w['K']} F{w['F']} T{w['T']}, "
                         f"{w['iters']} iterations + Wiener separation per step",
             "M": w["M"], "N": w["N"], "K": w["K"], "F": w["F"], "T": w["T"], "iters_per_step": w["iters"],
             "l2": "flushed between timed steps (512 MB write)", "precision": prec}
+
+
+def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local, sample_clocks):
+    """Times one form on the workload: each step is a whole job (fresh initial state, the
+    workload's iterations, Wiener separation) with X resident in HBM; then the same job end
+    to end through the C ABI with host buffers.  Returns the numbers of the bench line."""
+    w = WORKLOAD
+    F, T, M, N, K, iters = w["F"], w["T"], w["M"], w["N"], w["K"], w["iters"]
+    stream = torch.cuda.Stream()
+    Xd = torch.from_numpy(mix.X).cuda()
+    torch.cuda.synchronize()
+    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream, precision=PRECISIONS[precision])
+    out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():  # one whole job: fresh initial state, the iterations, Wiener separation
+        ctx.restart()
+        ctx.iterate(iters)
+        ctx.separate(out)
+
+    for _ in range(warmup):
+        step()
+    ctx.sync()
+    tune = None
+    if not args.no_autotune:
+        # the library's tuner picks the launch shapes for this workload (state restored after)
+        sp = ctx.autotune(3)
+        tune = {"trial_speedup": sp, "scales": [round(v, 4) for v in ctx.get_tuning()]}
+        for _ in range(warmup):
+            step()
+        ctx.sync()
+    # calibration (untimed): which kernel class dominates the step
+    ctx.set_timing(True)
+    step()
+    ctx.sync()
+    cal = ctx.kernel_times()
+    dom = max((k for k in cal if cal[k][1] > 0), key=lambda k: cal[k][0])
+    shares = {k: round(v[0] / max(1e-12, sum(x[0] for x in cal.values())), 4) for k, v in cal.items() if v[1]}
+    avg_all = {k: round(1e3 * v[0] / v[1], 2) for k, v in cal.items() if v[1]}
+    # the timed region brackets the dominant kernel's launches only
+    ctx.set_timing([dom])
+    for _ in range(warmup):  # capture that graph variant before the timed region
+        step()
+    ctx.sync()
+    ctx.kernel_times()
+    dev_id = None
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = None
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_id if sample_clocks else None) as clocks:
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ctx.sync()
+    launches = ctx.launch_count() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    kt = ctx.kernel_times()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = F * T * iters * steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel, from its launches inside the timed region
+    avg_ms = kt[dom][0] / kt[dom][1]
+    roofline = roofline_for(dom, avg_ms, precision, F, T, M, N, K, args.workload)
+    roofline["launches_timed"] = kt[dom][1]
+
+    # end to end through the C ABI with host buffers: H2D mixture, iterations, D2H images
+    ctx.set_timing(False)
+    Xh = np.ascontiguousarray(mix.X)
+    outh = np.empty((N, F, T, M), dtype=np.complex64)
+    ctx.reset(Xh, seed=rank)
+    ctx.iterate(iters)
+    ctx.separate(outh)
+    e2e_s = []
+    for _ in range(max(1, steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.reset(Xh, seed=rank)
+        ctx.iterate(iters)
+        ctx.separate(outh)  # synchronises (host output)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_val = F * T * iters * len(e2e_s) * world / e2e_total
+    ctx.close()
+    return {"value": value, "ms_per_step": total_ms / steps, "roofline": roofline, "launches": launches,
+            "e2e": e2e_val, "shares": shares, "avg_us": avg_all, "clocks": clocks.summary(), "tune": tune}
 
 
 def run_ours(args):
@@ -248,93 +358,15 @@ def run_ours(args):
     w = WORKLOAD
     F, T, M, N, K, iters = w["F"], w["T"], w["M"], w["N"], w["K"], w["iters"]
     mix = make_mixture(F, T, M, N, K, seed=rank, diffuse_frac=w["diffuse"])
-    stream = torch.cuda.Stream()
-    Xd = torch.from_numpy(mix.X).cuda()
-    torch.cuda.synchronize()
-    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream, precision=PRECISIONS[args.precision])
-    out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def step():  # one whole job: fresh initial state, 100 iterations, Wiener separation
-        ctx.restart()
-        ctx.iterate(iters)
-        ctx.separate(out)
-
-    for _ in range(args.warmup):
-        step()
-    ctx.sync()
-    # calibration (untimed): which kernel class dominates the step
-    ctx.set_timing(True)
-    step()
-    ctx.sync()
-    cal = ctx.kernel_times()
-    dom = max((k for k in cal if cal[k][1] > 0), key=lambda k: cal[k][0])
-    shares = {k: round(v[0] / max(1e-12, sum(x[0] for x in cal.values())), 4) for k, v in cal.items() if v[1]}
-    avg_all = {k: round(1e3 * v[0] / v[1], 2) for k, v in cal.items() if v[1]}
-    # the timed region brackets the dominant kernel's launches only
-    ctx.set_timing([dom])
-    for _ in range(args.warmup):  # capture that graph variant before the timed region
-        step()
-    ctx.sync()
-    ctx.kernel_times()
-    dev_id = None
-    try:
-        dev_id = str(torch.cuda.get_device_properties(local).uuid)
-        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
-    except Exception:
-        dev_id = None
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = ctx.launch_count()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(dev_id) as clocks:
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(i))
-            evs[i][0].record(stream)
-            step()
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-    ctx.sync()
-    launches = ctx.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    kt = ctx.kernel_times()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = F * T * iters * args.steps * world
-    value = units / (total_ms / 1e3)
-
-    # roofline of the dominant kernel, from its launches inside the timed region
-    avg_ms = kt[dom][0] / kt[dom][1]
-    roofline = roofline_for(dom, avg_ms, args.precision, F, T, M, N, K, args.workload)
-    roofline["launches_timed"] = kt[dom][1]
-
-    # end to end through the C ABI with host buffers: H2D mixture, 100 iterations, D2H images
-    ctx.set_timing(False)
-    Xh = np.ascontiguousarray(mix.X)
-    outh = np.empty((N, F, T, M), dtype=np.complex64)
-    ctx.reset(Xh, seed=rank)
-    ctx.iterate(iters)
-    ctx.separate(outh)
-    e2e_s = []
-    for _ in range(max(1, args.steps)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.reset(Xh, seed=rank)
-        ctx.iterate(iters)
-        ctx.separate(outh)  # synchronises (host output)
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_val = F * T * iters * len(e2e_s) * world / e2e_total
+    res = _measure(fm, torch, mix, args, args.precision, args.steps, args.warmup, rank, world, local, True)
+    # the plain FP32 form on the same workload, for the comparison the metric names
+    plain = None
+    if args.precision != "fp32" and not args.no_compare:
+        psteps = max(2, min(args.steps, 3))
+        pr = _measure(fm, torch, mix, args, "fp32", psteps, max(3, args.warmup), rank, world, local, False)
+        plain = {"value": pr["value"], "ms_per_step": pr["ms_per_step"], "e2e_value": pr["e2e"], "steps": psteps,
+                 "autotune": pr["tune"],
+                 "dominant_kernel": pr["roofline"]["kernel"], "roofline_frac": pr["roofline"]["frac"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -349,19 +381,21 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision],
             "data": "synthetic",
             "config": _config(args.precision) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": F * T * M * 8,
+            "roofline": res["roofline"], "cpu_baseline": cpu,
+            "e2e": {"value": res["e2e"], "unit": UNIT, "h2d_bytes_per_step": F * T * M * 8,
                     "d2h_bytes_per_step": N * F * T * M * 8},
-            "gpu_launches": launches, "clocks": clocks.summary(),
-            "kernel_share": shares, "kernel_avg_us": avg_all,
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "kernel_share": res["shares"], "kernel_avg_us": res["avg_us"], "autotune": res["tune"],
         }
+        if plain is not None:
+            line["plain_fp32"] = plain
+            line["speedup_vs_plain_fp32"] = res["value"] / plain["value"]
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -419,6 +453,9 @@ def run_batched(args):
             torch.cuda.synchronize()
             tot += time.perf_counter() - t0
         return tot
+    t_u = timed(step_batched)           # launch shapes as planned for each mixture alone
+    batch.sync()
+    tune_speedup = batch.autotune(2)    # one split scale for all members, timed on the batch
     l0 = sum(c.launch_count() for c in ctxs)
     t_b = timed(step_batched)
     launches = sum(c.launch_count() for c in ctxs) - l0
@@ -432,9 +469,11 @@ def run_batched(args):
         "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
         "config": {"workload": f"batched: {len(inst)} mixtures, T ~ U{{200..4000}}, M in {{2,4,8}}, N = M, K 16, "
-                               f"F 513, {iters} iterations each, one graph launch per step",
+                               f"F 513, {iters} iterations each, one graph launch per step, autotuned split scale",
                    "l2": "flushed between timed steps (512 MB write)", "precision": args.precision},
         "sequential_value": units * args.steps / t_s, "batched_over_sequential": t_s / t_b,
+        "untuned_value": units * args.steps / t_u, "tuned_over_untuned": t_u / t_b,
+        "tuner_trial_speedup": tune_speedup, "tuned_scales": ctxs[0].get_tuning(),
         "gpu_launches": launches,
     }), flush=True)
     batch.close()
@@ -539,7 +578,10 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0,
                     help="c4: arrival rate in requests/s (the same arrival pattern, rescaled); 0 = all at once")
     ap.add_argument("--instances", type=int, default=64, help="c3: number of mixtures")
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
+                    help="form to time: bf16 (default, the mixed-precision form), tf32, or fp32 (plain)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the planned launch shapes (no tuner run)")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])

@@ -196,6 +196,26 @@ fmnmf_status fmnmf_batch_sync(fmnmf_batch* batch);
 fmnmf_status fmnmf_batch_destroy(fmnmf_batch* batch);
 
 /*
+ * Launch-shape tuning.  Each context plans its launches to fill the GPU alone: the inner
+ * split counts of the tiled sweeps (plain form) or of the tensor-core V_fm and g~ kernels
+ * and the split-K GEMMs of the W and H sums (mixed form).  The tuner times whole iterations
+ * (n_iter per trial, from a saved copy of the state, which is restored afterwards) for
+ * those split counts scaled by 1, 1/2, 1/4 and 1/8 and keeps the fastest:
+ *  - fmnmf_autotune: coordinate descent over the context's four tunable launches;
+ *  - fmnmf_batch_autotune: one scale for every tunable launch of every member, timed on the
+ *    whole batch (members running together do better with smaller grids).
+ * speedup (may be NULL) receives the first trial's time over the best one.  Fewer splits
+ * change the order of the split sums, so results differ from an untuned context by
+ * rounding; fmnmf_get_tuning / fmnmf_set_tuning read and set the scales (8 floats in
+ * (0, 1]: W, H, g~, y~/V sweeps, V_fm and g~ tensor-core kernels, W and H GEMMs), so that a
+ * tuned shape can be reproduced or cached.  Synchronising.
+ */
+fmnmf_status fmnmf_autotune(fmnmf_ctx* ctx, int n_iter, double* speedup);
+fmnmf_status fmnmf_batch_autotune(fmnmf_batch* batch, int n_iter, double* speedup);
+fmnmf_status fmnmf_get_tuning(const fmnmf_ctx* ctx, float* scales);
+fmnmf_status fmnmf_set_tuning(fmnmf_ctx* ctx, const float* scales);
+
+/*
  * Serving (continuous batching).  A server accepts separation requests of any shape from
  * any thread and returns each one's separated images.  Its scheduler thread:
  *  - admits queued requests in arrival order while fewer than max_active are resident

@@ -75,6 +75,11 @@ struct fmnmf_ctx {
   GemmPlan gpW, gpH, gpL;
   int scmS = 1, scmSpan = 64;  // tensor-core V_fm: T splits and frames per split
   int gtcNP = 0, gtcS = 1, gtcSpan = 16;  // tensor-core g~ update (NP = 0: the CUDA-core sweep)
+  // launch shapes: the split counts plan() chose for the tunable launches, and the tuner's
+  // scales of them (<= 1: buffers are sized for the planned counts)
+  int caps[4] = {0, 0, 0, 0};
+  int baseS[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  float tscale[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
   int sms = 0;
   std::map<std::pair<int, unsigned>, GraphEntry> graphs;  // (chunk, timing mask) -> graph
   std::string err;
@@ -159,6 +164,24 @@ Geom make_geom(int SO, int SI, int ic_cap, int slots) {
   g.ICP = g.IC + 4;
   return g;
 }
+
+// The same tiling with a given number of inner splits.
+Geom make_geom_S(int SO, int SI, int ic_cap, int S) {
+  Geom g;
+  g.n_own_tiles = (SO + kOT - 1) / kOT;
+  S = std::max(1, std::min(S, (SI + 3) / 4));
+  int span = (SI + S - 1) / S;
+  span = (span + 3) & ~3;
+  g.S = (SI + span - 1) / span;
+  g.span = span;
+  g.IC = std::min(ic_cap, span);
+  g.ICP = g.IC + 4;
+  return g;
+}
+
+// Tunable launches: the inner split counts of the sweeps, the tensor-core V_fm and g~
+// kernels and the split-K GEMMs of the W and H sums.
+enum { TU_W = 0, TU_H, TU_G, TU_Y, TU_SCM, TU_GTC, TU_GEMM_W, TU_GEMM_H, TU_COUNT };
 
 // Largest sub-chunk (multiple of 4, <= 256) whose shared memory fits `limit` bytes.
 int ic_cap_for(int mode, int N, int K, int M, int maxm, int limit, bool lam_mem = false) {
@@ -291,7 +314,45 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
+  for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
+  const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
+                              ctx->mixed ? ctx->gpW.g.ksplit : 1, ctx->mixed ? ctx->gpH.g.ksplit : 1};
+  for (int t = 0; t < TU_COUNT; ++t) { ctx->baseS[t] = base[t]; ctx->tscale[t] = 1.f; }
   return FMNMF_OK;
+}
+
+// Re-derives the tunable launch shapes from the planned split counts and the tuner's scales.
+void apply_shapes(fmnmf_ctx* c) {
+  const int F = c->F, T = c->T, M = c->M, N = c->N, K = c->K, mx = c->maxm;
+  auto S_of = [&](int t, int smin) { return std::max(smin, (int)std::lround(c->baseS[t] * c->tscale[t])); };
+  auto lm = [&](int mode) { return c->mixed && (mode == MODE_G || mode == MODE_Y); };
+  c->gW = make_geom_S(F, T, c->caps[MODE_W], S_of(TU_W, 1));
+  c->gH = make_geom_S(T, F, c->caps[MODE_H], S_of(TU_H, 1));
+  c->gG = make_geom_S(F, T, c->caps[MODE_G], S_of(TU_G, 1));
+  c->gY = make_geom_S(F, T, c->caps[MODE_Y], S_of(TU_Y, 1));
+  c->smW = smem_bytes(MODE_W, N, K, M, mx, c->gW.IC);
+  c->smH = smem_bytes(MODE_H, N, K, M, mx, c->gH.IC);
+  c->smG = smem_bytes(MODE_G, N, K, M, mx, c->gG.IC, lm(MODE_G));
+  c->smY = smem_bytes(MODE_Y, N, K, M, mx, c->gY.IC, lm(MODE_Y));
+  if (!c->mixed) return;
+  auto frames = [&](int S, int kc, int& span, int& outS) {
+    const int nst = (T + kc - 1) / kc;
+    S = std::max(1, std::min(S, nst));
+    span = ((nst + S - 1) / S) * kc;
+    outS = (T + span - 1) / span;
+  };
+  frames(S_of(TU_SCM, 1), scm_frames_per_stage(mx), c->scmSpan, c->scmS);
+  if (c->gtcNP > 0) frames(S_of(TU_GTC, 1), gtc_frames_per_stage(), c->gtcSpan, c->gtcS);
+  auto gemm = [&](GemmPlan& gp, int S) {
+    const int kchunks = (gp.g.Kd + kGemmKc - 1) / kGemmKc;
+    S = std::max(S, (gp.g.Kd + 511) / 512);  // at most 512 terms per TMEM accumulator
+    const int kspan = ((kchunks + S - 1) / S) * kGemmKc;
+    gp.g.ksplit = (gp.g.Kd + kspan - 1) / kspan;
+    gp.g.kspan = kspan;
+    gp.grid.z = (unsigned)(gp.g.batch * gp.g.ksplit);
+  };
+  gemm(c->gpW, S_of(TU_GEMM_W, 1));
+  gemm(c->gpH, S_of(TU_GEMM_H, 1));
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -333,7 +394,7 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
       {(void**)&p.ll, 8},
       {(void**)&p.status, 4},
       {(void**)&p.part, part * 4},
-      {(void**)&p.llpart, (size_t)ctx->n_pt_blocks * 8},
+      {(void**)&p.llpart, (size_t)std::max(ctx->n_pt_blocks, ctx->F) * 8},
       {(void**)&p.counters, (size_t)nctr * 4},
       {(void**)&ctx->W0, N * K * F * 4},
       {(void**)&ctx->H0, N * K * T * 4},
@@ -427,6 +488,50 @@ struct Recorder {  // brackets launches with events when timing is on (works und
 
 cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec);
 
+// The end of an iteration.  With a Q update or normalisation and up to kFuseXtFrames
+// frames, the IP kernel also forms x~ and the log-likelihood of each bin right after the
+// bin's update (one launch instead of two: the short mixtures are launch-latency bound),
+// then the mu normalisation runs.  Longer mixtures keep the separate x~ / log-likelihood
+// kernel, whose many small CTAs keep more loads in flight than one CTA per bin.
+constexpr int kFuseXtFrames = 1024;
+cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int norm) {
+  cudaError_t e;
+  if (yflags && c->T > kFuseXtFrames) {
+    LaunchArgs a;
+    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = ipS;
+    a.grid = dim3(c->F);
+    a.xt_mode = 0;
+    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
+    LaunchArgs x;
+    x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+    x.n_pt_blocks = c->n_pt_blocks;
+    x.apply_phi = 1;
+    x.do_mu = norm ? 1 : 0;
+    x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
+    return rec.run(KK_XT, x);
+  }
+  if (yflags) {
+    LaunchArgs a;
+    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = ipS;
+    a.grid = dim3(c->F);
+    a.xt_mode = 1; a.ctr = c->ctrLL;
+    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
+    if (!norm) return cudaSuccess;
+    LaunchArgs x;
+    x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+    x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = 1;
+    x.grid = dim3(c->n_mu_blocks);
+    return rec.run(KK_XT, x);
+  }
+  LaunchArgs x;
+  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+  x.n_pt_blocks = c->n_pt_blocks;
+  x.apply_phi = 0;
+  x.do_mu = 0;
+  x.grid = dim3(c->n_pt_blocks);
+  return rec.run(KK_XT, x);
+}
+
 cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
   if (c->mixed) return enqueue_mixed_iteration(c, rec);
   const unsigned mask = c->opts.update_mask;
@@ -440,19 +545,7 @@ cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
     if ((e = rec.run(KK_G, tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG))) != cudaSuccess) return e;
   const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
   if ((e = rec.run(KK_Y, tile_args(c, c->gY, c->smY, yflags, c->ctrY))) != cudaSuccess) return e;
-  if (yflags) {
-    LaunchArgs a;
-    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = c->gY.S;
-    a.grid = dim3(c->F);
-    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
-  }
-  LaunchArgs x;
-  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
-  x.n_pt_blocks = c->n_pt_blocks;
-  x.apply_phi = (yflags != 0);
-  x.do_mu = norm ? 1 : 0;
-  x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
-  return rec.run(KK_XT, x);
+  return enqueue_tail(c, rec, yflags, c->gY.S, norm);
 }
 
 // The mixed-precision iteration: tensor-core GEMMs for lambda and the W / H sums.
@@ -516,19 +609,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     a.p.lam = c->lam;
     if ((e = rec.run(KK_Y, a)) != cudaSuccess) return e;
   }
-  if (yflags) {
-    LaunchArgs a;
-    a.p = c->p; a.st = c->st; a.flags = yflags; a.S = ipS;
-    a.grid = dim3(c->F);
-    if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
-  }
-  LaunchArgs x;
-  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
-  x.n_pt_blocks = c->n_pt_blocks;
-  x.apply_phi = (yflags != 0);
-  x.do_mu = norm ? 1 : 0;
-  x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
-  return rec.run(KK_XT, x);
+  return enqueue_tail(c, rec, yflags, ipS, norm);
 }
 
 // x~, y~, log-det and log-likelihood of the state currently on the device.
@@ -640,6 +721,49 @@ fmnmf_status seed_state(fmnmf_ctx* ctx, uint64_t seed) {
   CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
   // the host vectors die at return: wait for the copies
   CK(cudaStreamSynchronize(ctx->st));
+  return FMNMF_OK;
+}
+
+// Drops the captured graphs (their launch shapes changed).
+void clear_graphs(fmnmf_ctx* ctx) {
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (auto& kv : ctx->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& e : kv.second.ev) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+  }
+  ctx->graphs.clear();
+}
+
+// An exact copy of everything an iteration changes (W, H, g~, Q and Q^-1 in both storage
+// forms, log|det Q|^2, phi, x~, y~, the log-likelihood and, in the mixed form, lambda) for
+// the tuner's trials; restoring it makes the context continue bit for bit as it would have.
+struct SavedState {
+  void* buf = nullptr;
+  std::vector<std::pair<void*, size_t>> arrays;  // live array, bytes
+  std::vector<size_t> off;
+};
+fmnmf_status save_state(fmnmf_ctx* ctx, SavedState& sv) {
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
+  Prob& p = ctx->p;
+  sv.arrays = {{p.W, N * K * F * 4}, {p.H, N * K * T * 4}, {p.G, N * F * M * 4},
+               {p.Qx, F * M * M * sizeof(float4)}, {p.Qix, F * M * M * sizeof(float4)},
+               {p.Qf, F * M * M * sizeof(float2)}, {p.Qinv, F * M * M * sizeof(float2)},
+               {p.logdet, F * 8}, {p.phi, F * 4}, {p.xt, F * T * M * 4}, {p.yt, F * T * M * 4}, {p.ll, 8}};
+  if (ctx->mixed) sv.arrays.push_back({ctx->lam, N * F * T * 4});
+  size_t tot = 0;
+  for (auto& a : sv.arrays) { sv.off.push_back(tot); tot += (a.second + 255) & ~(size_t)255; }
+  cudaError_t e = cudaMallocAsync(&sv.buf, tot, ctx->st);
+  if (e != cudaSuccess) return set_err(ctx, FMNMF_ENOMEM, "tuner state copy (%zu bytes): %s", tot, cudaGetErrorString(e));
+  for (size_t i = 0; i < sv.arrays.size(); ++i)
+    CK(cudaMemcpyAsync((char*)sv.buf + sv.off[i], sv.arrays[i].first, sv.arrays[i].second, cudaMemcpyDeviceToDevice,
+                       ctx->st));
+  return FMNMF_OK;
+}
+fmnmf_status restore_state(fmnmf_ctx* ctx, const SavedState& sv) {
+  for (size_t i = 0; i < sv.arrays.size(); ++i)
+    CK(cudaMemcpyAsync(sv.arrays[i].first, (char*)sv.buf + sv.off[i], sv.arrays[i].second, cudaMemcpyDeviceToDevice,
+                       ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
   return FMNMF_OK;
 }
 
@@ -946,6 +1070,76 @@ const char* fmnmf_kernel_name(int i) { return (i >= 0 && i < KK_COUNT) ? kKindNa
 long long fmnmf_launch_count(const fmnmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 // ---- batches ---------------------------------------------------------------------------
+// One timed trial of the current launch shapes: n_iter iterations from the saved state (the
+// graph captured and run once untimed, then timed), in milliseconds; +inf if it failed.
+static double tune_trial(fmnmf_ctx* ctx, const SavedState& sv, int n_iter, cudaEvent_t e0, cudaEvent_t e1) {
+  clear_graphs(ctx);
+  if (restore_state(ctx, sv) != FMNMF_OK || fmnmf_iterate(ctx, n_iter) != FMNMF_OK) return INFINITY;
+  if (restore_state(ctx, sv) != FMNMF_OK) return INFINITY;
+  if (cudaEventRecord(e0, ctx->st) != cudaSuccess || fmnmf_iterate(ctx, n_iter) != FMNMF_OK ||
+      cudaEventRecord(e1, ctx->st) != cudaSuccess || check_status(ctx) != FMNMF_OK)
+    return INFINITY;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return INFINITY;
+  return ms;
+}
+
+static const float kTuneScales[] = {1.f, 0.5f, 0.25f, 0.125f};
+
+fmnmf_status fmnmf_autotune(fmnmf_ctx* ctx, int n_iter, double* speedup) {
+  if (!ctx || n_iter < 1) return set_err(ctx, FMNMF_EINVAL, "autotune: bad arguments");
+  SavedState sv;
+  fmnmf_status s = save_state(ctx, sv);
+  if (s != FMNMF_OK) return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int tun[4] = {ctx->mixed ? TU_SCM : TU_W, ctx->mixed ? TU_GTC : TU_H, ctx->mixed ? TU_GEMM_W : TU_G,
+                      ctx->mixed ? TU_GEMM_H : TU_Y};
+  const double t0 = tune_trial(ctx, sv, n_iter, e0, e1);
+  double best = t0;
+  // coordinate descent over the split scales, two passes
+  for (int pass = 0; pass < 2; ++pass)
+    for (int t : tun) {
+      if (t == TU_GTC && ctx->gtcNP == 0) continue;
+      const float keep = ctx->tscale[t];
+      float pick = keep;
+      for (float sc : kTuneScales) {
+        if (sc == keep) continue;
+        ctx->tscale[t] = sc;
+        apply_shapes(ctx);
+        const double ms = tune_trial(ctx, sv, n_iter, e0, e1);
+        if (ms < 0.98 * best) { best = ms; pick = sc; }
+      }
+      ctx->tscale[t] = pick;
+      apply_shapes(ctx);
+    }
+  clear_graphs(ctx);
+  s = restore_state(ctx, sv);
+  cudaFreeAsync(sv.buf, ctx->st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != FMNMF_OK) return s;
+  if (speedup) *speedup = (std::isfinite(t0) && std::isfinite(best) && best > 0) ? t0 / best : 1.0;
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_get_tuning(const fmnmf_ctx* ctx, float* scales) {
+  if (!ctx || !scales) return set_err(nullptr, FMNMF_EINVAL, "get_tuning: NULL argument");
+  for (int t = 0; t < TU_COUNT; ++t) scales[t] = ctx->tscale[t];
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_set_tuning(fmnmf_ctx* ctx, const float* scales) {
+  if (!ctx || !scales) return set_err(ctx, FMNMF_EINVAL, "set_tuning: NULL argument");
+  for (int t = 0; t < TU_COUNT; ++t)
+    if (!(scales[t] > 0.f && scales[t] <= 1.f)) return set_err(ctx, FMNMF_EINVAL, "set_tuning: scale %d not in (0, 1]", t);
+  for (int t = 0; t < TU_COUNT; ++t) ctx->tscale[t] = scales[t];
+  apply_shapes(ctx);
+  clear_graphs(ctx);
+  return FMNMF_OK;
+}
+
 fmnmf_status fmnmf_batch_create(fmnmf_ctx* const* ctxs, int n, fmnmf_batch** out) {
   if (!out || !ctxs || n < 1) return set_err(nullptr, FMNMF_EINVAL, "batch_create: bad arguments");
   *out = nullptr;
@@ -1022,6 +1216,74 @@ fmnmf_status fmnmf_batch_iterate(fmnmf_batch* b, int n_iter) {
     n_iter -= chunk;
   }
   return FMNMF_OK;
+}
+
+// The batch tuner: the members' split counts scaled together (one scale for every tunable
+// launch of every member); each candidate timed on the whole batch, from saved states.
+fmnmf_status fmnmf_batch_autotune(fmnmf_batch* b, int n_iter, double* speedup) {
+  if (!b || n_iter < 1) return set_err(nullptr, FMNMF_EINVAL, "batch_autotune: bad arguments");
+  fmnmf_ctx* ctx = nullptr;  // for CK
+  const size_t n = b->ctxs.size();
+  std::vector<SavedState> sv(n);
+  for (size_t i = 0; i < n; ++i) {
+    fmnmf_status s = save_state(b->ctxs[i], sv[i]);
+    if (s != FMNMF_OK) {
+      for (size_t j = 0; j < i; ++j) cudaFreeAsync(sv[j].buf, b->ctxs[j]->st);
+      return s;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto drop_graphs = [&] {
+    if (b->st) cudaStreamSynchronize(b->st);
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->graph_launches.clear();
+  };
+  auto restore_all = [&] {
+    for (size_t i = 0; i < n; ++i)
+      if (restore_state(b->ctxs[i], sv[i]) != FMNMF_OK) return false;
+    for (auto* c : b->ctxs)
+      if (cudaStreamSynchronize(c->st) != cudaSuccess) return false;
+    return true;
+  };
+  auto trial = [&]() -> double {
+    drop_graphs();
+    if (!restore_all() || fmnmf_batch_iterate(b, n_iter) != FMNMF_OK) return INFINITY;
+    if (!restore_all()) return INFINITY;
+    if (cudaEventRecord(e0, b->st) != cudaSuccess || fmnmf_batch_iterate(b, n_iter) != FMNMF_OK ||
+        cudaEventRecord(e1, b->st) != cudaSuccess || fmnmf_batch_sync(b) != FMNMF_OK)
+      return INFINITY;
+    float ms = 0.f;
+    return cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? (double)ms : INFINITY;
+  };
+  auto set_all = [&](float sc) {
+    for (auto* c : b->ctxs) {
+      for (int t = 0; t < TU_COUNT; ++t) c->tscale[t] = sc;
+      apply_shapes(c);
+      clear_graphs(c);
+    }
+  };
+  set_all(1.f);
+  const double t0 = trial();
+  double best = t0;
+  float pick = 1.f;
+  for (float sc : kTuneScales) {
+    if (sc == 1.f) continue;
+    set_all(sc);
+    const double ms = trial();
+    if (ms < 0.98 * best) { best = ms; pick = sc; }
+  }
+  set_all(pick);
+  drop_graphs();
+  const bool ok = restore_all();
+  for (size_t i = 0; i < n; ++i) cudaFreeAsync(sv[i].buf, b->ctxs[i]->st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return set_err(nullptr, FMNMF_ECUDA, "batch_autotune: restoring a member's state failed");
+  if (speedup) *speedup = (std::isfinite(t0) && std::isfinite(best) && best > 0) ? t0 / best : 1.0;
+  return fmnmf_batch_sync(b);
 }
 
 fmnmf_status fmnmf_batch_sync(fmnmf_batch* b) {

@@ -705,9 +705,12 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 // so Q_f^-1 and log|det Q_f|^2 are carried across iterations instead of re-factored.
 // Then phi_f = tr(Q_f Q_f^H)/M: Q_f /= sqrt(phi), Q_f^-1 *= sqrt(phi), g~_nf /= phi,
 // log|det|^2 -= M log phi; nu_nf = sum_m g~_nfm: g~_nf /= nu, w_nkf *= nu.
+// With xt_mode the same CTA then computes x~ = |Q_f x_ft|^2 for its bin's frames with the
+// new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the last CTA to finish adds
+// the bins up in bin order (Eq. 17).
 // ---------------------------------------------------------------------------------
 template <int MAXM>
-__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
+__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr) {
   constexpr int MM = MAXM * MAXM;
   __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
   __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
@@ -828,6 +831,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
   // phi normalisation and write-back
   __shared__ double phi_s;
   __shared__ float nu_s[64];
+  __shared__ float2 qf_s[MM];  // the normalised Q_f in float32 (x~ of this bin's frames)
   if (warp == 0) {
     double phi = 1.0;
     df sq = df_make(1.f), isq = df_make(1.f);
@@ -847,6 +851,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
       p.Qx[(size_t)f * M * M + e] = cdf_pack(q);
       p.Qix[(size_t)f * M * M + e] = cdf_pack(qi);
       p.Qf[(size_t)f * M * M + e] = make_float2(q.re.hi, q.im.hi);
+      qf_s[r * MAXM + c] = make_float2(q.re.hi, q.im.hi);
       p.Qinv[(size_t)f * M * M + e] = make_float2(qi.re.hi, qi.im.hi);
     }
     if (lane == 0) {
@@ -884,6 +889,85 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags) {
       }
       __syncthreads();
     }
+  }
+  if (!xt_mode) return;
+  // x~ = |Q_f x_ft|^2 for this bin's frames with the new (normalised) Q_f, y~ /= phi_f,
+  // and this bin's log-likelihood terms (Eq. 17); the last CTA adds the bins up
+  __syncthreads();
+  const int T = p.T;
+  const float ph = (float)phi_s;
+  const bool exact = (M == MAXM);
+  float part = 0.f;
+  for (int t = tid; t < T; t += blockDim.x) {
+    const size_t pt = (size_t)f * T + t;
+    float2 x[MAXM];
+    float yv[MAXM];
+    if (exact) {
+#pragma unroll
+      for (int q = 0; q < MAXM / 2; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p.X + pt * MAXM) + q);
+        x[2 * q] = make_float2(v.x, v.y);
+        x[2 * q + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) yv[m] = p.yt[pt * MAXM + m];
+    } else {
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        x[j] = (j < M) ? __ldg(p.X + pt * M + j) : make_float2(0.f, 0.f);
+        yv[j] = (j < M) ? p.yt[pt * M + j] : 1.f;
+      }
+    }
+    float ls = 0.f;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      if (m < M) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+          if (j < M) {
+            const float2 q = qf_s[m * MAXM + j];
+            re = fmaf(q.x, x[j].x, fmaf(-q.y, x[j].y, re));
+            im = fmaf(q.x, x[j].y, fmaf(q.y, x[j].x, im));
+          }
+        }
+        const float xv = re * re + im * im;
+        const float y = yv[m] / ph;
+        p.yt[pt * M + m] = y;
+        p.xt[pt * M + m] = xv;
+        ls += -xv / y - logf(y);
+      }
+    }
+    part += ls;
+  }
+  __shared__ double red_s[MAXM];
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if (lane == 0) red_s[warp] = (double)part;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red_s[w];
+    p.llpart[f] = sum;
+  }
+  if (!arrive_last(p.counters + ctr, (unsigned)F)) return;
+  double sll = 0.0, sld = 0.0;
+  for (int b = tid; b < F; b += blockDim.x) {
+    sll += __ldcg(p.llpart + b);
+    sld += __ldcg(p.logdet + b);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sll += __shfl_xor_sync(0xffffffffu, sll, off);
+    sld += __shfl_xor_sync(0xffffffffu, sld, off);
+  }
+  __shared__ double red2_s[2][MAXM];
+  if (lane == 0) { red2_s[0][warp] = sll; red2_s[1][warp] = sld; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, d = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red2_s[0][w]; d += red2_s[1][w]; }
+    const double ll = a + (double)T * d - (double)F * T * M * 1.1447298858494002;  // log(pi)
+    *p.ll = ll;
+    if (!isfinite(ll)) flag(p.status, ST_NONFINITE);
   }
 }
 

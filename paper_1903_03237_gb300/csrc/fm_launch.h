@@ -11,10 +11,10 @@ enum KernelKind {
   KK_H = 1,      // H update (Eq. 24)
   KK_G = 2,      // g~ update (Eq. 21) + nu normalisation
   KK_Y = 3,      // y~ refresh, V_fm (Eq. 18), IP (Eqs. 19-20) + phi normalisation
-  KK_XT = 4,     // x~, log-likelihood (Eq. 17), mu normalisation
+  KK_XT = 4,     // x~, log-likelihood (Eq. 17) (long mixtures), mu normalisation
   KK_PREP = 5,   // per-bin float64 preparation (log-det, Q^-1)
   KK_SEP = 6,    // Wiener filter (Eq. 3)
-  KK_IP = 7,     // IP solve (Eqs. 19-20) + per-bin normalisation
+  KK_IP = 7,     // IP solve (Eqs. 19-20) + per-bin normalisation (+ x~ and log-likelihood terms)
   KK_GL = 8,     // mixed form: lambda = W^T H on the tensor cores
   KK_GW = 9,     // mixed form: W numerator / denominator GEMM
   KK_GH = 10,    // mixed form: H numerator / denominator GEMM
@@ -33,6 +33,7 @@ struct LaunchArgs {
   int S = 0;              // k_ip: number of V_fm splits
   unsigned ctr = 0;       // first arrival counter of this launch
   int n_pt_blocks = 0;    // k_xt_ll
+  int xt_mode = 0;        // k_ip: also x~ and the log-likelihood of its bin
   int apply_phi = 0;      // k_xt_ll
   int do_mu = 0;          // k_xt_ll
   float2* out = nullptr;  // k_separate

@@ -35,6 +35,7 @@ EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "
            "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
            "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc",
            "fmnmf_batch_create", "fmnmf_batch_iterate", "fmnmf_batch_sync", "fmnmf_batch_destroy",
+           "fmnmf_autotune", "fmnmf_batch_autotune", "fmnmf_get_tuning", "fmnmf_set_tuning",
            "fmnmf_footprint", "fmnmf_server_create", "fmnmf_server_submit", "fmnmf_server_poll",
            "fmnmf_server_wait", "fmnmf_server_result", "fmnmf_server_stats", "fmnmf_server_destroy"]
 
@@ -70,6 +71,10 @@ _sig = {
     "fmnmf_batch_create": (_S, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     "fmnmf_batch_iterate": (_S, [_P, _I]),
     "fmnmf_batch_sync": (_S, [_P]),
+    "fmnmf_autotune": (_S, [_P, _I, ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_batch_autotune": (_S, [_P, _I, ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_get_tuning": (_S, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "fmnmf_set_tuning": (_S, [_P, ctypes.POINTER(ctypes.c_float)]),
     "fmnmf_batch_destroy": (_S, [_P]),
     "fmnmf_footprint": (_S, [_I, _I, _I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]),
     "fmnmf_server_create": (_S, [_P, ctypes.POINTER(_P)]),
@@ -249,6 +254,21 @@ class Context:
     def launch_count(self) -> int:
         return int(_lib.fmnmf_launch_count(self._ctx))
 
+    def autotune(self, n_iter: int = 2) -> float:
+        """Times the launch-shape candidates (state restored afterwards); returns the speedup."""
+        sp = ctypes.c_double()
+        _check(_lib.fmnmf_autotune(self._ctx, n_iter, ctypes.byref(sp)), self._ctx)
+        return sp.value
+
+    def get_tuning(self) -> list:
+        v = (ctypes.c_float * 8)()
+        _check(_lib.fmnmf_get_tuning(self._ctx, v), self._ctx)
+        return list(v)
+
+    def set_tuning(self, scales):
+        v = (ctypes.c_float * 8)(*scales)
+        _check(_lib.fmnmf_set_tuning(self._ctx, v), self._ctx)
+
 
 class Batch:
     """Several contexts iterated by one graph launch (one concurrent branch per context)."""
@@ -264,6 +284,12 @@ class Batch:
 
     def sync(self):
         _check(_lib.fmnmf_batch_sync(self._b), None)
+
+    def autotune(self, n_iter: int = 2) -> float:
+        """One split scale for all members, timed on the whole batch; returns the speedup."""
+        sp = ctypes.c_double()
+        _check(_lib.fmnmf_batch_autotune(self._b, n_iter, ctypes.byref(sp)), None)
+        return sp.value
 
     def close(self):
         if self._b:

@@ -55,3 +55,27 @@ def test_batch_then_alone_orders(fm):
     ref.iterate(5)
     for x, y in zip(a.get_state(), ref.get_state()):
         np.testing.assert_array_equal(x, y)
+
+
+def test_batch_autotune_restores_state_and_matches_tuned_alone(fm):
+    mixes = [make_mixture(F, T, M, N, K, 1000 + i) for i, (F, T, M, N, K, _) in enumerate(CASES)]
+    ctxs = [fm.Context(m.X, c[3], c[4], seed=i, precision=c[5]) for i, (m, c) in enumerate(zip(mixes, CASES))]
+    with fm.Batch(ctxs) as b:
+        b.iterate(2)
+        b.sync()
+        before = [c.get_state() for c in ctxs]
+        sp = b.autotune(2)
+        assert sp >= 1.0
+        # the tuner's trials leave every member's state as it was
+        for c, st in zip(ctxs, before):
+            for x, y in zip(c.get_state(), st):
+                np.testing.assert_array_equal(x, y)
+        b.iterate(3)
+        b.sync()
+    for i, (m, c) in enumerate(zip(mixes, CASES)):
+        alone = fm.Context(m.X, c[3], c[4], seed=i, precision=c[5])
+        alone.iterate(2)                      # the planned shapes, as the batch before tuning
+        alone.set_tuning(ctxs[i].get_tuning())
+        alone.iterate(3)
+        for x, y in zip(ctxs[i].get_state(), alone.get_state()):
+            np.testing.assert_array_equal(x, y)

@@ -31,10 +31,12 @@ def fm():
     return fastmnmf
 
 
-def _mixed_errors(fm, F, T, M, N, K, precision, seed=1, diffuse=0.0):
+def _mixed_errors(fm, F, T, M, N, K, precision, seed=1, diffuse=0.0, tuning=None):
     mix = make_mixture(F, T, M, N, K, seed, diffuse_frac=diffuse)
     W, H, G, Q = make_state(F, T, M, N, K, seed)
     ctx = fm.Context(mix.X, N, K, precision=precision)
+    if tuning is not None:
+        ctx.set_tuning(tuning)
     ctx.set_state(W, H, G, Q)
     ctx.iterate(1)
     ll = ctx.loglik()
@@ -84,3 +86,9 @@ def test_mixed_trajectory_monotone(fm):
     d = np.diff(lls)
     # rounding of the BF16 contractions may cost a tiny decrease; the trend must rise
     assert lls[-1] > lls[0] and d.min() > -1e-4 * abs(lls[0]), (d.min(), lls)
+
+
+@pytest.mark.parametrize("scale", [0.5, 0.125])
+def test_mixed_tuned_shapes(fm, scale):
+    err = _mixed_errors(fm, 70, 600, 8, 6, 32, fm.PREC_BF16, tuning=[scale] * 8)
+    assert max(err[k] for k in ("W", "H", "G", "Q", "LL", "separated")) < TOL_MIXED, err

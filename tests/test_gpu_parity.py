@@ -43,10 +43,12 @@ SHAPES = [
 ]
 
 
-def _one_iter_case(fm, F, T, M, N, K, seed=1, mask=O.UPDATE_ALL, normalise=True):
+def _one_iter_case(fm, F, T, M, N, K, seed=1, mask=O.UPDATE_ALL, normalise=True, tuning=None):
     mix = make_mixture(F, T, M, N, K, seed)
     W, H, G, Q = make_state(F, T, M, N, K, seed)
     ctx = fm.Context(mix.X, N, K, seed=0, update_mask=mask, normalise=normalise)
+    if tuning is not None:
+        ctx.set_tuning(tuning)
     ctx.set_state(W, H, G, Q)
     X64 = mix.X.astype(np.complex128)
     ll0 = ctx.loglik()
@@ -65,6 +67,31 @@ def _one_iter_case(fm, F, T, M, N, K, seed=1, mask=O.UPDATE_ALL, normalise=True)
 def test_one_iteration_matches_oracle(fm, shape):
     err = _one_iter_case(fm, *shape)
     assert max(err.values()) < TOL, err
+
+
+def test_long_mixture_separate_xt_kernel(fm):
+    # more than 1024 frames: x~ and the log-likelihood run in their own kernel after the IP
+    err = _one_iter_case(fm, 9, 1100, 3, 2, 4, seed=5)
+    assert max(err.values()) < TOL, err
+
+
+@pytest.mark.parametrize("scale", [0.5, 0.125])
+def test_tuned_shapes_match_oracle(fm, scale):
+    # fewer inner splits (the tuner's candidates) change only the order of the split sums
+    err = _one_iter_case(fm, 70, 300, 4, 3, 16, seed=4, tuning=[scale] * 8)
+    assert max(err.values()) < TOL, err
+
+
+def test_autotune_restores_state(fm):
+    mix = make_mixture(65, 260, 4, 3, 16, 8)
+    ctx = fm.Context(mix.X, 3, 16, seed=2)
+    ctx.iterate(2)
+    st, ll = ctx.get_state(), ctx.loglik()
+    assert ctx.autotune(2) >= 1.0
+    for a, b in zip(ctx.get_state(), st):
+        np.testing.assert_array_equal(a, b)
+    assert ctx.loglik() == ll
+    assert all(0 < v <= 1 for v in ctx.get_tuning())
 
 
 @pytest.mark.parametrize("mask", [O.UPDATE_W, O.UPDATE_H, O.UPDATE_G, O.UPDATE_Q],
