@@ -85,13 +85,13 @@ def roofline_for(dom, avg_ms, precision, F, T, M, N, K, workload):
     if precision == "fp32" and kernel_flops(dom, F, T, M, N, K) > 0:
         achieved = kernel_flops(dom, F, T, M, N, K) / (avg_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": read_traffic(dom, workload), "kernel": dom,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": read_traffic(dom, workload, precision), "kernel": dom,
                 "avg_launch_us": avg_ms * 1e3,
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (max SM clock)"}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = kernel_bytes(dom, F, T, M, N, K) / (avg_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": read_traffic(dom, workload), "kernel": dom, "avg_launch_us": avg_ms * 1e3,
+            "traffic": read_traffic(dom, workload, precision), "kernel": dom, "avg_launch_us": avg_ms * 1e3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 
 
@@ -103,14 +103,15 @@ def read_peaks():
         return None
 
 
-def read_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary (None if not captured)."""
+def read_traffic(kernel: str, workload: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary (None if not captured for this
+    kernel, workload and form)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         for line in open(path):
             parts = line.split()
-            if len(parts) >= 3 and parts[0] == kernel and parts[1] == workload:
-                return float(parts[2])
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == precision:
+                return float(parts[3])
     except OSError:
         pass
     return None
@@ -292,6 +293,9 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev_id if sample_clocks else None) as clocks:
+        # NVTX range "timed" (main form only): lets ncu capture exactly the timed launches
+        if sample_clocks:
+            torch.cuda.nvtx.range_push("timed")
         for i in range(steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))
@@ -299,6 +303,8 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
             step()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
+        if sample_clocks:
+            torch.cuda.nvtx.range_pop()
     ctx.sync()
     launches = ctx.launch_count() - launches0
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
