@@ -182,6 +182,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float, device) -> float:
+    """The maximum of a per-rank figure over all ranks (a job lasts as long as its slowest
+    rank); the value itself without a process group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput of replicas: the units all ranks processed over the slowest time."""
+    return units_per_rank * world / max_seconds
+
+
 def oracle_iteration_rate(mix, W, H, G, Q, n_iter: int):
     """Times the float64 oracle (as it stands) on the host; returns (rate, cores, seconds)."""
     from oracle import fastmnmf_oracle as O
@@ -309,11 +326,8 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
     launches = ctx.launch_count() - launches0
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     kt = ctx.kernel_times()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = F * T * iters * steps * world / (total_ms / 1e3)
+    total_ms = reduce_max(total_ms, "cuda")
+    value = job_rate(F * T * iters * steps, world, total_ms / 1e3)
 
     # roofline of the dominant kernel, from its launches inside the timed region
     avg_ms = kt[dom][0] / kt[dom][1]
@@ -335,12 +349,8 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
         ctx.iterate(iters)
         ctx.separate(outh)  # synchronises (host output)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_val = F * T * iters * len(e2e_s) * world / e2e_total
+    e2e_total = reduce_max(sum(e2e_s), "cuda")
+    e2e_val = job_rate(F * T * iters * len(e2e_s), world, e2e_total)
     ctx.close()
     return {"value": value, "ms_per_step": total_ms / steps, "roofline": roofline, "launches": launches,
             "e2e": e2e_val, "shares": shares, "avg_us": avg_all, "clocks": clocks.summary(), "tune": tune}

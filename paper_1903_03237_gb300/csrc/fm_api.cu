@@ -270,7 +270,10 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     };
     plan_gemm(ctx->gpW, F, K, T, 2 * N, nt_for(K), true);
     plan_gemm(ctx->gpH, T, K, F, 2 * N, nt_for(K), true);
-    plan_gemm(ctx->gpL, F, T, K, N, 128, false);
+    // lambda: the widest column tile that still gives about two waves of CTAs
+    int ntL = 128;
+    while (ntL > 32 && (long long)((F + 127) / 128) * ((T + ntL - 1) / ntL) * N < 2LL * sms) ntL /= 2;
+    plan_gemm(ctx->gpL, F, T, K, N, ntL, false);
     // V_fm: bin groups x T splits.  Enough splits for two waves, then the split count (up
     // to twice that) whose last wave is fullest; spans are whole stages.
     const int nb = (F + scm_bins_per_cta(mx) - 1) / scm_bins_per_cta(mx);

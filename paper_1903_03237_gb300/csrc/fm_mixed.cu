@@ -33,10 +33,21 @@ __global__ void __launch_bounds__(kThreads) k_pr(Prob p, float* __restrict__ PR,
   if (pt >= npts) return;
   const int f = (int)(pt / (unsigned)T);
   float y[MAXM], x[MAXM];
+  if (M == MAXM && MAXM % 4 == 0) {  // whole points as float4
 #pragma unroll
-  for (int m = 0; m < MAXM; ++m) {
-    x[m] = (m < M) ? p.xt[(size_t)pt * M + m] : 0.f;
-    y[m] = (mode == 0 && m < M) ? p.yt[(size_t)pt * M + m] : 0.f;
+    for (int q = 0; q < MAXM / 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(p.xt + (size_t)pt * MAXM + 4 * q);
+      x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+      const float4 w = mode == 0 ? *reinterpret_cast<const float4*>(p.yt + (size_t)pt * MAXM + 4 * q)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[4 * q] = w.x; y[4 * q + 1] = w.y; y[4 * q + 2] = w.z; y[4 * q + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      x[m] = (m < M) ? p.xt[(size_t)pt * M + m] : 0.f;
+      y[m] = (mode == 0 && m < M) ? p.yt[(size_t)pt * M + m] : 0.f;
+    }
   }
   if (mode == 1) {
     for (int n = 0; n < N; ++n) {
