@@ -75,6 +75,8 @@ struct fmnmf_ctx {
   GemmPlan gpW, gpH, gpL;
   int scmS = 1, scmSpan = 64;  // tensor-core V_fm: T splits and frames per split
   int gtcNP = 0, gtcS = 1, gtcSpan = 16;  // tensor-core g~ update (NP = 0: the CUDA-core sweep)
+  bool gtcTma = false;                     // tensor maps of x~ and lambda for its inputs
+  alignas(64) CUtensorMap gtcTmX, gtcTmL;
   // launch shapes: the split counts plan() chose for the tunable launches, and the tuner's
   // scales of them (<= 1: buffers are sized for the planned counts)
   int caps[4] = {0, 0, 0, 0};
@@ -446,6 +448,11 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
     l.B = p.H; l.sBb = (long long)K * T; l.sBj = 1; l.sBk = T; l.bmodB = (int)N;
     l.C = ctx->lam; l.sCs = 0; l.sCb = FT; l.sCi = T; l.sCj = 1;
     l.status = p.status;
+    if (ctx->gtcNP > 0) {
+      Prob q = p;
+      q.lam = ctx->lam;
+      ctx->gtcTma = gtc_tensor_maps(ctx->maxm, q, &ctx->gtcTmX, &ctx->gtcTmL);
+    }
   }
   CK(cudaMemsetAsync(p.counters, 0, (size_t)nctr * 4, ctx->st));
   CK(cudaMemsetAsync(p.status, 0, 4, ctx->st));
@@ -588,7 +595,8 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
       q.lam = c->lam;
       if ((e = rec.run_fn(KK_G, [&] {
              c->launches++;
-             return launch_g_tc(c->maxm, c->gtcNP, q, c->gtcS, c->gtcSpan, c->ctrG, c->st);
+             return launch_g_tc(c->maxm, c->gtcNP, q, c->gtcS, c->gtcSpan, c->ctrG, c->gtcTma ? &c->gtcTmX : nullptr,
+                                c->gtcTma ? &c->gtcTmL : nullptr, c->st);
            })) != cudaSuccess)
         return e;
     } else {

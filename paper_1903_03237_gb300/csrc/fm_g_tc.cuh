@@ -12,13 +12,16 @@
 // added into registers.
 //
 // The kernel follows the V_fm kernel's organisation: warps 0-3 form the operands and own
-// the TMEM lanes, warp 4 issues the TMA copies of the x~ and lambda rows (two stages ahead,
-// when 16-byte aligned: T*M and T multiples of 4) and the MMAs; they meet at mbarriers.
-// Per stage of 16 frames a thread forms, for one (bin, 8 frames, channel), y~ from lambda
-// and g~, the A rows x~/y~^2 and 1/y~, and some (bin, 8 frames, source) rows of lambda.
+// the TMEM lanes, warp 4 issues the MMAs and the TMA tile copies of the x~ and lambda boxes
+// (tensor maps; kGtcIn stages ahead, when T is a multiple of 4); they meet at mbarriers.
+// Shared-memory layouts: x~ [bin][frame][channel], lambda [source][bin][frame].
+// Per stage of 32 frames the threads form, per (bin, 8 frames, channel), y~ from lambda and
+// g~ and the A rows x~/y~^2 and 1/y~, and per (bin, 8 frames, source) the lambda rows.
 // Each split writes partial sums part[S][2][N][F][M]; the last CTA of a bin group to
 // finish sums them in split order and applies the update.
 #pragma once
+#include <cuda.h>
+
 #include "fm_common.cuh"
 #include "fm_kernels.cuh"
 #include "fm_tc.cuh"
@@ -26,8 +29,9 @@
 namespace fm {
 
 constexpr int kGtcThreads = 128;
-constexpr int kGtcKc = 16;           // frames per stage (one BF16 MMA k-step)
+constexpr int kGtcKc = 32;           // frames per stage (two BF16 MMA k-steps)
 constexpr int kGtcBlockFrames = 256;
+constexpr int kGtcIn = 2;            // input stages in flight (TMA runs up to 2 stages ahead)
 
 template <int MAXM, int NP>
 struct GtcCfg {
@@ -39,21 +43,25 @@ struct GtcCfg {
   static constexpr int OPS = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int XT_BYTES = FG * kGtcKc * MAXM * 4;  // one stage of x~ rows
   static constexpr uint32_t TCOLS = 2 * NC < 32 ? 32 : 2 * NC;
-  static constexpr int NB_ITEMS = FG * 2 * NP;   // lambda rows (bin, frame group, source)
+  static constexpr int NFG = kGtcKc / 8;         // 8-frame groups per stage
+  static constexpr int NA_ITEMS = FG * NFG * MAXM;  // A items (bin, frame group, channel)
+  static constexpr int NB_ITEMS = FG * NFG * NP;    // lambda rows (bin, frame group, source)
   static_assert(NC >= 16 && NC <= 256 && NC % 16 == 0, "MMA N");
   static_assert((32 / MAXM) * NP % 16 == 0, "a warp reads whole 16-column groups of its bins");
-  static_assert(FG * 2 * MAXM == kGtcThreads, "one (bin, frame group, channel) per thread");
+  static_assert(FG * MAXM == 64, "A rows (ab, bin, channel) fill the 128 MMA rows");
   __host__ __device__ static int lam_bytes(int N) { return FG * N * kGtcKc * 4; }
-  __host__ __device__ static int smem(int N) { return 2 * OPS + 2 * (XT_BYTES + lam_bytes(N)) + FG * N * MAXM * 4; }
+  __host__ __device__ static int smem(int N) { return 2 * OPS + kGtcIn * (XT_BYTES + lam_bytes(N)) + FG * N * MAXM * 4; }
 };
 
 template <int MAXM, int NP>
-__global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int span, unsigned ctr_base) {
+__global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int span, unsigned ctr_base, int tma,
+                                                              const __grid_constant__ CUtensorMap tm_xt,
+                                                              const __grid_constant__ CUtensorMap tm_lam) {
   using C = GtcCfg<MAXM, NP>;
   constexpr int KC = kGtcKc;
   extern __shared__ __align__(1024) unsigned char ssm[];
   __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ __align__(8) uint64_t xbar[2];
+  __shared__ __align__(8) uint64_t xbar[kGtcIn];
   __shared__ __align__(8) uint64_t rbar[2];
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -63,20 +71,19 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
   const int tbeg = s * span, tend = min(T, tbeg + span);
   const int nst = tend > tbeg ? (tend - tbeg + KC - 1) / KC : 0;
   const int nbins = min(C::FG, F - f0);
-  // x~ rows start at byte 4*M*(f*T + t) and lambda rows at byte 4*((n*F + f)*T + t), t a
-  // multiple of 16: 16-byte aligned for every row iff T*M and T are multiples of 4 (and so
-  // are the copy lengths 4*M*nt and 4*nt)
-  const bool use_tma = ((T * M) & 3) == 0 && (T & 3) == 0;
+  // tma: the host encoded the tensor maps (T a multiple of 4, so that the row strides are
+  // multiples of 16 bytes); otherwise the inputs are loaded by the threads
+  const bool use_tma = tma != 0;
   const int IN_BYTES = C::XT_BYTES + C::lam_bytes(N);
-  auto xbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c & 1) * IN_BYTES); };
-  auto lbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c & 1) * IN_BYTES + C::XT_BYTES); };
-  float* gs = reinterpret_cast<float*>(ssm + 2 * C::OPS + 2 * IN_BYTES);  // g~ [FG][N][MAXM]
+  auto xbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c % kGtcIn) * IN_BYTES); };
+  auto lbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c % kGtcIn) * IN_BYTES + C::XT_BYTES); };
+  float* gs = reinterpret_cast<float*>(ssm + 2 * C::OPS + kGtcIn * IN_BYTES);  // g~ [FG][N][MAXM]
   constexpr int MMA_WARP = kGtcThreads / 32;
 
   if (warp == 0) { tmem_alloc(&tbase, C::TCOLS); tmem_relinquish(); }
   if (tid == 0) {
     mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1);
-    mbar_init(&xbar[0], 1); mbar_init(&xbar[1], 1);
+    for (int i = 0; i < kGtcIn; ++i) mbar_init(&xbar[i], 1);
     mbar_init(&rbar[0], kGtcThreads); mbar_init(&rbar[1], kGtcThreads);
   }
   for (int e = tid; e < C::FG * N * MAXM; e += kGtcThreads + 32) {
@@ -101,46 +108,52 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
 
   if (warp == MMA_WARP) {
     // ------------------------------ input copies and MMAs ------------------------------
+    // one tiled copy per array and stage: the x~ box (KC*M values of FG bins) and the lambda
+    // box (KC frames x FG bins x N sources); zero fill past T and F
     auto issue_in = [&](int c) {
-      const int t0 = tbeg + c * KC, nt = min(KC, tend - t0);
-      fence_async_smem();
-      if (lane == 0) mbar_expect_tx(&xbar[c & 1], (uint32_t)(nt * M * 4 + nt * 4 * N) * (uint32_t)nbins);
-      __syncwarp();
-      for (int g = lane; g < nbins; g += 32)
-        tma_bulk_g2s(xbuf(c) + g * KC * M, p.xt + ((size_t)(f0 + g) * T + t0) * M, (uint32_t)(nt * M * 4), &xbar[c & 1]);
-      for (int e = lane; e < nbins * N; e += 32) {
-        const int g = e / N, n = e % N;
-        tma_bulk_g2s(lbuf(c) + (g * N + n) * KC, p.lam + ((size_t)n * F + f0 + g) * T + t0, (uint32_t)(nt * 4),
-                     &xbar[c & 1]);
+      const int t0 = tbeg + c * KC;
+      if (lane == 0) {
+        fence_async_smem();
+        uint64_t* xb = &xbar[c % kGtcIn];
+        mbar_expect_tx(xb, (uint32_t)(C::XT_BYTES / MAXM * M + C::lam_bytes(N)));
+        tma_tile_2d(xbuf(c), &tm_xt, t0 * M, f0, xb);
+        tma_tile_3d(lbuf(c), &tm_lam, t0, f0, 0, xb);
       }
+      __syncwarp();
     };
     int issued = -1;
     if (use_tma) {
-      for (int c = 0; c < min(2, nst); ++c) issue_in(c);
-      issued = min(2, nst) - 1;
+      for (int c = 0; c < min(kGtcIn, nst); ++c) issue_in(c);
+      issued = min(kGtcIn, nst) - 1;
     }
     for (int c = 0; c < nst; ++c) {
       if (!mbar_wait(&rbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
       tc_fence_after();
-      if (use_tma && c + 2 < nst) { issue_in(c + 2); issued = c + 2; }
       if (lane == 0) {
         unsigned char* st = ssm + (c & 1) * C::OPS;
         const uint32_t acc = tacc + (uint32_t)(((c / C::SPB) & 1) * C::NC);
         const uint32_t sah = smem_u32(st), sal = sah + C::A_BYTES;
         const uint32_t sbh = sah + 2 * C::A_BYTES, sbl = sbh + C::B_BYTES;
         constexpr uint32_t ALBO = 128 * 16, BLBO = C::NC * 16;
-        const uint64_t ah = umma_desc(sah, ALBO, 128), al = umma_desc(sal, ALBO, 128);
-        const uint64_t bh = umma_desc(sbh, BLBO, 128), bl = umma_desc(sbl, BLBO, 128);
-        umma_f16(acc, ah, bh, idesc, (c % C::SPB != 0) ? 1u : 0u);
-        umma_f16(acc, ah, bl, idesc, 1u);
-        umma_f16(acc, al, bh, idesc, 1u);
+#pragma unroll
+        for (int q = 0; q < KC / 16; ++q) {
+          const uint64_t ah = umma_desc(sah + q * 2 * ALBO, ALBO, 128), al = umma_desc(sal + q * 2 * ALBO, ALBO, 128);
+          const uint64_t bh = umma_desc(sbh + q * 2 * BLBO, BLBO, 128), bl = umma_desc(sbl + q * 2 * BLBO, BLBO, 128);
+          umma_f16(acc, ah, bh, idesc, (c % C::SPB != 0 || q > 0) ? 1u : 0u);
+          umma_f16(acc, ah, bl, idesc, 1u);
+          umma_f16(acc, al, bh, idesc, 1u);
+        }
         umma_commit(&mbar[c & 1]);
       }
       __syncwarp();
+      // then the copies of stage c + kGtcIn into stage c's (consumed) input buffer: issuing
+      // the MMAs first keeps them off the copies' issue time
+      if (use_tma && c + kGtcIn < nst) { issue_in(c + kGtcIn); issued = c + kGtcIn; }
     }
     if (!ok) {
       if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-      for (int c = max(0, issued - 1); c <= issued; ++c) mbar_wait(&xbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries);
+      for (int c = max(0, issued - kGtcIn + 1); c <= issued; ++c)
+        mbar_wait(&xbar[c % kGtcIn], (uint32_t)((c / kGtcIn) & 1), kMaxTries);
     }
   } else {
     // ------------------------------ operand formation ------------------------------
@@ -162,13 +175,6 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
         }
       }
     };
-    // this thread's A item: (bin g, frame group, channel m); rows (ab, g, m)
-    const int a_m = tid % MAXM, a_g = (tid / MAXM) % C::FG, a_fgrp = tid / (MAXM * C::FG);
-    const bool a_ok = (a_g < nbins) && (a_m < M);
-    const int a_row = a_g * MAXM + a_m;
-    const uint32_t a_off0 = (uint32_t)(a_fgrp * (128 * 16) + a_row * 16);
-    const uint32_t a_off1 = a_off0 + 64 * 16;
-
     int c = 0;
     for (; c < nst; ++c) {
       const int t0 = tbeg + c * KC, nt = min(KC, tend - t0);
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       float* xs = xbuf(c);
       float* ls = lbuf(c);
       if (use_tma) {
-        if (!mbar_wait(&xbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
+        if (!mbar_wait(&xbar[c % kGtcIn], (uint32_t)((c / kGtcIn) & 1), kMaxTries)) { ok = false; break; }
       } else {
         for (int e = tid; e < nbins * nt * M; e += kGtcThreads) {
           const int g = e / (nt * M), j = e - g * (nt * M);
@@ -191,12 +197,17 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
         }
         for (int e = tid; e < nbins * N * nt; e += kGtcThreads) {
           const int gn = e / nt, t = e - gn * nt, g = gn / N, n = gn % N;
-          ls[gn * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
+          ls[(n * C::FG + g) * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
         }
         asm volatile("bar.sync 1, %0;\n" ::"n"(kGtcThreads) : "memory");
       }
-      // ---- A rows: x~/y~^2 and 1/y~ for 8 frames of (bin, channel) ----
-      {
+      // ---- A rows: x~/y~^2 and 1/y~ for 8 frames of (bin, channel); rows (ab, g, m) ----
+      for (int e = tid; e < C::NA_ITEMS; e += kGtcThreads) {
+        const int a_m = e % MAXM, a_g = (e / MAXM) % C::FG, a_fgrp = e / (MAXM * C::FG);
+        const bool a_ok = (a_g < nbins) && (a_m < M);
+        const int a_row = a_g * MAXM + a_m;
+        const uint32_t a_off0 = (uint32_t)(a_fgrp * (128 * 16) + a_row * 16);
+        const uint32_t a_off1 = a_off0 + 64 * 16;
         const int nv = min(8, nt - 8 * a_fgrp);
         float av[8], bv[8];
         if (a_ok && nv > 0) {
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
           for (int j = 0; j < 8; ++j) y[j] = 0.f;
           for (int n = 0; n < N; ++n) {
             const float gv = gs[(a_g * N + n) * MAXM + a_m];
-            const float* lp = ls + (a_g * N + n) * KC + 8 * a_fgrp;
+            const float* lp = ls + (n * C::FG + a_g) * KC + 8 * a_fgrp;
             const float4 l0 = *reinterpret_cast<const float4*>(lp);
             const float4 l1 = *reinterpret_cast<const float4*>(lp + 4);
             y[0] = fmaf(l0.x, gv, y[0]); y[1] = fmaf(l0.y, gv, y[1]); y[2] = fmaf(l0.z, gv, y[2]); y[3] = fmaf(l0.w, gv, y[3]);
@@ -233,11 +244,11 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       }
       // ---- B rows: lambda of 8 frames per (bin, source) ----
       for (int e = tid; e < C::NB_ITEMS; e += kGtcThreads) {
-        const int n = e % NP, g = (e / NP) % C::FG, fgrp = e / (NP * C::FG);
+        const int n = e % NP, g = (e / NP) % C::FG, fgrp = e / (NP * C::FG);  // fgrp < NFG
         const int nv = min(8, nt - 8 * fgrp);
         float lv8[8];
         if (g < nbins && n < N && nv > 0) {
-          const float* lp = ls + (g * N + n) * KC + 8 * fgrp;
+          const float* lp = ls + (n * C::FG + g) * KC + 8 * fgrp;
           const float4 l0 = *reinterpret_cast<const float4*>(lp);
           const float4 l1 = *reinterpret_cast<const float4*>(lp + 4);
           lv8[0] = l0.x; lv8[1] = l0.y; lv8[2] = l0.z; lv8[3] = l0.w;

@@ -1,6 +1,7 @@
 // Host-side launch interface of the FastMNMF kernels (one translation unit per channel
 // bucket MAXM in {2, 4, 8}; fm_api.cu dispatches on the bucket).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "fm_common.cuh"
 
@@ -65,7 +66,11 @@ cudaError_t scm_prepare(int maxm, int N);  // allow that much shared memory
 int scm_occupancy(int maxm, int N);        // resident k_scm_tc CTAs per SM
 // tensor-core g~ update (N padded to np sources; np = 0: N unsupported)
 int gtc_np(int maxm, int N);
-cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, cudaStream_t st);
+// tx, tl: tensor maps of x~ and lambda from gtc_tensor_maps, or null (the kernel's threads
+// then load the inputs)
+cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, const CUtensorMap* tx,
+                        const CUtensorMap* tl, cudaStream_t st);
+bool gtc_tensor_maps(int maxm, const Prob& p, CUtensorMap* tx, CUtensorMap* tl);
 cudaError_t gtc_prepare(int maxm, int np, int N);
 int gtc_occupancy(int maxm, int np, int N);
 int gtc_smem(int maxm, int np, int N);

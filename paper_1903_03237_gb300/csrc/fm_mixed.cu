@@ -11,6 +11,9 @@
 // sweeps; the IP, x~, log-likelihood and normalisation are those of the plain form.
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -197,11 +200,53 @@ int scm_occupancy(int maxm, int N) { return maxm == 2 ? scm_occ<2>(N) : maxm == 
 
 // ---- g~ update on the tensor cores ----
 template <int MAXM, int NP>
-static cudaError_t gtc_launch(const Prob& p, int S, int span, unsigned ctr, cudaStream_t st) {
+static cudaError_t gtc_launch(const Prob& p, int S, int span, unsigned ctr, const CUtensorMap* tx,
+                              const CUtensorMap* tl, cudaStream_t st) {
   using C = GtcCfg<MAXM, NP>;
   const dim3 grid((p.F + C::FG - 1) / C::FG, S);
-  k_g_tc<MAXM, NP><<<grid, kGtcThreads + 32, C::smem(p.N), st>>>(p, S, span, ctr);
+  CUtensorMap zero;
+  std::memset(&zero, 0, sizeof zero);
+  const bool tma = tx != nullptr && tl != nullptr;
+  k_g_tc<MAXM, NP><<<grid, kGtcThreads + 32, C::smem(p.N), st>>>(p, S, span, ctr, tma ? 1 : 0, tma ? *tx : zero,
+                                                                tma ? *tl : zero);
   return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+bool gtc_tensor_maps(int maxm, const Prob& p, CUtensorMap* tx, CUtensorMap* tl) {
+  // rows of x~ (T*M floats per bin) and lambda (T floats per source and bin) must start on
+  // 16-byte boundaries: T a multiple of 4
+  if (p.T % 4 != 0 || p.lam == nullptr || p.N > 256) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int FG = 64 / maxm, KC = kGtcKc;
+  const cuuint64_t dx[2] = {(cuuint64_t)p.T * p.M, (cuuint64_t)p.F};
+  const cuuint64_t sx[1] = {(cuuint64_t)p.T * p.M * 4};
+  const cuuint32_t bx[2] = {(cuuint32_t)(KC * p.M), (cuuint32_t)FG};
+  const cuuint32_t ex[2] = {1, 1};
+  if (enc(tx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p.xt, dx, sx, bx, ex, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t dl[3] = {(cuuint64_t)p.T, (cuuint64_t)p.F, (cuuint64_t)p.N};
+  const cuuint64_t sl[2] = {(cuuint64_t)p.T * 4, (cuuint64_t)p.F * p.T * 4};
+  const cuuint32_t bl[3] = {(cuuint32_t)KC, (cuuint32_t)FG, (cuuint32_t)p.N};
+  const cuuint32_t el[3] = {1, 1, 1};
+  return enc(tl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p.lam, dl, sl, bl, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 template <int MAXM, int NP>
 static cudaError_t gtc_configure(int N) {
@@ -243,8 +288,11 @@ static auto gtc_dispatch(int maxm, int np, Fn&& fn) {
     default: return fn(std::integral_constant<int, 2>(), std::integral_constant<int, 8>());
   }
 }
-cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, cudaStream_t st) {
-  return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return gtc_launch<decltype(mx)::value, decltype(n)::value>(p, S, span, ctr, st); });
+cudaError_t launch_g_tc(int maxm, int np, const Prob& p, int S, int span, unsigned ctr, const CUtensorMap* tx,
+                        const CUtensorMap* tl, cudaStream_t st) {
+  return gtc_dispatch(maxm, np, [&](auto mx, auto n) {
+    return gtc_launch<decltype(mx)::value, decltype(n)::value>(p, S, span, ctr, tx, tl, st);
+  });
 }
 cudaError_t gtc_prepare(int maxm, int np, int N) {
   return gtc_dispatch(maxm, np, [&](auto mx, auto n) { return gtc_configure<decltype(mx)::value, decltype(n)::value>(N); });

@@ -18,7 +18,7 @@
 //   - the X rows (per 8-frame group, into groups padded by 16 bytes so that the lanes'
 //     loads spread over the banks) and lambda rows of the FG bins arrive by TMA
 //     (cp.async.bulk with an mbarrier transaction count, issued by the lanes of warp 0)
-//     one stage ahead, when 16-byte aligned (T*M even, T a multiple of 4), else by plain
+//     IN stages ahead, when 16-byte aligned (T*M even, T a multiple of 4), else by plain
 //     loads;
 //   - y~ = sum_n lambda g~ for 8 frames per (bin, channel): written to the state (before
 //     the phi normalisation) and, as 1/y~, into the B operand (one 16-byte row each);
@@ -60,6 +60,9 @@ struct ScmCfg {
   static constexpr int X_BYTES = FG * NFG * (8 * MAXM + 2) * 8;
   static constexpr uint32_t TCOLS = 2 * NC < 32 ? 32 : 2 * NC;  // two accumulators
   static constexpr int NCW = (MAXM == 2) ? 16 : 8;       // accumulator columns a warp reads
+  // input stages in flight: TMA runs up to IN stages ahead (3 where the stage inputs are
+  // largest and the shared memory allows four CTAs per SM, else 2)
+  static constexpr int IN = (MAXM == 8) ? 3 : 2;
   static constexpr int NB_ITEMS = FG * MAXM * NFG;       // weight items (bin, m, 8 frames)
   static_assert(FG * MAXM * NFG * AP == kScmThreads, "one product item per thread");
   static_assert(kScmThreads % NB_ITEMS == 0, "weight items spread evenly over the threads");
@@ -69,7 +72,7 @@ struct ScmCfg {
     return b <= kScmLamMax ? b : 0;
   }
   __host__ __device__ static int smem(int N) {
-    return 2 * OPS + 2 * (X_BYTES + lam_bytes(N)) + FG * N * MAXM * 4;
+    return 2 * OPS + IN * (X_BYTES + lam_bytes(N)) + FG * N * MAXM * 4;
   }
 };
 
@@ -110,7 +113,7 @@ __device__ __forceinline__ void formation_sync() { asm volatile("bar.sync 1, %0;
 
 // EXACT: M == MAXM (a compile-time channel count in the address arithmetic).
 // Warps 0-3 form the operands and own the TMEM lanes (accumulator rows); warp 4 issues the
-// input copies (two stages ahead) and the MMAs.  They meet only at mbarriers:
+// input copies (IN stages ahead) and the MMAs.  They meet only at mbarriers:
 //   xbar[i]: the inputs of the stage in input buffer i landed (TMA transaction count);
 //   rbar[i]: the operands of the stage in operand buffer i are formed (128 arrivals), which
 //            also frees that stage's input buffer;
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
   constexpr int KC = C::KC;
   extern __shared__ __align__(1024) unsigned char ssm[];
   __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ __align__(8) uint64_t xbar[2];
+  __shared__ __align__(8) uint64_t xbar[ScmCfg<MAXM>::IN];
   __shared__ __align__(8) uint64_t rbar[2];
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -140,15 +143,15 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
   // T*M is even and T is a multiple of 4, and so are the copy lengths nf*M*8 and nt*4.
   const bool use_tma = ((T * M) & 1) == 0 && (T & 3) == 0;
   const int IN_BYTES = C::X_BYTES + LB;
-  auto xbuf = [&](int c) { return reinterpret_cast<float2*>(ssm + 2 * C::OPS + (c & 1) * IN_BYTES); };
-  auto lbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c & 1) * IN_BYTES + C::X_BYTES); };
-  float* gs = reinterpret_cast<float*>(ssm + 2 * C::OPS + 2 * IN_BYTES);  // g~ [FG][N][MAXM]
+  auto xbuf = [&](int c) { return reinterpret_cast<float2*>(ssm + 2 * C::OPS + (c % C::IN) * IN_BYTES); };
+  auto lbuf = [&](int c) { return reinterpret_cast<float*>(ssm + 2 * C::OPS + (c % C::IN) * IN_BYTES + C::X_BYTES); };
+  float* gs = reinterpret_cast<float*>(ssm + 2 * C::OPS + C::IN * IN_BYTES);  // g~ [FG][N][MAXM]
   constexpr int MMA_WARP = kScmThreads / 32;
 
   if (warp == 0) { tmem_alloc(&tbase, C::TCOLS); tmem_relinquish(); }
   if (tid == 0) {
     mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1);
-    mbar_init(&xbar[0], 1); mbar_init(&xbar[1], 1);
+    for (int i = 0; i < C::IN; ++i) mbar_init(&xbar[i], 1);
     mbar_init(&rbar[0], kScmThreads); mbar_init(&rbar[1], kScmThreads);
   }
   for (int e = tid; e < C::FG * N * MAXM; e += kScmThreads + 32) {
@@ -170,30 +173,28 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       const int t0 = tbeg + c * KC, nt = min(KC, tend - t0);
       const int ng = (nt + 7) >> 3;
       fence_async_smem();  // the formation warps' generic reads of this buffer came first
-      if (lane == 0) mbar_expect_tx(&xbar[c & 1], (uint32_t)(nt * M * 8 + (lam_s ? nt * 4 * N : 0)) * (uint32_t)nbins);
+      uint64_t* xb = &xbar[c % C::IN];
+      if (lane == 0) mbar_expect_tx(xb, (uint32_t)(nt * M * 8 + (lam_s ? nt * 4 * N : 0)) * (uint32_t)nbins);
       __syncwarp();
       for (int e = lane; e < nbins * ng; e += 32) {
         const int g = e / ng, k = e % ng, nf = min(8, nt - 8 * k);
         tma_bulk_g2s(xbuf(c) + (g * C::NFG + k) * GS, p.X + ((size_t)(f0 + g) * T + t0 + 8 * k) * M,
-                     (uint32_t)(nf * M * 8), &xbar[c & 1]);
+                     (uint32_t)(nf * M * 8), xb);
       }
       if (lam_s)
         for (int e = lane; e < nbins * N; e += 32) {
           const int g = e / N, n = e % N;
-          tma_bulk_g2s(lbuf(c) + (g * N + n) * KC, p.lam + ((size_t)n * F + f0 + g) * T + t0, (uint32_t)(nt * 4),
-                       &xbar[c & 1]);
+          tma_bulk_g2s(lbuf(c) + (g * N + n) * KC, p.lam + ((size_t)n * F + f0 + g) * T + t0, (uint32_t)(nt * 4), xb);
         }
     };
     int issued = -1;  // last input stage whose copies were issued
     if (use_tma) {
-      for (int c = 0; c < min(2, nst); ++c) issue_in(c);
-      issued = min(2, nst) - 1;
+      for (int c = 0; c < min(C::IN, nst); ++c) issue_in(c);
+      issued = min(C::IN, nst) - 1;
     }
     for (int c = 0; c < nst; ++c) {
       if (!mbar_wait(&rbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
       tc_fence_after();
-      // stage c's inputs are consumed: its input buffer takes stage c+2
-      if (use_tma && c + 2 < nst) { issue_in(c + 2); issued = c + 2; }
       if (lane == 0) {
         unsigned char* st = ssm + (c & 1) * C::OPS;
         const uint32_t acc = tacc + (uint32_t)(((c / C::SPB) & 1) * C::NC);
@@ -211,11 +212,15 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
         umma_commit(&mbar[c & 1]);
       }
       __syncwarp();
+      // then the copies of stage c + IN into stage c's (consumed) input buffer: issuing the
+      // MMAs first keeps them off the copies' issue time
+      if (use_tma && c + C::IN < nst) { issue_in(c + C::IN); issued = c + C::IN; }
     }
     if (!ok) {
       if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
       // copies still in flight land before the CTA releases its shared memory (bounded)
-      for (int c = max(0, issued - 1); c <= issued; ++c) mbar_wait(&xbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries);
+      for (int c = max(0, issued - C::IN + 1); c <= issued; ++c)
+        mbar_wait(&xbar[c % C::IN], (uint32_t)((c / C::IN) & 1), kMaxTries);
     }
   } else {
     // ------------------------------ operand formation ------------------------------
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       float2* xs = xbuf(c);
       float* ls = lbuf(c);
       if (use_tma) {
-        if (!mbar_wait(&xbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
+        if (!mbar_wait(&xbar[c % C::IN], (uint32_t)((c / C::IN) & 1), kMaxTries)) { ok = false; break; }
       } else {
         for (int e = tid; e < nbins * nt * M; e += kScmThreads) {
           const int g = e / (nt * M), j = e - g * (nt * M), t = j / M;
