@@ -77,6 +77,8 @@ struct fmnmf_ctx {
   int gtcNP = 0, gtcS = 1, gtcSpan = 16;  // tensor-core g~ update (NP = 0: the CUDA-core sweep)
   bool gtcTma = false;                     // tensor maps of x~ and lambda for its inputs
   alignas(64) CUtensorMap gtcTmX, gtcTmL;
+  bool scmTma = false;                     // tensor map of lambda for the V_fm kernel
+  alignas(64) CUtensorMap scmTmL;
   // launch shapes: the split counts plan() chose for the tunable launches, and the tuner's
   // scales of them (<= 1: buffers are sized for the planned counts)
   int caps[4] = {0, 0, 0, 0};
@@ -448,11 +450,10 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
     l.B = p.H; l.sBb = (long long)K * T; l.sBj = 1; l.sBk = T; l.bmodB = (int)N;
     l.C = ctx->lam; l.sCs = 0; l.sCb = FT; l.sCi = T; l.sCj = 1;
     l.status = p.status;
-    if (ctx->gtcNP > 0) {
-      Prob q = p;
-      q.lam = ctx->lam;
-      ctx->gtcTma = gtc_tensor_maps(ctx->maxm, q, &ctx->gtcTmX, &ctx->gtcTmL);
-    }
+    Prob q = p;
+    q.lam = ctx->lam;
+    if (ctx->gtcNP > 0) ctx->gtcTma = gtc_tensor_maps(ctx->maxm, q, &ctx->gtcTmX, &ctx->gtcTmL);
+    ctx->scmTma = scm_tensor_map(ctx->maxm, q, &ctx->scmTmL);
   }
   CK(cudaMemsetAsync(p.counters, 0, (size_t)nctr * 4, ctx->st));
   CK(cudaMemsetAsync(p.status, 0, 4, ctx->st));
@@ -612,7 +613,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     Prob q = c->p;
     q.lam = c->lam;
     // V_fm in split BF16 in either mixed form: single BF16 or TF32 operands miss the 1e-3 bar
-    if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, q, c->scmS, c->scmSpan, c->st); })) != cudaSuccess)
+    if ((e = rec.run_fn(KK_Y, [&] { c->launches++; return launch_scm_tc(c->maxm, q, c->scmS, c->scmSpan, c->scmTma ? &c->scmTmL : nullptr, c->st); })) != cudaSuccess)
       return e;
     ipS = c->scmS;
   } else {

@@ -58,7 +58,9 @@ cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStr
 cudaError_t configure_gemm();
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st);
 // V_fm split sums on the tensor cores (and y~), grid (ceil(F / bins per CTA), S).
-cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, cudaStream_t st);
+// tl: tensor map of lambda from scm_tensor_map, or null (per-row copies or plain loads)
+cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, const CUtensorMap* tl, cudaStream_t st);
+bool scm_tensor_map(int maxm, const Prob& p, CUtensorMap* tl);
 int scm_bins_per_cta(int maxm);
 int scm_frames_per_stage(int maxm);
 int scm_smem(int maxm, int N);             // dynamic shared memory of k_scm_tc for N sources

@@ -140,11 +140,14 @@ cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStr
 }
 
 template <int MAXM>
-static cudaError_t scm_launch(const Prob& p, int S, int span, cudaStream_t st) {
+static cudaError_t scm_launch(const Prob& p, int S, int span, const CUtensorMap* tl, cudaStream_t st) {
   using C = ScmCfg<MAXM>;
   const dim3 grid((p.F + C::FG - 1) / C::FG, S);
-  if (p.M == MAXM) k_scm_tc<MAXM, true><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span);
-  else k_scm_tc<MAXM, false><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span);
+  CUtensorMap zero;
+  std::memset(&zero, 0, sizeof zero);
+  const int tma = tl != nullptr;
+  if (p.M == MAXM) k_scm_tc<MAXM, true><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span, tma, tma ? *tl : zero);
+  else k_scm_tc<MAXM, false><<<grid, kScmThreads + 32, C::smem(p.N), st>>>(p, S, span, tma, tma ? *tl : zero);
   return cudaGetLastError();
 }
 // The kernel's shared memory grows with N (lambda rows and g~ staged per bin): raise the
@@ -182,10 +185,10 @@ cudaError_t configure_gemm() {
   return gemm_configure<128, false>();
 }
 
-cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, cudaStream_t st) {
-  if (maxm == 2) return scm_launch<2>(p, S, span, st);
-  if (maxm == 4) return scm_launch<4>(p, S, span, st);
-  return scm_launch<8>(p, S, span, st);
+cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, const CUtensorMap* tl, cudaStream_t st) {
+  if (maxm == 2) return scm_launch<2>(p, S, span, tl, st);
+  if (maxm == 4) return scm_launch<4>(p, S, span, tl, st);
+  return scm_launch<8>(p, S, span, tl, st);
 }
 
 int scm_bins_per_cta(int maxm) { return 128 / (maxm * maxm); }
@@ -226,6 +229,27 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// lambda [N][F][T] as a 3-D tensor (frames, bins, sources) with a (kc, fg, N) box.
+static bool lam_tensor_map(const Prob& p, int kc, int fg, CUtensorMap* tl) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || p.T % 4 != 0 || p.lam == nullptr || p.N > 256) return false;
+  const cuuint64_t dl[3] = {(cuuint64_t)p.T, (cuuint64_t)p.F, (cuuint64_t)p.N};
+  const cuuint64_t sl[2] = {(cuuint64_t)p.T * 4, (cuuint64_t)p.F * p.T * 4};
+  const cuuint32_t bl[3] = {(cuuint32_t)kc, (cuuint32_t)fg, (cuuint32_t)p.N};
+  const cuuint32_t el[3] = {1, 1, 1};
+  return enc(tl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p.lam, dl, sl, bl, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+bool scm_tensor_map(int maxm, const Prob& p, CUtensorMap* tl) {
+  const int fg = 128 / (maxm * maxm), kc = scm_frames_per_stage(maxm);
+  // only when the kernel stages lambda (its stage fits the shared-memory cap)
+  if ((maxm == 2 ? ScmCfg<2>::lam_bytes(p.N) : maxm == 4 ? ScmCfg<4>::lam_bytes(p.N) : ScmCfg<8>::lam_bytes(p.N)) == 0)
+    return false;
+  return lam_tensor_map(p, kc, fg, tl);
+}
+
 bool gtc_tensor_maps(int maxm, const Prob& p, CUtensorMap* tx, CUtensorMap* tl) {
   // rows of x~ (T*M floats per bin) and lambda (T floats per source and bin) must start on
   // 16-byte boundaries: T a multiple of 4
@@ -240,13 +264,7 @@ bool gtc_tensor_maps(int maxm, const Prob& p, CUtensorMap* tx, CUtensorMap* tl) 
   if (enc(tx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p.xt, dx, sx, bx, ex, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
-  const cuuint64_t dl[3] = {(cuuint64_t)p.T, (cuuint64_t)p.F, (cuuint64_t)p.N};
-  const cuuint64_t sl[2] = {(cuuint64_t)p.T * 4, (cuuint64_t)p.F * p.T * 4};
-  const cuuint32_t bl[3] = {(cuuint32_t)KC, (cuuint32_t)FG, (cuuint32_t)p.N};
-  const cuuint32_t el[3] = {1, 1, 1};
-  return enc(tl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p.lam, dl, sl, bl, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+  return lam_tensor_map(p, KC, FG, tl);
 }
 template <int MAXM, int NP>
 static cudaError_t gtc_configure(int N) {

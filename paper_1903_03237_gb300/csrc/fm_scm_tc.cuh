@@ -17,7 +17,8 @@
 // Per stage of KC frames (KC = 32 for MAXM 8 and 4, 16 for MAXM 2: 128 product items):
 //   - the X rows (per 8-frame group, into groups padded by 16 bytes so that the lanes'
 //     loads spread over the banks) and lambda rows of the FG bins arrive by TMA
-//     (cp.async.bulk with an mbarrier transaction count, issued by the lanes of warp 0)
+//     (cp.async.bulk with an mbarrier transaction count, issued by the lanes of warp 4; the
+//     lambda rows as one tiled copy through a tensor map when the host made one)
 //     IN stages ahead, when 16-byte aligned (T*M even, T a multiple of 4), else by plain
 //     loads;
 //   - y~ = sum_n lambda g~ for 8 frames per (bin, channel): written to the state (before
@@ -33,6 +34,8 @@
 // g = gq*GL + gl, GL = 8 / MAXM.
 // Split sums go to part[S][F][M][MAXM^2] for k_ip.
 #pragma once
+#include <cuda.h>
+
 #include "fm_common.cuh"
 #include "fm_tc.cuh"
 
@@ -119,7 +122,8 @@ __device__ __forceinline__ void formation_sync() { asm volatile("bar.sync 1, %0;
 //            also frees that stage's input buffer;
 //   mbar[i]: the MMAs of the stage in operand buffer i completed (tcgen05.commit).
 template <int MAXM, bool EXACT>
-__global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, int span) {
+__global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, int span, int lam_tma,
+                                                                const __grid_constant__ CUtensorMap tm_lam) {
   using C = ScmCfg<MAXM>;
   constexpr int KC = C::KC;
   extern __shared__ __align__(1024) unsigned char ssm[];
@@ -174,17 +178,23 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       const int ng = (nt + 7) >> 3;
       fence_async_smem();  // the formation warps' generic reads of this buffer came first
       uint64_t* xb = &xbar[c % C::IN];
-      if (lane == 0) mbar_expect_tx(xb, (uint32_t)(nt * M * 8 + (lam_s ? nt * 4 * N : 0)) * (uint32_t)nbins);
+      // lambda: one tiled copy of the (KC frames x FG bins x N sources) box through the tensor
+      // map (zero fill past T and F), else one copy per (bin, source) row
+      const uint32_t lam_tx = !lam_s ? 0u : lam_tma ? (uint32_t)LB : (uint32_t)(nt * 4 * N * nbins);
+      if (lane == 0) {
+        mbar_expect_tx(xb, (uint32_t)(nt * M * 8) * (uint32_t)nbins + lam_tx);
+        if (lam_s && lam_tma) tma_tile_3d(lbuf(c), &tm_lam, t0, f0, 0, xb);
+      }
       __syncwarp();
       for (int e = lane; e < nbins * ng; e += 32) {
         const int g = e / ng, k = e % ng, nf = min(8, nt - 8 * k);
         tma_bulk_g2s(xbuf(c) + (g * C::NFG + k) * GS, p.X + ((size_t)(f0 + g) * T + t0 + 8 * k) * M,
                      (uint32_t)(nf * M * 8), xb);
       }
-      if (lam_s)
+      if (lam_s && !lam_tma)
         for (int e = lane; e < nbins * N; e += 32) {
           const int g = e / N, n = e % N;
-          tma_bulk_g2s(lbuf(c) + (g * N + n) * KC, p.lam + ((size_t)n * F + f0 + g) * T + t0, (uint32_t)(nt * 4), xb);
+          tma_bulk_g2s(lbuf(c) + (n * C::FG + g) * KC, p.lam + ((size_t)n * F + f0 + g) * T + t0, (uint32_t)(nt * 4), xb);
         }
     };
     int issued = -1;  // last input stage whose copies were issued
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
         if (lam_s)
           for (int e = tid; e < nbins * N * nt; e += kScmThreads) {
             const int gn = e / nt, t = e - gn * nt, g = gn / N, n = gn % N;
-            ls[gn * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
+            ls[(n * C::FG + g) * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
           }
         formation_sync();
       }
@@ -309,8 +319,8 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
             const float gv = gs[(w_g * N + n) * MAXM + w_m];
             float l[8];
             if (lam_s) {
-              const float4 l0 = *reinterpret_cast<const float4*>(ls + (w_g * N + n) * KC + 8 * w_fgrp);
-              const float4 l1 = *reinterpret_cast<const float4*>(ls + (w_g * N + n) * KC + 8 * w_fgrp + 4);
+              const float4 l0 = *reinterpret_cast<const float4*>(ls + (n * C::FG + w_g) * KC + 8 * w_fgrp);
+              const float4 l1 = *reinterpret_cast<const float4*>(ls + (n * C::FG + w_g) * KC + 8 * w_fgrp + 4);
               l[0] = l0.x; l[1] = l0.y; l[2] = l0.z; l[3] = l0.w; l[4] = l1.x; l[5] = l1.y; l[6] = l1.z; l[7] = l1.w;
             } else {
 #pragma unroll
