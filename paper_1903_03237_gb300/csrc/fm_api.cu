@@ -61,6 +61,7 @@ struct fmnmf_ctx {
   Geom gW{}, gH{}, gG{}, gY{}, gS{};
   size_t smW = 0, smH = 0, smG = 0, smY = 0, smS = 0;
   int n_pt_blocks = 0, n_mu_blocks = 0;
+  size_t ipSmem = 0;  // the IP kernel's prefetch buffers (0: none)
   unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
   // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
   float* W0 = nullptr;
@@ -210,6 +211,10 @@ size_t sep_smem_bytes(int N, int K, int M, int maxm, int ic, bool lam_mem = fals
   return fl * 4 + 2 * (size_t)kOT * maxm * maxm * sizeof(float2);
 }
 
+// Mixtures of at most this many frames form x~ and the log-likelihood inside the IP kernel
+// (see enqueue_tail).
+constexpr int kFuseXtFrames = 1024;
+
 fmnmf_status plan(fmnmf_ctx* ctx) {
   const int F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K, mx = ctx->maxm;
   int dev = 0, sms = 0;
@@ -321,6 +326,12 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   }
   ctx->n_pt_blocks = (int)(((size_t)F * T + kThreads * kPtsPerThread - 1) / (kThreads * kPtsPerThread));
   ctx->n_mu_blocks = N * K;  // one CTA per (n, k) row
+  {
+    // the IP kernel prefetches the bin's X and y~ rows (when it forms x~), g~ and W
+    const size_t tm = (size_t)T * M;
+    const size_t pfb = (2 * tm + ((tm + 3) & ~(size_t)3) + (((size_t)N * M + 3) & ~(size_t)3) + (size_t)N * K) * 4;
+    ctx->ipSmem = (T <= kFuseXtFrames && pfb <= (size_t)kIpPrefetchMax) ? pfb : 0;
+  }
   for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
                               ctx->mixed ? ctx->gpW.g.ksplit : 1, ctx->mixed ? ctx->gpH.g.ksplit : 1};
@@ -504,7 +515,6 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec);
 // bin's update (one launch instead of two: the short mixtures are launch-latency bound),
 // then the mu normalisation runs.  Longer mixtures keep the separate x~ / log-likelihood
 // kernel, whose many small CTAs keep more loads in flight than one CTA per bin.
-constexpr int kFuseXtFrames = 1024;
 cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int norm) {
   cudaError_t e;
   if (yflags && c->T > kFuseXtFrames) {
@@ -526,6 +536,7 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
     a.p = c->p; a.st = c->st; a.flags = yflags; a.S = ipS;
     a.grid = dim3(c->F);
     a.xt_mode = 1; a.ctr = c->ctrLL;
+    a.smem = c->ipSmem;
     if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
     if (!norm) return cudaSuccess;
     LaunchArgs x;

@@ -709,8 +709,11 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 // new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the last CTA to finish adds
 // the bins up in bin order (Eq. 17).
 // ---------------------------------------------------------------------------------
+// With pf (dynamic shared memory for it given), the CTA prefetches at its start what the
+// later phases read but the IP does not change: the bin's X and y~ rows (x~ part) and its
+// g~ and W entries (normalisation), with cp.async, so those loads overlap the IP chain.
 template <int MAXM>
-__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr) {
+__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf) {
   constexpr int MM = MAXM * MAXM;
   __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
   __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
@@ -724,6 +727,30 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = p.M, N = p.N, K = p.K, F = p.F;
   if (f >= F) return;
+  // prefetch buffers: X row [T*M] complex, y~ row [T*M], g~ [N][M], W [N][K]
+  extern __shared__ __align__(16) float ipsm[];
+  const int TMq = p.T * M;
+  float2* pf_x = reinterpret_cast<float2*>(ipsm);
+  float* pf_y = ipsm + 2 * TMq;
+  float* pf_g = pf_y + ((TMq + 3) & ~3);
+  float* pf_w = pf_g + ((N * M + 3) & ~3);
+  if (pf) {
+    const size_t row = (size_t)f * TMq;
+    if (xt_mode) {
+      if ((TMq & 1) == 0)
+        for (int e = tid; e < TMq / 2; e += blockDim.x)
+          cpa16(reinterpret_cast<float*>(pf_x + 2 * e), reinterpret_cast<const float*>(p.X + row + 2 * e));
+      else
+        for (int e = tid; e < TMq; e += blockDim.x) cpa8(pf_x + e, p.X + row + e, true);
+      if ((TMq & 3) == 0)
+        for (int e = tid; e < TMq / 4; e += blockDim.x) cpa16(pf_y + 4 * e, p.yt + row + 4 * e);
+      else
+        for (int e = tid; e < TMq; e += blockDim.x) cpa4(pf_y + e, p.yt + row + e, true);
+    }
+    for (int e = tid; e < N * M; e += blockDim.x) cpa4(pf_g + e, p.G + ((size_t)(e / M) * F + f) * M + e % M, true);
+    for (int e = tid; e < N * K; e += blockDim.x) cpa4(pf_w + e, p.W + (size_t)e * F + f, true);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   for (int e = tid; e < M * M; e += blockDim.x) {
     const int r = e / M, c = e % M;
     Q_s[r * MAXM + c] = p.Qx[(size_t)f * M * M + e];
@@ -793,7 +820,10 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
         // s = Re(c^H q)
         df sv = df{0.f, 0.f};
         if (lane < M) sv = cdf_cmul(cdf_unpack(c_s[lane]), cdf_unpack(q_s[lane])).re;
-        for (int o = 16; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
+        // lanes < M hold the terms: a butterfly over the first MAXM lanes, then lane 0's
+        // sum to every lane (the Q_f^-1 update below runs on all 32 lanes)
+        for (int o = MAXM / 2; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
+        sv = df{__shfl_sync(0xffffffffu, sv.hi, 0), __shfl_sync(0xffffffffu, sv.lo, 0)};
         if (!(sv.hi > 0.f) || !isfinite(sv.hi)) { if (lane == 0) bad_s = 1; sv = df_make(1.f); }
         const df r = df_rsqrt(sv);
         ld_add += (double)logf(sv.hi) + (double)(sv.lo / sv.hi);
@@ -828,6 +858,8 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     }
     __syncthreads();
   }
+  if (pf) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();  // prefetched rows visible to every thread
   // phi normalisation and write-back
   __shared__ double phi_s;
   __shared__ float nu_s[64];
@@ -871,11 +903,12 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
       const int nn = min(64, N - n0);
       if (tid < nn) {
         float* gp = p.G + ((size_t)(n0 + tid) * F + f) * M;
+        const float* gsrc = pf ? pf_g + (n0 + tid) * M : gp;
         float gv[MAXM];
         float nu = 0.f;
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
-          if (m < M) { gv[m] = gp[m] / fphi; nu += gv[m]; }
+          if (m < M) { gv[m] = gsrc[m] / fphi; nu += gv[m]; }
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
           if (m < M) gp[m] = gv[m] / nu;
@@ -885,7 +918,8 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
       __syncthreads();
       for (int e = tid; e < nn * K; e += blockDim.x) {
         const int n = e / K, k = e - n * K;
-        p.W[((size_t)(n0 + n) * K + k) * F + f] *= nu_s[n];
+        float* wp = p.W + ((size_t)(n0 + n) * K + k) * F + f;
+        *wp = (pf ? pf_w[(n0 + n) * K + k] : *wp) * nu_s[n];
       }
       __syncthreads();
     }
@@ -902,7 +936,13 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     const size_t pt = (size_t)f * T + t;
     float2 x[MAXM];
     float yv[MAXM];
-    if (exact) {
+    if (pf) {
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        x[j] = (j < M) ? pf_x[t * M + j] : make_float2(0.f, 0.f);
+        yv[j] = (j < M) ? pf_y[t * M + j] : 1.f;
+      }
+    } else if (exact) {
 #pragma unroll
       for (int q = 0; q < MAXM / 2; ++q) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(p.X + pt * MAXM) + q);

@@ -19,7 +19,7 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
       break;
     case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p); break;
     case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;
-    case KK_IP: k_ip<MX><<<a.grid, MX * 32, 0, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr); break;
+    case KK_IP: k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -47,7 +47,8 @@ cudaError_t FM_CAT(configure_m, FM_MAXM)(int bytes) {
   if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_H>, A, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_G>, A, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_Y>, A, bytes)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_separate<MX>, A, bytes);
+  if ((e = cudaFuncSetAttribute(k_separate<MX>, A, bytes)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ip<MX>, A, kIpPrefetchMax);
 }
 
 }  // namespace fm
