@@ -64,9 +64,11 @@ __device__ __forceinline__ df df_mulf(df x, float y) {
   return fast_two_sum(p.hi, p.lo);
 }
 
-// Reciprocal: one Newton step on the float32 reciprocal, r = r0 + r0 (1 - x r0).
+// Reciprocal: the hardware estimate r0 (rcp.approx, a few ulp), then one Newton step
+// r = r0 + r0 (1 - x r0) with the residual in float-float; the relative error is about
+// the square of the estimate's, ~1e-13.
 __device__ __forceinline__ df df_rcp(df x) {
-  const float r0 = 1.0f / x.hi;
+  const float r0 = __fdividef(1.0f, x.hi);
   const df e = df_sub(df_make(1.f), df_mulf(x, r0));  // 1 - x r0
   return df_add(df_make(r0), df_mulf(e, r0));
 }
@@ -79,8 +81,18 @@ __device__ __forceinline__ df df_sqrt(df x) {
   const df e = df_sub(x, two_prod(s, s));
   return fast_two_sum(s, e.hi * (0.5f / s));
 }
-// 1/sqrt(x)
-__device__ __forceinline__ df df_rsqrt(df x) { return df_rcp(df_sqrt(x)); }
+// 1/sqrt(x) for x > 0: the hardware estimate r0 = rsqrtf(hi), then one Newton-Raphson
+// step r = r0 + r0 (1 - x r0^2) / 2 with x r0^2 in float-float (Karp & Markstein, "High-
+// precision division and square root", ACM TOMS 1997).  1 - x r0^2 is small, so its float
+// value suffices; the relative error is about 1.5 times the square of the estimate's, ~1e-13.
+__device__ __forceinline__ df df_rsqrt(df x) {
+  const float r0 = rsqrtf(x.hi);
+  const df t = df_mul(x, two_prod(r0, r0));
+  const float e = (1.f - t.hi) - t.lo;  // 1 - t.hi is exact (t.hi is within a few ulp of 1)
+  return fast_two_sum(r0, 0.5f * r0 * e);
+}
+// log(x) for x > 0 to float accuracy of log(hi), plus the first-order term of lo
+__device__ __forceinline__ df df_logf(df x) { return two_sum(logf(x.hi), __fdividef(x.lo, x.hi)); }
 
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 __device__ __forceinline__ df df_from_double(double d) {
@@ -112,5 +124,9 @@ __device__ __forceinline__ df shfl_xor_df(df v, int o) {
   return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 __device__ __forceinline__ cdf shfl_xor_cdf(cdf v, int o) { return cdf{shfl_xor_df(v.re, o), shfl_xor_df(v.im, o)}; }
+__device__ __forceinline__ df shfl_df(df v, int src) {
+  return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) { return cdf{shfl_df(v.re, src), shfl_df(v.im, src)}; }
 
 }  // namespace fm

@@ -709,6 +709,87 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 // new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the last CTA to finish adds
 // the bins up in bin order (Eq. 17).
 // ---------------------------------------------------------------------------------
+// The row sweep of the IP update for one bin (Eqs. 19-20), on one warp, with Q_f^-1 held
+// in registers: lane l holds the entries (i, j) with j = l % MAXM and i = l / MAXM + r * IG
+// (IG = 32 / MAXM, r < R; R = 2 for MAXM = 8, else 1, lanes >= MAXM^2 then idle).  Per row m:
+//   c = Q_f^-1 e_m (shuffled from the lanes that hold column m),
+//   q = T V_fm^-1 c              (sum over j: butterfly within the MAXM lanes of row i),
+//   s = Re(c^H q),  u~ = q^H Q_f^-1   (both a sum over i: one butterfly across the rows),
+//   r = 1/sqrt(s),  row m of Q_f <- (q r)^H,
+//   Q_f^-1 <- Q_f^-1 - c (r u~ - e_m^T) r       (Sherman-Morrison),  log|det Q_f|^2 += log s.
+// Entries outside M x M are zero and stay zero.  Q_f^-1 goes back to Qi_s at the end;
+// returns the sum of log s in float-float (lane 0), sets bad when some s is not positive
+// and finite.
+template <int MAXM>
+__device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q_s, float4* Qi_s, int M,
+                                      df Tdf, int lane, int& bad) {
+  constexpr int MM = MAXM * MAXM;
+  constexpr int R = MM > 32 ? MM / 32 : 1;
+  constexpr int IG = 32 / MAXM;
+  constexpr int LIM = MM < 32 ? MM : 32;  // lanes taking part in the sums over i
+  const int j = lane % MAXM, i0 = lane / MAXM;
+  bool ok[R];
+  cdf qi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + r * IG;
+    ok[r] = lane < MM && i < M && j < M;
+    qi[r] = ok[r] ? cdf_unpack(Qi_s[i * MAXM + j]) : cdf_zero();
+  }
+  df ld_add = df{0.f, 0.f};
+  for (int m = 0; m < M; ++m) {
+    cdf v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ok[r] ? cdf_unpack(Vi[m][(i0 + r * IG) * MAXM + j]) : cdf_zero();
+    // c_j = Qi[j][m] (lane (j % IG) MAXM + m, slot j / IG), c_i = Qi[i][m] (lane i0 MAXM + m, slot r)
+    cdf cj = cdf_zero(), ci[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const cdf a = shfl_cdf(qi[r], (j % IG) * MAXM + m);
+      if (j / IG == r) cj = a;
+      const cdf b = shfl_cdf(qi[r], i0 * MAXM + m);
+      ci[r] = (lane < MM && i0 + r * IG < M) ? b : cdf_zero();
+    }
+    cdf q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) q[r] = cdf_mul(v[r], cj);
+#pragma unroll
+    for (int o = 1; o < MAXM; o <<= 1)
+#pragma unroll
+      for (int r = 0; r < R; ++r) q[r] = cdf_add(q[r], shfl_xor_cdf(q[r], o));
+    df a = df{0.f, 0.f};
+    cdf b = cdf_zero();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      q[r] = cdf_scale(q[r], Tdf);
+      a = df_add(a, cdf_cmul(ci[r], q[r]).re);
+      b = cdf_add(b, cdf_cmul(q[r], qi[r]));
+    }
+    // a and b are the same on the MAXM lanes of a row: sum them over the rows
+#pragma unroll
+    for (int o = MAXM; o < LIM; o <<= 1) {
+      a = df_add(a, shfl_xor_df(a, o));
+      b = cdf_add(b, shfl_xor_cdf(b, o));
+    }
+    df sv = a;
+    if (!(sv.hi > 0.f) || !isfinite(sv.hi)) { bad = 1; sv = df_make(1.f); }
+    const df rs = df_rsqrt(sv);
+    if (lane == 0) ld_add = df_add(ld_add, df_logf(sv));
+    if (j == 0)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane < MM && i0 + r * IG < M) Q_s[m * MAXM + i0 + r * IG] = cdf_pack(cdf_conj(cdf_scale(q[r], rs)));
+    cdf uj = cdf_scale(b, rs);
+    if (j == m) uj.re = df_sub(uj.re, df_make(1.f));
+#pragma unroll
+    for (int r = 0; r < R; ++r) qi[r] = cdf_sub(qi[r], cdf_scale(cdf_mul(ci[r], uj), rs));
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (ok[r]) Qi_s[(i0 + r * IG) * MAXM + j] = cdf_pack(qi[r]);
+  return ld_add;
+}
+
 // With pf (dynamic shared memory for it given), the CTA prefetches at its start what the
 // later phases read but the IP does not change: the bin's X and y~ rows (x~ part) and its
 // g~ and W entries (normalisation), with cp.async, so those loads overlap the IP chain.
@@ -719,10 +800,9 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
   __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
   __shared__ float4 row_s[MAXM][MAXM];   // per warp: row k after scaling
   __shared__ float4 Q_s[MM], Qi_s[MM];
-  __shared__ float4 c_s[MAXM], q_s[MAXM], u_s[MAXM];
   __shared__ float vsum_s[MAXM][MM];      // packed split sums per m
   __shared__ double ld_s;
-  __shared__ int bad_s;
+  __shared__ int bad_s, rw_s;
   const int f = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = p.M, N = p.N, K = p.K, F = p.F;
@@ -756,7 +836,18 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     Q_s[r * MAXM + c] = p.Qx[(size_t)f * M * M + e];
     Qi_s[r * MAXM + c] = p.Qix[(size_t)f * M * M + e];
   }
-  if (tid == 0) { ld_s = p.logdet[f]; bad_s = 0; }
+  if (tid == 0) {
+    ld_s = p.logdet[f];
+    bad_s = 0;
+    // The single-warp phases (row sweep, phi) run on warp rw.  CTAs resident on one SM
+    // hold consecutive warp slots, and a slot's scheduler is its index mod 4: picking the
+    // warp from the CTA's slot index spreads those phases of co-resident CTAs over the
+    // four schedulers instead of stacking them all on the first one.
+    unsigned slot;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+    const int nw = (int)(blockDim.x >> 5);
+    rw_s = (int)((slot / nw) % nw);
+  }
   if (flags & FLAG_DO_V) {
     // packed split sums (float32, fixed order over the splits)
     const size_t psz = (size_t)F * M * MM;
@@ -800,79 +891,32 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
       if (!ok && lane == 0) bad_s = 1;
     }
     __syncthreads();
-    if (warp == 0) {
-      const df Tdf = df_make((float)p.T);
-      double ld_add = 0.0;
-      for (int m = 0; m < M; ++m) {
-        const float4* Vi = A_s[m];
-        if (lane < M) c_s[lane] = Qi_s[lane * MAXM + m];
-        __syncwarp();
-        // q_i = T sum_j Vi[i][j] c_j   (lanes: i = lane / MAXM, j = lane % MAXM, MAXM*MAXM <= 64)
-        for (int base = 0; base < MM; base += 32) {
-          const int e = base + lane;
-          const int i = e / MAXM, j = e % MAXM;
-          cdf t = cdf_zero();
-          if (e < MM && i < M && j < M) t = cdf_mul(cdf_unpack(Vi[i * MAXM + j]), cdf_unpack(c_s[j]));
-          for (int o = 1; o < MAXM; o <<= 1) t = cdf_add(t, shfl_xor_cdf(t, o));
-          if (e < MM && j == 0 && i < M) q_s[i] = cdf_pack(cdf_scale(t, Tdf));
-        }
-        __syncwarp();
-        // s = Re(c^H q)
-        df sv = df{0.f, 0.f};
-        if (lane < M) sv = cdf_cmul(cdf_unpack(c_s[lane]), cdf_unpack(q_s[lane])).re;
-        // lanes < M hold the terms: a butterfly over the first MAXM lanes, then lane 0's
-        // sum to every lane (the Q_f^-1 update below runs on all 32 lanes)
-        for (int o = MAXM / 2; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
-        sv = df{__shfl_sync(0xffffffffu, sv.hi, 0), __shfl_sync(0xffffffffu, sv.lo, 0)};
-        if (!(sv.hi > 0.f) || !isfinite(sv.hi)) { if (lane == 0) bad_s = 1; sv = df_make(1.f); }
-        const df r = df_rsqrt(sv);
-        ld_add += (double)logf(sv.hi) + (double)(sv.lo / sv.hi);
-        // q_new, row m of Q = q_new^H
-        if (lane < M) {
-          const cdf qn = cdf_scale(cdf_unpack(q_s[lane]), r);
-          q_s[lane] = cdf_pack(qn);
-          Q_s[m * MAXM + lane] = cdf_pack(cdf_conj(qn));
-        }
-        __syncwarp();
-        // u_j = sum_i conj(qn_i) Qi[i][j]   (lanes: j = lane / MAXM, i = lane % MAXM)
-        for (int base = 0; base < MM; base += 32) {
-          const int e = base + lane;
-          const int j = e / MAXM, i = e % MAXM;
-          cdf t = cdf_zero();
-          if (e < MM && i < M && j < M) t = cdf_cmul(cdf_unpack(q_s[i]), cdf_unpack(Qi_s[i * MAXM + j]));
-          for (int o = 1; o < MAXM; o <<= 1) t = cdf_add(t, shfl_xor_cdf(t, o));
-          if (e < MM && i == 0 && j < M) u_s[j] = cdf_pack(t);
-        }
-        __syncwarp();
-        // Qi[i][j] -= c_i (u_j - delta_jm) r
-        for (int e = lane; e < M * M; e += 32) {
-          const int i = e / M, j = e % M;
-          cdf uj = cdf_unpack(u_s[j]);
-          if (j == m) uj.re = df_sub(uj.re, df_make(1.f));
-          const cdf d = cdf_scale(cdf_mul(cdf_unpack(c_s[i]), uj), r);
-          Qi_s[i * MAXM + j] = cdf_pack(cdf_sub(cdf_unpack(Qi_s[i * MAXM + j]), d));
-        }
-        __syncwarp();
+    const int rw = rw_s;
+    if (warp == rw) {
+      int bad = 0;
+      const df ld_add = ip_rows<MAXM>(A_s, Q_s, Qi_s, M, df_make((float)p.T), lane, bad);
+      if (lane == 0) {
+        ld_s += df_to_double(ld_add);
+        if (bad) bad_s = 1;
       }
-      if (lane == 0) ld_s += ld_add;
     }
     __syncthreads();
   }
   if (pf) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();  // prefetched rows visible to every thread
   // phi normalisation and write-back
-  __shared__ double phi_s;
+  __shared__ float phi_s;
   __shared__ float nu_s[64];
   __shared__ float2 qf_s[MM];  // the normalised Q_f in float32 (x~ of this bin's frames)
-  if (warp == 0) {
-    double phi = 1.0;
-    df sq = df_make(1.f), isq = df_make(1.f);
+  const int rw = rw_s;
+  const int rtid = (tid + (int)blockDim.x - 32 * rw) % (int)blockDim.x;  // warp rw first
+  if (warp == rw) {
+    df ph = df_make(1.f), sq = df_make(1.f), isq = df_make(1.f);
     if (flags & FLAG_NORMALISE) {
       df tr = df{0.f, 0.f};
       for (int e = lane; e < M * M; e += 32) tr = df_add(tr, cdf_abs2(cdf_unpack(Q_s[(e / M) * MAXM + e % M])));
       for (int o = 16; o > 0; o >>= 1) tr = df_add(tr, shfl_xor_df(tr, o));
-      const df ph = df_div(tr, df_make((float)M));
-      phi = df_to_double(ph);
+      ph = df_div(tr, df_make((float)M));
       sq = df_sqrt(ph);
       isq = df_rcp(sq);
     }
@@ -887,10 +931,10 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
       p.Qinv[(size_t)f * M * M + e] = make_float2(qi.re.hi, qi.im.hi);
     }
     if (lane == 0) {
-      phi_s = phi;
-      const double ld = ld_s - (double)M * log(phi);
+      phi_s = ph.hi;
+      const double ld = ld_s - (double)M * df_to_double(df_logf(ph));
       p.logdet[f] = ld;
-      p.phi[f] = (float)phi;
+      p.phi[f] = ph.hi;
       if (bad_s) flag(p.status, ST_SINGULAR);
       if (!isfinite(ld)) flag(p.status, ST_NONFINITE);
     }
@@ -898,12 +942,12 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
   if (flags & FLAG_NORMALISE) {
     // g~_nf /= phi_f, then nu_nf = sum_m g~_nfm: g~_nf /= nu_nf, w_nkf *= nu_nf
     __syncthreads();
-    const float fphi = (float)phi_s;
+    const float fphi = phi_s;
     for (int n0 = 0; n0 < N; n0 += 64) {
       const int nn = min(64, N - n0);
-      if (tid < nn) {
-        float* gp = p.G + ((size_t)(n0 + tid) * F + f) * M;
-        const float* gsrc = pf ? pf_g + (n0 + tid) * M : gp;
+      if (rtid < nn) {
+        float* gp = p.G + ((size_t)(n0 + rtid) * F + f) * M;
+        const float* gsrc = pf ? pf_g + (n0 + rtid) * M : gp;
         float gv[MAXM];
         float nu = 0.f;
 #pragma unroll
@@ -912,7 +956,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
           if (m < M) gp[m] = gv[m] / nu;
-        nu_s[tid] = nu;
+        nu_s[rtid] = nu;
         if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
       }
       __syncthreads();
@@ -929,7 +973,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
   // and this bin's log-likelihood terms (Eq. 17); the last CTA adds the bins up
   __syncthreads();
   const int T = p.T;
-  const float ph = (float)phi_s;
+  const float ph = phi_s;
   const bool exact = (M == MAXM);
   float part = 0.f;
   for (int t = tid; t < T; t += blockDim.x) {
@@ -975,7 +1019,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
         const float y = yv[m] / ph;
         p.yt[pt * M + m] = y;
         p.xt[pt * M + m] = xv;
-        ls += -xv / y - logf(y);
+        ls += -__fdividef(xv, y) - __logf(y);  // the log-likelihood terms only: fast forms
       }
     }
     part += ls;
