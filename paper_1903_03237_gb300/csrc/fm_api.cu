@@ -62,6 +62,7 @@ struct fmnmf_ctx {
   size_t smW = 0, smH = 0, smG = 0, smY = 0, smS = 0;
   int n_pt_blocks = 0, n_mu_blocks = 0;
   size_t ipSmem = 0;  // the IP kernel's prefetch buffers (0: none)
+  bool fusedPR = false;  // the IP kernel forms P, R of the next W update (no separate launch)
   unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
   // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
   float* W0 = nullptr;
@@ -332,6 +333,12 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     const size_t pfb = (2 * tm + ((tm + 3) & ~(size_t)3) + (((size_t)N * M + 3) & ~(size_t)3) + (size_t)N * K) * 4;
     ctx->ipSmem = (T <= kFuseXtFrames && pfb <= (size_t)kIpPrefetchMax) ? pfb : 0;
   }
+  {
+    // mixed form, x~ formed in the IP kernel with its prefetch, and a W update to feed
+    const unsigned mask = ctx->opts.update_mask;
+    const bool ip_runs = ctx->opts.normalise || (mask & FMNMF_UPDATE_Q);
+    ctx->fusedPR = ctx->mixed && ip_runs && (mask & FMNMF_UPDATE_W) && T <= kFuseXtFrames && ctx->ipSmem > 0;
+  }
   for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
                               ctx->mixed ? ctx->gpW.g.ksplit : 1, ctx->mixed ? ctx->gpH.g.ksplit : 1};
@@ -537,12 +544,16 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
     a.grid = dim3(c->F);
     a.xt_mode = 1; a.ctr = c->ctrLL;
     a.smem = c->ipSmem;
+    a.pr = c->fusedPR ? c->PR : nullptr;
+    // with the mu normalisation to follow, its kernel adds up the log-likelihood (a last
+    // block beside the mu blocks) and the IP kernel skips its serial tail
+    a.ll_tail = norm ? 0 : 1;
     if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
     if (!norm) return cudaSuccess;
     LaunchArgs x;
     x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
-    x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = 1;
-    x.grid = dim3(c->n_mu_blocks);
+    x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = 1; x.ll_bins = 1;
+    x.grid = dim3(c->n_mu_blocks + 1);
     return rec.run(KK_XT, x);
   }
   LaunchArgs x;
@@ -590,7 +601,9 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     });
   };
   if (mask & FMNMF_UPDATE_W) {
-    if ((e = pr(0)) != cudaSuccess) return e;
+    // P, R of the W update: formed by the previous iteration's IP kernel (or by the state
+    // refresh) when fusedPR is set
+    if (!c->fusedPR && (e = pr(0)) != cudaSuccess) return e;
     if ((e = gemm(KK_GW, c->gpW)) != cudaSuccess) return e;
     if ((e = apply(c->p.W, c->gpW.g.ksplit, c->F)) != cudaSuccess) return e;
   }
@@ -655,6 +668,13 @@ fmnmf_status refresh_state(fmnmf_ctx* ctx) {
   x.p = ctx->p; x.st = ctx->st; x.ctr = ctx->ctrLL; x.n_pt_blocks = ctx->n_pt_blocks;
   x.apply_phi = 0; x.do_mu = 0; x.grid = dim3(ctx->n_pt_blocks);
   CK(launch(ctx, KK_XT, x));
+  if (ctx->fusedPR) {
+    // P, R of the first W update (later ones come from the IP kernel)
+    Prob q = ctx->p;
+    q.lam = ctx->lam;
+    ctx->launches++;
+    CK(launch_pr(ctx->maxm, q, ctx->PR, 0, ctx->st));
+  }
   return FMNMF_OK;
 }
 
@@ -773,6 +793,7 @@ fmnmf_status save_state(fmnmf_ctx* ctx, SavedState& sv) {
                {p.Qf, F * M * M * sizeof(float2)}, {p.Qinv, F * M * M * sizeof(float2)},
                {p.logdet, F * 8}, {p.phi, F * 4}, {p.xt, F * T * M * 4}, {p.yt, F * T * M * 4}, {p.ll, 8}};
   if (ctx->mixed) sv.arrays.push_back({ctx->lam, N * F * T * 4});
+  if (ctx->fusedPR) sv.arrays.push_back({ctx->PR, 2 * N * F * T * 4});  // P, R of the next W update
   size_t tot = 0;
   for (auto& a : sv.arrays) { sv.off.push_back(tot); tot += (a.second + 255) & ~(size_t)255; }
   cudaError_t e = cudaMallocAsync(&sv.buf, tot, ctx->st);

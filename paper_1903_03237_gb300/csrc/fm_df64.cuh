@@ -64,11 +64,10 @@ __device__ __forceinline__ df df_mulf(df x, float y) {
   return fast_two_sum(p.hi, p.lo);
 }
 
-// Reciprocal: the hardware estimate r0 (rcp.approx, a few ulp), then one Newton step
-// r = r0 + r0 (1 - x r0) with the residual in float-float; the relative error is about
-// the square of the estimate's, ~1e-13.
+// Reciprocal: one Newton step on the correctly rounded float32 reciprocal (any float
+// range), r = r0 + r0 (1 - x r0), with the residual in float-float.
 __device__ __forceinline__ df df_rcp(df x) {
-  const float r0 = __fdividef(1.0f, x.hi);
+  const float r0 = __frcp_rn(x.hi);
   const df e = df_sub(df_make(1.f), df_mulf(x, r0));  // 1 - x r0
   return df_add(df_make(r0), df_mulf(e, r0));
 }
@@ -86,13 +85,15 @@ __device__ __forceinline__ df df_sqrt(df x) {
 // precision division and square root", ACM TOMS 1997).  1 - x r0^2 is small, so its float
 // value suffices; the relative error is about 1.5 times the square of the estimate's, ~1e-13.
 __device__ __forceinline__ df df_rsqrt(df x) {
+  // outside [1e-30, 1e30] (r0^2 would leave the normal range): through sqrt and reciprocal
+  if (!(x.hi >= 1e-30f && x.hi <= 1e30f)) return df_rcp(df_sqrt(x));
   const float r0 = rsqrtf(x.hi);
   const df t = df_mul(x, two_prod(r0, r0));
   const float e = (1.f - t.hi) - t.lo;  // 1 - t.hi is exact (t.hi is within a few ulp of 1)
   return fast_two_sum(r0, 0.5f * r0 * e);
 }
 // log(x) for x > 0 to float accuracy of log(hi), plus the first-order term of lo
-__device__ __forceinline__ df df_logf(df x) { return two_sum(logf(x.hi), __fdividef(x.lo, x.hi)); }
+__device__ __forceinline__ df df_logf(df x) { return two_sum(logf(x.hi), x.lo / x.hi); }
 
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 __device__ __forceinline__ df df_from_double(double d) {

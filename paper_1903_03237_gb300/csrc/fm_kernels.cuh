@@ -709,6 +709,30 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 // new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the last CTA to finish adds
 // the bins up in bin order (Eq. 17).
 // ---------------------------------------------------------------------------------
+// P_n = sum_m g~_nfm x~_m / y~_m^2 and R_n = sum_m g~_nfm / y~_m at one TF point (the
+// per-point factors of the W and H updates, Eqs. 23-24), into PR[n][pt] and PR[N + n][pt]
+// (source stride ns).  g points at g~_{0f0}, source stride gs.  Every kernel that forms
+// them calls this one definition, so they all produce the same bits.
+template <int MAXM>
+__device__ __forceinline__ void pr_point(const float (&x)[MAXM], const float (&y)[MAXM], int M, int N,
+                                         const float* g, size_t gs, float* PR, size_t ns, size_t pt) {
+  float A[MAXM], B[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    B[m] = (m < M) ? __fdividef(1.f, y[m]) : 0.f;
+    A[m] = x[m] * B[m] * B[m];
+  }
+  for (int n = 0; n < N; ++n) {
+    const float* gn = g + (size_t)n * gs;
+    float P = 0.f, R = 0.f;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m)
+      if (m < M) { P = fmaf(gn[m], A[m], P); R = fmaf(gn[m], B[m], R); }
+    PR[(size_t)n * ns + pt] = P;
+    PR[(size_t)(N + n) * ns + pt] = R;
+  }
+}
+
 // The row sweep of the IP update for one bin (Eqs. 19-20), on one warp, with Q_f^-1 held
 // in registers: lane l holds the entries (i, j) with j = l % MAXM and i = l / MAXM + r * IG
 // (IG = 32 / MAXM, r < R; R = 2 for MAXM = 8, else 1, lanes >= MAXM^2 then idle).  Per row m:
@@ -793,8 +817,12 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
 // With pf (dynamic shared memory for it given), the CTA prefetches at its start what the
 // later phases read but the IP does not change: the bin's X and y~ rows (x~ part) and its
 // g~ and W entries (normalisation), with cp.async, so those loads overlap the IP chain.
+// With PR (and pf), the x~ part also forms P_n, R_n of its frames from the new x~, y~ and
+// the normalised g~ (the factors of the next W update).  With ll_tail == 0 the bins'
+// log-likelihood terms are left in llpart / logdet for a later kernel to add up.
 template <int MAXM>
-__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf) {
+__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf,
+                                                  float* __restrict__ PR, int ll_tail) {
   constexpr int MM = MAXM * MAXM;
   __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
   __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
@@ -955,7 +983,10 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
           if (m < M) { gv[m] = gsrc[m] / fphi; nu += gv[m]; }
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
-          if (m < M) gp[m] = gv[m] / nu;
+          if (m < M) {
+            gp[m] = gv[m] / nu;
+            if (pf) pf_g[(n0 + rtid) * M + m] = gv[m] / nu;  // the normalised g~ for P, R
+          }
         nu_s[rtid] = nu;
         if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
       }
@@ -1003,8 +1034,11 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
       }
     }
     float ls = 0.f;
+    float xa[MAXM], ya[MAXM];
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) {
+      xa[m] = 0.f;
+      ya[m] = 0.f;
       if (m < M) {
         float re = 0.f, im = 0.f;
 #pragma unroll
@@ -1019,10 +1053,13 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
         const float y = yv[m] / ph;
         p.yt[pt * M + m] = y;
         p.xt[pt * M + m] = xv;
-        ls += -__fdividef(xv, y) - __logf(y);  // the log-likelihood terms only: fast forms
+        xa[m] = xv;
+        ya[m] = y;
+        ls += -xv / y - logf(y);
       }
     }
     part += ls;
+    if (PR != nullptr && pf) pr_point<MAXM>(xa, ya, M, N, pf_g, (size_t)M, PR, (size_t)F * T, pt);
   }
   __shared__ double red_s[MAXM];
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
@@ -1033,7 +1070,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red_s[w];
     p.llpart[f] = sum;
   }
-  if (!arrive_last(p.counters + ctr, (unsigned)F)) return;
+  if (!ll_tail || !arrive_last(p.counters + ctr, (unsigned)F)) return;
   double sll = 0.0, sld = 0.0;
   for (int b = tid; b < F; b += blockDim.x) {
     sll += __ldcg(p.llpart + b);
@@ -1063,7 +1100,7 @@ constexpr int kPtsPerThread = 4;
 
 template <int MAXM>
 __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int apply_phi, int do_mu,
-                                                    unsigned ctr) {
+                                                    unsigned ctr, int ll_bins) {
   const int tid = threadIdx.x;
   const int M = p.M, T = p.T, F = p.F;
   if ((int)blockIdx.x < n_pt_blocks) {
@@ -1185,7 +1222,7 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
       *p.ll = ll;
       if (!isfinite(ll)) flag(p.status, ST_NONFINITE);
     }
-  } else if (do_mu) {
+  } else if ((int)blockIdx.x < n_pt_blocks + (do_mu ? p.N * p.K : 0)) {
     // mu_nk = sum_f w_nkf;  w_nk /= mu;  h_nk *= mu   (one CTA per (n, k) row)
     const int nk = (int)blockIdx.x - n_pt_blocks;
     float* __restrict__ w = p.W + (size_t)nk * F;
@@ -1202,6 +1239,28 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
     for (int f = tid; f < F; f += kThreads) w[f] *= inv;
     for (int t = tid; t < T; t += kThreads) h[t] *= mu;
     if (tid == 0 && !(mu > 0.f && isfinite(mu))) flag(p.status, ST_NONFINITE);
+  } else if (ll_bins) {
+    // the last block: the per-bin log-likelihood terms and log-dets that the IP kernel left,
+    // added up in bin order (Eq. 17)
+    double sll = 0.0, sld = 0.0;
+    for (int b = tid; b < F; b += kThreads) {
+      sll += __ldcg(p.llpart + b);
+      sld += __ldcg(p.logdet + b);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      sll += __shfl_xor_sync(0xffffffffu, sll, off);
+      sld += __shfl_xor_sync(0xffffffffu, sld, off);
+    }
+    __shared__ double red_ll[2][kThreads / 32];
+    if ((tid & 31) == 0) { red_ll[0][tid >> 5] = sll; red_ll[1][tid >> 5] = sld; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, d = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) { a += red_ll[0][w]; d += red_ll[1][w]; }
+      const double ll = a + (double)T * d - (double)F * T * M * 1.1447298858494002;  // log(pi)
+      *p.ll = ll;
+      if (!isfinite(ll)) flag(p.status, ST_NONFINITE);
+    }
   }
 }
 

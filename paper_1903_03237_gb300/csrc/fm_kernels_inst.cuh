@@ -15,11 +15,13 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
     case KK_G: k_tile<MX, MODE_G><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
     case KK_Y: k_tile<MX, MODE_Y><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
     case KK_XT:
-      k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr);
+      k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr, a.ll_bins);
       break;
     case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p); break;
     case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;
-    case KK_IP: k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0); break;
+    case KK_IP:
+      k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -61,21 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_pr(Prob p, float* __restrict__ PR,
         if (m < M) y[m] = fmaf(l, g[m], y[m]);
     }
   }
-  float A[MAXM], B[MAXM];
-#pragma unroll
-  for (int m = 0; m < MAXM; ++m) {
-    B[m] = (m < M) ? __fdividef(1.f, y[m]) : 0.f;
-    A[m] = x[m] * B[m] * B[m];
-  }
-  for (int n = 0; n < N; ++n) {
-    const float* g = p.G + ((size_t)n * F + f) * M;
-    float P = 0.f, R = 0.f;
-#pragma unroll
-    for (int m = 0; m < MAXM; ++m)
-      if (m < M) { P = fmaf(g[m], A[m], P); R = fmaf(g[m], B[m], R); }
-    PR[(size_t)n * npts + pt] = P;
-    PR[(size_t)(N + n) * npts + pt] = R;
-  }
+  pr_point<MAXM>(x, y, M, N, p.G + (size_t)f * M, (size_t)F * M, PR, npts, pt);
 }
 
 // fac[n][k][o] *= sqrt(num/den) with num = sum_s C[s][n][o][k], den = sum_s C[s][N+n][o][k].
