@@ -820,8 +820,11 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
 // With PR (and pf), the x~ part also forms P_n, R_n of its frames from the new x~, y~ and
 // the normalised g~ (the factors of the next W update).  With ll_tail == 0 the bins'
 // log-likelihood terms are left in llpart / logdet for a later kernel to add up.
+// Threads of an IP CTA in every channel bucket: warps m < M run the Gauss-Jordan sweeps,
+// one warp the row sweep; all of them the prefetch and the per-frame x~ / P / R / LL part.
+constexpr int kIpThreads = 256;
 template <int MAXM>
-__global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf,
+__global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf,
                                                   float* __restrict__ PR, int ll_tail) {
   constexpr int MM = MAXM * MAXM;
   __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
@@ -1061,7 +1064,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     part += ls;
     if (PR != nullptr && pf) pr_point<MAXM>(xa, ya, M, N, pf_g, (size_t)M, PR, (size_t)F * T, pt);
   }
-  __shared__ double red_s[MAXM];
+  __shared__ double red_s[kIpThreads / 32];
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
   if (lane == 0) red_s[warp] = (double)part;
   __syncthreads();
@@ -1080,7 +1083,7 @@ __global__ void __launch_bounds__(32 * MAXM) k_ip(Prob p, int S, int flags, int 
     sll += __shfl_xor_sync(0xffffffffu, sll, off);
     sld += __shfl_xor_sync(0xffffffffu, sld, off);
   }
-  __shared__ double red2_s[2][MAXM];
+  __shared__ double red2_s[2][kIpThreads / 32];
   if (lane == 0) { red2_s[0][warp] = sll; red2_s[1][warp] = sld; }
   __syncthreads();
   if (tid == 0) {
