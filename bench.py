@@ -61,21 +61,32 @@ def kernel_flops(kind: str, F, T, M, N, K) -> float:
     return float(per_point.get(kind, 0)) * ft
 
 
+# Mixtures of at most this many frames form x~, the log-likelihood terms and the P, R of the
+# next W update inside the IP kernel (the library's choice; longer ones use separate kernels).
+FUSE_XT_FRAMES = 1024
+
+
 def kernel_bytes(kind: str, F, T, M, N, K) -> float:
     """Algorithmic DRAM bytes of one launch of a mixed-form kernel class (operands read
     once, results written once; float32 / complex64 storage)."""
     ft = F * T
+    fused = T <= FUSE_XT_FRAMES
+    mu = 8 * N * K * (F + T)                                      # W and H read and written
+    ip = 4 * F * M ** 4 + 64 * F * M * M                          # one V_fm set read; Q, Q^-1 read and written
+    if fused:
+        ip += 20 * ft * M + 8 * N * ft                            # X, y~ read, x~, y~ written; P, R written
     return float({
         "gemm_lambda": 4 * N * ft + 4 * N * K * (F + T),         # lambda written, W and H read
         "gemm_w": 8 * N * ft + 4 * N * K * T,                     # P, R and H read
         "gemm_h": 8 * N * ft + 4 * N * K * F,                     # P, R and W read
-        "pr": 4 * ft * M + 2 * ft * M + 2 * N * ft + 8 * N * ft,  # x~, mean of (y~, lambda), P and R written
+        # x~ and lambda read (H update; with the fused path the only pass), or the mean of the
+        # W-update pass (x~, y~ read) and the H-update pass; P and R written
+        "pr": (4 * ft * M + 4 * N * ft if fused else 4 * ft * M + 2 * ft * M + 2 * N * ft) + 8 * N * ft,
         "g_update": 4 * N * ft + 4 * ft * M,                      # lambda and x~ read
         "scm": 4 * N * ft + 8 * ft * M + 4 * ft * M,              # lambda, X read, y~ written
-        "xt_loglik": 20 * ft * M,                                 # X, y~ read; x~, y~ written
+        "xt_loglik": (0 if fused else 20 * ft * M) + mu,          # X, y~ read; x~, y~ written; mu
         "wiener": 8 * ft * M + 4 * N * ft + 8 * N * ft * M,       # X, lambda read; images written
-        # one V_fm set read; Q, Q^-1 read and written; X, y~ read, x~, y~ written (fused x~ / LL)
-        "ip": 4 * F * M ** 4 + 64 * F * M * M + 20 * ft * M,
+        "ip": ip,
         "apply": 8 * N * K * (F + T),                               # num/den (one split) read, W or H updated
     }.get(kind, 0))
 
