@@ -200,7 +200,7 @@ fmnmf_status fmnmf_batch_destroy(fmnmf_batch* batch);
  * split counts of the tiled sweeps (plain form) or of the tensor-core V_fm and g~ kernels
  * and the split-K GEMMs of the W and H sums (mixed form).  The tuner times whole iterations
  * (n_iter per trial, from a saved copy of the state, which is restored afterwards) for
- * those split counts scaled by 1, 1/2, 1/4 and 1/8 and keeps the fastest:
+ * those split counts scaled by 1, 3/4, 1/2, 3/8, 1/4, 3/16 and 1/8 and keeps the fastest:
  *  - fmnmf_autotune: coordinate descent over the context's four tunable launches;
  *  - fmnmf_batch_autotune: one scale for every tunable launch of every member, timed on the
  *    whole batch (members running together do better with smaller grids).

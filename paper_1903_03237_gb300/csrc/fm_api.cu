@@ -1128,7 +1128,10 @@ static double tune_trial(fmnmf_ctx* ctx, const SavedState& sv, int n_iter, cudaE
   return ms;
 }
 
-static const float kTuneScales[] = {1.f, 0.5f, 0.25f, 0.125f};
+// Split-count scales the tuner tries.  The planner aims at two or more waves (HBM-bound
+// mixtures); the in-between scales reach one-wave shapes of short mixtures, where a CTA
+// that pipelines a few stages beats two waves of one-stage CTAs.
+static const float kTuneScales[] = {1.f, 0.75f, 0.5f, 0.375f, 0.25f, 0.1875f, 0.125f};
 
 fmnmf_status fmnmf_autotune(fmnmf_ctx* ctx, int n_iter, double* speedup) {
   if (!ctx || n_iter < 1) return set_err(ctx, FMNMF_EINVAL, "autotune: bad arguments");

@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
   __shared__ float4 Q_s[MM], Qi_s[MM];
   __shared__ float vsum_s[MAXM][MM];      // packed split sums per m
   __shared__ double ld_s;
-  __shared__ int bad_s, rw_s;
+  __shared__ int bad_s;
   const int f = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = p.M, N = p.N, K = p.K, F = p.F;
@@ -870,14 +870,6 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
   if (tid == 0) {
     ld_s = p.logdet[f];
     bad_s = 0;
-    // The single-warp phases (row sweep, phi) run on warp rw.  CTAs resident on one SM
-    // hold consecutive warp slots, and a slot's scheduler is its index mod 4: picking the
-    // warp from the CTA's slot index spreads those phases of co-resident CTAs over the
-    // four schedulers instead of stacking them all on the first one.
-    unsigned slot;
-    asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
-    const int nw = (int)(blockDim.x >> 5);
-    rw_s = (int)((slot / nw) % nw);
   }
   if (flags & FLAG_DO_V) {
     // packed split sums (float32, fixed order over the splits)
@@ -922,8 +914,7 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
       if (!ok && lane == 0) bad_s = 1;
     }
     __syncthreads();
-    const int rw = rw_s;
-    if (warp == rw) {
+    if (warp == 0) {
       int bad = 0;
       const df ld_add = ip_rows<MAXM>(A_s, Q_s, Qi_s, M, df_make((float)p.T), lane, bad);
       if (lane == 0) {
@@ -939,9 +930,7 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
   __shared__ float phi_s;
   __shared__ float nu_s[64];
   __shared__ float2 qf_s[MM];  // the normalised Q_f in float32 (x~ of this bin's frames)
-  const int rw = rw_s;
-  const int rtid = (tid + (int)blockDim.x - 32 * rw) % (int)blockDim.x;  // warp rw first
-  if (warp == rw) {
+  if (warp == 0) {
     df ph = df_make(1.f), sq = df_make(1.f), isq = df_make(1.f);
     if (flags & FLAG_NORMALISE) {
       df tr = df{0.f, 0.f};
@@ -976,9 +965,9 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
     const float fphi = phi_s;
     for (int n0 = 0; n0 < N; n0 += 64) {
       const int nn = min(64, N - n0);
-      if (rtid < nn) {
-        float* gp = p.G + ((size_t)(n0 + rtid) * F + f) * M;
-        const float* gsrc = pf ? pf_g + (n0 + rtid) * M : gp;
+      if (tid < nn) {
+        float* gp = p.G + ((size_t)(n0 + tid) * F + f) * M;
+        const float* gsrc = pf ? pf_g + (n0 + tid) * M : gp;
         float gv[MAXM];
         float nu = 0.f;
 #pragma unroll
@@ -988,9 +977,9 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
         for (int m = 0; m < MAXM; ++m)
           if (m < M) {
             gp[m] = gv[m] / nu;
-            if (pf) pf_g[(n0 + rtid) * M + m] = gv[m] / nu;  // the normalised g~ for P, R
+            if (pf) pf_g[(n0 + tid) * M + m] = gv[m] / nu;  // the normalised g~ for P, R
           }
-        nu_s[rtid] = nu;
+        nu_s[tid] = nu;
         if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
       }
       __syncthreads();
