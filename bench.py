@@ -62,7 +62,7 @@ def kernel_flops(kind: str, F, T, M, N, K) -> float:
 
 
 # Mixtures of at most this many frames form x~, the log-likelihood terms and the P, R of the
-# next W update inside the IP kernel (the library's choice; longer ones use separate kernels).
+# next W update inside the IP kernel (the library's choice); longer ones in the x~ kernel.
 FUSE_XT_FRAMES = 1024
 
 
@@ -72,21 +72,18 @@ def kernel_bytes(kind: str, F, T, M, N, K) -> float:
     ft = F * T
     fused = T <= FUSE_XT_FRAMES
     mu = 8 * N * K * (F + T)                                      # W and H read and written
+    xt = 20 * ft * M + 8 * N * ft                                 # X, y~ read, x~, y~ written; P, R of the next W update
     ip = 4 * F * M ** 4 + 64 * F * M * M                          # one V_fm set read; Q, Q^-1 read and written
-    if fused:
-        ip += 20 * ft * M + 8 * N * ft                            # X, y~ read, x~, y~ written; P, R written
     return float({
         "gemm_lambda": 4 * N * ft + 4 * N * K * (F + T),         # lambda written, W and H read
         "gemm_w": 8 * N * ft + 4 * N * K * T,                     # P, R and H read
         "gemm_h": 8 * N * ft + 4 * N * K * F,                     # P, R and W read
-        # x~ and lambda read (H update; with the fused path the only pass), or the mean of the
-        # W-update pass (x~, y~ read) and the H-update pass; P and R written
-        "pr": (4 * ft * M + 4 * N * ft if fused else 4 * ft * M + 2 * ft * M + 2 * N * ft) + 8 * N * ft,
+        "pr": 4 * ft * M + 4 * N * ft + 8 * N * ft,               # H update: x~, lambda read; P, R written
         "g_update": 4 * N * ft + 4 * ft * M,                      # lambda and x~ read
         "scm": 4 * N * ft + 8 * ft * M + 4 * ft * M,              # lambda, X read, y~ written
-        "xt_loglik": (0 if fused else 20 * ft * M) + mu,          # X, y~ read; x~, y~ written; mu
+        "xt_loglik": (0 if fused else xt) + mu,                   # x~ part (long mixtures) and mu
         "wiener": 8 * ft * M + 4 * N * ft + 8 * N * ft * M,       # X, lambda read; images written
-        "ip": ip,
+        "ip": ip + (xt if fused else 0),                         # x~ part inside the IP kernel (short mixtures)
         "apply": 8 * N * K * (F + T),                               # num/den (one split) read, W or H updated
     }.get(kind, 0))
 

@@ -62,7 +62,7 @@ struct fmnmf_ctx {
   size_t smW = 0, smH = 0, smG = 0, smY = 0, smS = 0;
   int n_pt_blocks = 0, n_mu_blocks = 0;
   size_t ipSmem = 0;  // the IP kernel's prefetch buffers (0: none)
-  bool fusedPR = false;  // the IP kernel forms P, R of the next W update (no separate launch)
+  bool fusedPR = false;  // the kernel that forms x~ also forms P, R of the next W update
   unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
   // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
   float* W0 = nullptr;
@@ -334,10 +334,12 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     ctx->ipSmem = (T <= kFuseXtFrames && pfb <= (size_t)kIpPrefetchMax) ? pfb : 0;
   }
   {
-    // mixed form, x~ formed in the IP kernel with its prefetch, and a W update to feed
+    // mixed form with a W update to feed: the kernel that forms x~ at the end of an
+    // iteration (the IP kernel with its prefetch for short mixtures, else k_xt_ll) forms P, R
     const unsigned mask = ctx->opts.update_mask;
     const bool ip_runs = ctx->opts.normalise || (mask & FMNMF_UPDATE_Q);
-    ctx->fusedPR = ctx->mixed && ip_runs && (mask & FMNMF_UPDATE_W) && T <= kFuseXtFrames && ctx->ipSmem > 0;
+    const bool ip_forms_xt = ip_runs && T <= kFuseXtFrames;
+    ctx->fusedPR = ctx->mixed && (mask & FMNMF_UPDATE_W) && (!ip_forms_xt || ctx->ipSmem > 0);
   }
   for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
@@ -535,6 +537,7 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
     x.n_pt_blocks = c->n_pt_blocks;
     x.apply_phi = 1;
     x.do_mu = norm ? 1 : 0;
+    x.pr = c->fusedPR ? c->PR : nullptr;
     x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
     return rec.run(KK_XT, x);
   }
@@ -561,6 +564,7 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
   x.n_pt_blocks = c->n_pt_blocks;
   x.apply_phi = 0;
   x.do_mu = 0;
+  x.pr = c->fusedPR ? c->PR : nullptr;
   x.grid = dim3(c->n_pt_blocks);
   return rec.run(KK_XT, x);
 }

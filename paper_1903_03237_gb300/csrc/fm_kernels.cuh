@@ -1092,7 +1092,7 @@ constexpr int kPtsPerThread = 4;
 
 template <int MAXM>
 __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int apply_phi, int do_mu,
-                                                    unsigned ctr, int ll_bins) {
+                                                    unsigned ctr, int ll_bins, float* __restrict__ PR) {
   const int tid = threadIdx.x;
   const int M = p.M, T = p.T, F = p.F;
   if ((int)blockIdx.x < n_pt_blocks) {
@@ -1183,6 +1183,8 @@ __global__ void __launch_bounds__(kThreads) k_xt_ll(Prob p, int n_pt_blocks, int
           }
       }
       part += ls;
+      // P, R of the next W update from this point's new x~, y~ and the bin's g~
+      if (PR != nullptr) pr_point<MAXM>(xv, yv, M, p.N, p.G + (size_t)f * M, (size_t)F * M, PR, npts, pt);
     }
     // block reduction in a fixed order (float64 from the warp sums on)
     __shared__ double red[kThreads / 32];

@@ -15,7 +15,7 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
     case KK_G: k_tile<MX, MODE_G><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
     case KK_Y: k_tile<MX, MODE_Y><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.flags, a.ctr); break;
     case KK_XT:
-      k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr, a.ll_bins);
+      k_xt_ll<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.n_pt_blocks, a.apply_phi, a.do_mu, a.ctr, a.ll_bins, a.pr);
       break;
     case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p); break;
     case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;

@@ -38,7 +38,7 @@ struct LaunchArgs {
   int apply_phi = 0;      // k_xt_ll
   int do_mu = 0;          // k_xt_ll
   int ll_bins = 0;        // k_xt_ll: a last block adds up the IP kernel's per-bin log-likelihood terms
-  float* pr = nullptr;    // k_ip: also form P, R of the next W update here
+  float* pr = nullptr;    // k_ip, k_xt_ll: also form P, R of the next W update here
   int ll_tail = 1;        // k_ip: the last CTA adds up the log-likelihood (0: a later kernel does)
   float2* out = nullptr;  // k_separate
 };
