@@ -3,12 +3,15 @@
 // cores in FP32, the IP in float-float.
 //
 //   lambda_n = W_n^T H_n                     (Eq. 9)      k_gemm_tc  [F x T] per source
-//   P, R per TF bin from x~ and y~           (Eqs. 23-24) k_pr
+//   P, R per TF bin from x~ and y~           (Eqs. 23-24) k_pr for the H update; for the W
+//                                                         update the kernel that forms x~
+//                                                         (k_ip or k_xt_ll) writes them
 //   num/den W_n = [P_n; R_n] H_n^T           (Eq. 23)     k_gemm_tc  sum over t, split-K
 //   num/den H_n = [P_n; R_n]^T W_n^T         (Eq. 24)     k_gemm_tc  sum over f, split-K
 //   W, H <- W, H * sqrt(num/den)                          k_apply (sums the splits in order)
-// The g~ update (Eq. 21) and V_fm (Eq. 18) read the materialised lambda in the tiled
-// sweeps; the IP, x~, log-likelihood and normalisation are those of the plain form.
+// The g~ update (Eq. 21, k_g_tc) and V_fm (Eq. 18, k_scm_tc) run on the tensor cores from
+// the materialised lambda; the IP, x~, log-likelihood and normalisation kernels are those
+// of the plain form.
 #include <cuda_runtime.h>
 
 #include <cudaTypedefs.h>
