@@ -335,11 +335,8 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   }
   {
     // mixed form with a W update to feed: the kernel that forms x~ at the end of an
-    // iteration (the IP kernel with its prefetch for short mixtures, else k_xt_ll) forms P, R
-    const unsigned mask = ctx->opts.update_mask;
-    const bool ip_runs = ctx->opts.normalise || (mask & FMNMF_UPDATE_Q);
-    const bool ip_forms_xt = ip_runs && T <= kFuseXtFrames;
-    ctx->fusedPR = ctx->mixed && (mask & FMNMF_UPDATE_W) && (!ip_forms_xt || ctx->ipSmem > 0);
+    // iteration (the IP kernel for short mixtures, else k_xt_ll) forms P, R
+    ctx->fusedPR = ctx->mixed && (ctx->opts.update_mask & FMNMF_UPDATE_W);
   }
   for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,

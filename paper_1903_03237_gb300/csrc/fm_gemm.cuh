@@ -45,51 +45,84 @@ __host__ __device__ inline int gemm_stage_bytes(int nt, bool tf32) {
 // the rows are not contiguous in k).  A thread issues the loads of up to 8 rows before
 // converting and storing any of them, so that many loads are in flight.
 template <bool TF32, int ROWS>
+struct StageShape {
+  static constexpr int EPG = TF32 ? 4 : 8;              // values per 16-byte core row
+  static constexpr int KG = kGemmKc / EPG;
+  static constexpr int ITEMS = ROWS * KG / kGemmThreads;  // 16-byte rows per thread
+  static constexpr int BATCH = ITEMS < 8 ? ITEMS : 8;     // loads issued together (in flight at once)
+  static_assert(ITEMS * kGemmThreads == ROWS * KG, "whole rows per thread");
+};
+
+// Loads the values of a thread's 16-byte rows i0 .. i0 + BATCH - 1 of the tile (see
+// gemm_stage_tile) into v; nothing is converted or stored yet.
+template <bool TF32, int ROWS>
+__device__ __forceinline__ void gemm_tile_load(const float* __restrict__ src, long long sr, long long sk, int r0,
+                                               int rlim, int k0, int kn, bool vec, int i0,
+                                               float (&v)[StageShape<TF32, ROWS>::BATCH][StageShape<TF32, ROWS>::EPG]) {
+  using Sh = StageShape<TF32, ROWS>;
+  constexpr int EPG = Sh::EPG;
+#pragma unroll
+  for (int u = 0; u < Sh::BATCH; ++u) {
+    const int e = (i0 + u) * kGemmThreads + threadIdx.x;
+    const int r = e % ROWS, kk = (e / ROWS) * EPG;
+    const bool rok = r0 + r < rlim;
+    const float* p = src + (long long)(r0 + r) * sr + (long long)(k0 + kk) * sk;
+    if (rok && vec && kk + EPG <= kn) {
+#pragma unroll
+      for (int q = 0; q < EPG / 4; ++q) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p) + q);
+        v[u][4 * q] = x.x; v[u][4 * q + 1] = x.y; v[u][4 * q + 2] = x.z; v[u][4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPG; ++j) v[u][j] = (rok && kk + j < kn) ? __ldg(p + (long long)j * sk) : 0.f;
+    }
+  }
+}
+
+// Rounds the loaded rows to BF16 / TF32 and stores them as core rows.
+template <bool TF32, int ROWS>
+__device__ __forceinline__ void gemm_tile_store(int i0, const float (&v)[StageShape<TF32, ROWS>::BATCH][StageShape<TF32, ROWS>::EPG],
+                                                unsigned char* dst) {
+  using Sh = StageShape<TF32, ROWS>;
+  constexpr int EPG = Sh::EPG;
+#pragma unroll
+  for (int u = 0; u < Sh::BATCH; ++u) {
+    const int e = (i0 + u) * kGemmThreads + threadIdx.x;
+    const int r = e % ROWS, kg = e / ROWS;
+    uint4 o;
+    if (TF32) {
+      o = make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
+                     __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
+    } else {
+      const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]);
+      const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4 % EPG], v[u][5 % EPG]);
+      const __nv_bfloat162 h3 = __floats2bfloat162_rn(v[u][6 % EPG], v[u][7 % EPG]);
+      o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
+                     *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+    }
+    *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = o;
+  }
+}
+
+// Stages a rows x kGemmKc tile of src(r0 + r, k0 + k) (zero outside [rlim) x [kn)) as BF16 or
+// TF32 into the K-major core-matrix layout with the 16-byte k-groups outermost: core row
+// (r, kg) at byte (kg * rows + r) * 16.  A thread builds whole 16-byte rows (8 BF16 or 4
+// TF32 values); consecutive threads take consecutive r, so the stores fill all banks.  The
+// loads are float4 when the tile rows are contiguous in k and 16-byte aligned (vec), else
+// scalar (consecutive threads then read consecutive r, which is the stride-1 index when
+// the rows are not contiguous in k).  A thread issues the loads of up to 8 rows before
+// converting and storing any of them, so that many loads are in flight.
+template <bool TF32, int ROWS>
 __device__ __forceinline__ void gemm_stage_tile(const float* __restrict__ src, long long sr, long long sk, int r0,
                                                 int rlim, int k0, int kn, bool vec, unsigned char* dst) {
-  constexpr int EPG = TF32 ? 4 : 8;
-  constexpr int KG = kGemmKc / EPG;
-  constexpr int ITEMS = ROWS * KG / kGemmThreads;  // 16-byte rows per thread
-  constexpr int BATCH = ITEMS < 8 ? ITEMS : 8;     // loads issued together (in flight at once)
-  static_assert(ITEMS * kGemmThreads == ROWS * KG, "whole rows per thread");
+  using Sh = StageShape<TF32, ROWS>;
 #pragma unroll 1
-  for (int i0 = 0; i0 < ITEMS; i0 += BATCH) {
-    float v[BATCH][EPG];
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int e = (i0 + u) * kGemmThreads + threadIdx.x;
-      const int r = e % ROWS, kk = (e / ROWS) * EPG;
-      const bool rok = r0 + r < rlim;
-      const float* p = src + (long long)(r0 + r) * sr + (long long)(k0 + kk) * sk;
-      if (rok && vec && kk + EPG <= kn) {
-#pragma unroll
-        for (int q = 0; q < EPG / 4; ++q) {
-          const float4 x = __ldg(reinterpret_cast<const float4*>(p) + q);
-          v[u][4 * q] = x.x; v[u][4 * q + 1] = x.y; v[u][4 * q + 2] = x.z; v[u][4 * q + 3] = x.w;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < EPG; ++j) v[u][j] = (rok && kk + j < kn) ? __ldg(p + (long long)j * sk) : 0.f;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int e = (i0 + u) * kGemmThreads + threadIdx.x;
-      const int r = e % ROWS, kg = e / ROWS;
-      uint4 o;
-      if (TF32) {
-        o = make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
-                       __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
-      } else {
-        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]);
-        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4 % EPG], v[u][5 % EPG]);
-        const __nv_bfloat162 h3 = __floats2bfloat162_rn(v[u][6 % EPG], v[u][7 % EPG]);
-        o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
-                       *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
-      }
-      *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = o;
-    }
+  for (int i0 = 0; i0 < Sh::ITEMS; i0 += Sh::BATCH) {
+    float v[Sh::BATCH][Sh::EPG];
+    gemm_tile_load<TF32, ROWS>(src, sr, sk, r0, rlim, k0, kn, vec, i0, v);
+    gemm_tile_store<TF32, ROWS>(i0, v, dst);
   }
 }
 
@@ -131,8 +164,20 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       if (!mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
     }
     const int kn = min(kGemmKc, kend - k0);
-    gemm_stage_tile<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, st);
-    gemm_stage_tile<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
+    using SA = StageShape<TF32, 128>;
+    using SB = StageShape<TF32, NT>;
+    if constexpr (SA::ITEMS == SA::BATCH && SB::ITEMS == SB::BATCH && SA::ITEMS + SB::ITEMS <= 10) {
+      // both tiles in one small batch each (BF16, NT <= 32): the loads of A and B in flight
+      // together (wider tiles would need more registers than the occupancy allows)
+      float va[SA::BATCH][SA::EPG], vb[SB::BATCH][SB::EPG];
+      gemm_tile_load<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, 0, va);
+      gemm_tile_load<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, 0, vb);
+      gemm_tile_store<TF32, 128>(0, va, st);
+      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES);
+    } else {
+      gemm_stage_tile<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, st);
+      gemm_stage_tile<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();

@@ -6,7 +6,7 @@
 //   k_tile<MODE_H>   H update, Eq. 24:   num/den[n,k,t] = sum_f w_nkf sum_m g~_nfm {x~/y~^2, 1/y~}
 //   k_tile<MODE_G>   g~ update, Eq. 21:  num/den[n,f,m] = sum_t lambda_ftn {x~/y~^2, 1/y~}
 //   k_tile<MODE_Y>   y~ refresh; split sums of V_fm = (1/T) sum_t x x^H / y~_ftm (Eq. 18)
-//   k_ip             IP, Eqs. 19-20, float64, one warp per bin (+ phi and nu normalisation)
+//   k_ip             IP, Eqs. 19-20, float-float, one CTA per bin (+ phi and nu normalisation)
 //   k_xt_ll          x~ = |Q_f x_ft|^2 (below Eq. 17); log-likelihood, Eq. 17; mu normalisation
 // A k_tile CTA owns kOT consecutive "own" elements and one split of the summed "inner"
 // index; each split writes partial sums and the last CTA to arrive for an own tile sums
@@ -691,13 +691,14 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 }
 
 // ---------------------------------------------------------------------------------
-// IP update (Eqs. 18-20) and the per-bin normalisation.  One CTA per bin, one warp per
-// channel, float-float arithmetic (about 48 significand bits) on the FP32 pipes.
+// IP update (Eqs. 18-20) and the per-bin normalisation.  One CTA per bin, float-float
+// arithmetic (about 48 significand bits) on the FP32 pipes.
 //
 // Eq. 19 solves (Q_f V_fm) q = e_m with the current Q_f.  Since (Q_f V_fm)^-1 =
 // V_fm^-1 Q_f^-1, q = V_fm^-1 c_m with c_m = Q_f^-1 e_m.  V_fm depends only on y~, so the
 // M inverses are formed first, in parallel (warp m sweeps V_fm: Hermitian positive
-// definite, no pivoting).  Warp 0 then runs the rows in order m = 0..M-1:
+// definite, no pivoting).  Warp 0 then runs the rows in order m = 0..M-1 (ip_rows, with
+// Q_f^-1 in registers):
 //   q = V_fm^-1 c_m,   s = c_m^H q  (= q^H V_fm q, Eq. 20),   q_new = q / sqrt(s),
 //   row m of Q_f <- q_new^H,
 //   Q_f^-1 <- Q_f^-1 - c_m (q_new^H Q_f^-1 - e_m^T) / sqrt(s)   (Sherman-Morrison),
@@ -706,8 +707,8 @@ __global__ void __launch_bounds__(kThreads) k_tile(Prob p, Geom g, int flags, un
 // Then phi_f = tr(Q_f Q_f^H)/M: Q_f /= sqrt(phi), Q_f^-1 *= sqrt(phi), g~_nf /= phi,
 // log|det|^2 -= M log phi; nu_nf = sum_m g~_nfm: g~_nf /= nu, w_nkf *= nu.
 // With xt_mode the same CTA then computes x~ = |Q_f x_ft|^2 for its bin's frames with the
-// new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the last CTA to finish adds
-// the bins up in bin order (Eq. 17).
+// new Q_f (y~ /= phi_f) and the bin's log-likelihood terms; the bins are added up in bin
+// order (Eq. 17) by the last CTA to finish or by a later kernel (ll_tail).
 // ---------------------------------------------------------------------------------
 // P_n = sum_m g~_nfm x~_m / y~_m^2 and R_n = sum_m g~_nfm / y~_m at one TF point (the
 // per-point factors of the W and H updates, Eqs. 23-24), into PR[n][pt] and PR[N + n][pt]
@@ -731,6 +732,66 @@ __device__ __forceinline__ void pr_point(const float (&x)[MAXM], const float (&y
     PR[(size_t)n * ns + pt] = P;
     PR[(size_t)(N + n) * ns + pt] = R;
   }
+}
+
+// In-place Gauss-Jordan inverse of one Hermitian positive definite V_fm on one warp, in
+// float-float, with the matrix in registers: lane l holds entries (i, j), j = l % MAXM,
+// i = l / MAXM + r * IG (the layout of ip_rows).  v holds the packed split sums (real parts
+// on and above the diagonal, imaginary parts below); the inverse goes to A (row-major,
+// leading dimension MAXM).  Per pivot k the pivot row and column come by shuffles:
+//   A[k][k] <- 1/p,  A[k][j] <- A[k][j]/p,  A[i][k] <- -A[i][k]/p,
+//   A[i][j] <- A[i][j] - A[i][k] (A[k][j]/p)          (p = A[k][k], no pivoting).
+// Returns false (on every lane) when a pivot is not positive and finite.
+template <int MAXM>
+__device__ __forceinline__ bool gj_inverse(const float* v, float4* A, int M, int lane) {
+  constexpr int MM = MAXM * MAXM;
+  constexpr int R = MM > 32 ? MM / 32 : 1;
+  constexpr int IG = 32 / MAXM;
+  const int j = lane % MAXM, i0 = lane / MAXM;
+  bool own[R];
+  cdf a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + r * IG;
+    own[r] = lane < MM && i < M && j < M;
+    float re = 0.f, im = 0.f;
+    if (own[r]) {
+      if (i == j) re = v[i * MAXM + i];
+      else if (i < j) { re = v[i * MAXM + j]; im = v[j * MAXM + i]; }
+      else { re = v[j * MAXM + i]; im = -v[i * MAXM + j]; }
+    }
+    a[r] = cdf_make(re, im);
+  }
+  bool ok = true;
+  for (int k = 0; k < M; ++k) {
+    // A[i][k] of this lane's rows (lane i0 MAXM + k, slot r); A[k][j] and A[k][k] (lanes
+    // (k % IG) MAXM + j and (k % IG) MAXM + k, slot k / IG)
+    cdf col[R], row = cdf_zero(), piv = cdf_zero();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      col[r] = shfl_cdf(a[r], i0 * MAXM + k);
+      const cdf rw = shfl_cdf(a[r], (k % IG) * MAXM + j);
+      const cdf pv = shfl_cdf(a[r], (k % IG) * MAXM + k);
+      if (k / IG == r) { row = rw; piv = pv; }
+    }
+    ok = ok && (piv.re.hi > 0.f) && isfinite(piv.re.hi);
+    const df inv = df_rcp(piv.re);
+    const cdf rs = cdf_scale(row, inv);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!own[r]) continue;
+      const int i = i0 + r * IG;
+      if (i == k && j == k) a[r] = cdf{inv, df{0.f, 0.f}};
+      else if (i == k) a[r] = rs;
+      else if (j == k) a[r] = cdf_scale(col[r], df_neg(inv));
+      else a[r] = cdf_sub(a[r], cdf_mul(col[r], rs));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (own[r]) A[(i0 + r * IG) * MAXM + j] = cdf_pack(a[r]);
+  __syncwarp();
+  return ok;
 }
 
 // The row sweep of the IP update for one bin (Eqs. 19-20), on one warp, with Q_f^-1 held
@@ -817,19 +878,17 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
 // With pf (dynamic shared memory for it given), the CTA prefetches at its start what the
 // later phases read but the IP does not change: the bin's X and y~ rows (x~ part) and its
 // g~ and W entries (normalisation), with cp.async, so those loads overlap the IP chain.
-// With PR (and pf), the x~ part also forms P_n, R_n of its frames from the new x~, y~ and
+// With PR, the x~ part also forms P_n, R_n of its frames from the new x~, y~ and
 // the normalised g~ (the factors of the next W update).  With ll_tail == 0 the bins'
 // log-likelihood terms are left in llpart / logdet for a later kernel to add up.
-// Threads of an IP CTA in every channel bucket: warps m < M run the Gauss-Jordan sweeps,
-// one warp the row sweep; all of them the prefetch and the per-frame x~ / P / R / LL part.
-constexpr int kIpThreads = 256;
+// One warp per channel of the bucket (warps m < M run the Gauss-Jordan sweeps, warp 0 the
+// row sweep; all of them the prefetch and the per-frame x~ / P / R / LL part), at most 64
+// registers a thread: 2048 threads per SM, which keeps room for other contexts' kernels.
 template <int MAXM>
-__global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf,
+__global__ void __launch_bounds__(32 * MAXM, 32 / MAXM) k_ip(Prob p, int S, int flags, int xt_mode, unsigned ctr, int pf,
                                                   float* __restrict__ PR, int ll_tail) {
   constexpr int MM = MAXM * MAXM;
   __shared__ float4 A_s[MAXM][MM];       // per warp m: sum_t x x^H / y~_m, then its inverse
-  __shared__ float4 col_s[MAXM][MAXM];   // per warp: column k before the sweep step
-  __shared__ float4 row_s[MAXM][MAXM];   // per warp: row k after scaling
   __shared__ float4 Q_s[MM], Qi_s[MM];
   __shared__ float vsum_s[MAXM][MM];      // packed split sums per m
   __shared__ double ld_s;
@@ -878,39 +937,7 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
       vsum_s[e / MM][e % MM] = sum_splits(p.part + (size_t)f * M * MM + e, psz, S);
     __syncthreads();
     if (warp < M) {
-      const int m = warp;
-      float4* A = A_s[m];
-      const float* v = vsum_s[m];
-      for (int e = lane; e < M * M; e += 32) {
-        const int j = e / M, c = e % M;
-        float re, im;
-        if (j == c) { re = v[j * MAXM + j]; im = 0.f; }
-        else if (j < c) { re = v[j * MAXM + c]; im = v[c * MAXM + j]; }
-        else { re = v[c * MAXM + j]; im = -v[j * MAXM + c]; }
-        A[j * MAXM + c] = make_float4(re, 0.f, im, 0.f);
-      }
-      __syncwarp();
-      // in-place Gauss-Jordan sweep of the Hermitian positive definite matrix
-      bool ok = true;
-      for (int k = 0; k < M; ++k) {
-        if (lane < M) col_s[m][lane] = A[lane * MAXM + k];
-        __syncwarp();
-        const df piv = cdf_unpack(col_s[m][k]).re;
-        ok = ok && (piv.hi > 0.f) && isfinite(piv.hi);
-        const df inv = df_rcp(piv);
-        if (lane < M) row_s[m][lane] = cdf_pack(cdf_scale(cdf_unpack(A[k * MAXM + lane]), inv));
-        __syncwarp();
-        for (int e = lane; e < M * M; e += 32) {
-          const int i = e / M, j = e % M;
-          cdf val;
-          if (i == k && j == k) val = cdf{inv, df{0.f, 0.f}};
-          else if (i == k) val = cdf_unpack(row_s[m][j]);
-          else if (j == k) val = cdf_scale(cdf_unpack(col_s[m][i]), df_neg(inv));
-          else val = cdf_sub(cdf_unpack(A[i * MAXM + j]), cdf_mul(cdf_unpack(col_s[m][i]), cdf_unpack(row_s[m][j])));
-          A[i * MAXM + j] = cdf_pack(val);
-        }
-        __syncwarp();
-      }
+      const bool ok = gj_inverse<MAXM>(vsum_s[warp], A_s[warp], M, lane);
       if (!ok && lane == 0) bad_s = 1;
     }
     __syncthreads();
@@ -1051,9 +1078,13 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
       }
     }
     part += ls;
-    if (PR != nullptr && pf) pr_point<MAXM>(xa, ya, M, N, pf_g, (size_t)M, PR, (size_t)F * T, pt);
+    // the normalised g~ of this bin: its prefetch copy, or the values this CTA wrote (visible
+    // after the barrier above)
+    if (PR != nullptr)
+      pr_point<MAXM>(xa, ya, M, N, pf ? pf_g : p.G + (size_t)f * M, pf ? (size_t)M : (size_t)F * M, PR,
+                     (size_t)F * T, pt);
   }
-  __shared__ double red_s[kIpThreads / 32];
+  __shared__ double red_s[MAXM];
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
   if (lane == 0) red_s[warp] = (double)part;
   __syncthreads();
@@ -1072,7 +1103,7 @@ __global__ void __launch_bounds__(kIpThreads, 4) k_ip(Prob p, int S, int flags, 
     sll += __shfl_xor_sync(0xffffffffu, sll, off);
     sld += __shfl_xor_sync(0xffffffffu, sld, off);
   }
-  __shared__ double red2_s[2][kIpThreads / 32];
+  __shared__ double red2_s[2][MAXM];
   if (lane == 0) { red2_s[0][warp] = sll; red2_s[1][warp] = sld; }
   __syncthreads();
   if (tid == 0) {

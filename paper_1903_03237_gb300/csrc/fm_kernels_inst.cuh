@@ -20,7 +20,7 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
     case KK_PREP: k_prep_q<MX><<<a.grid, kThreads, 0, a.st>>>(a.p); break;
     case KK_SEP: k_separate<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.g, a.out); break;
     case KK_IP:
-      k_ip<MX><<<a.grid, kIpThreads, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
+      k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
       break;
     default: return cudaErrorInvalidValue;
   }

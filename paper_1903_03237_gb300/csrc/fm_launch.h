@@ -84,8 +84,9 @@ int gtc_frames_per_stage();
 cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
                          cudaStream_t st);
 
-// Largest dynamic shared memory of the IP kernel's prefetch (X and y~ rows, g~, W of a bin).
-constexpr int kIpPrefetchMax = 96 * 1024;
+// Largest dynamic shared memory of the IP kernel's prefetch (X and y~ rows, g~, W of a bin):
+// small enough that four or more IP CTAs stay resident per SM.
+constexpr int kIpPrefetchMax = 40 * 1024;
 
 // Sets the calling thread's message returned by fmnmf_last_error(NULL).
 void set_thread_error(const char* msg);

@@ -92,3 +92,31 @@ def test_mixed_trajectory_monotone(fm):
 def test_mixed_tuned_shapes(fm, scale):
     err = _mixed_errors(fm, 70, 600, 8, 6, 32, fm.PREC_BF16, tuning=[scale] * 8)
     assert max(err[k] for k in ("W", "H", "G", "Q", "LL", "separated")) < TOL_MIXED, err
+
+
+SECOND = [(37, 150, 3, 3, 5), (33, 200, 8, 6, 20), (20, 1100, 4, 3, 8)]
+
+
+@pytest.mark.parametrize("shape", SECOND, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in SECOND])
+def test_mixed_second_iteration(fm, shape):
+    # The W update of every iteration after the first reads P, R formed at the end of the
+    # previous one (by the IP kernel up to 1024 frames, by the x~ kernel beyond), not by a
+    # separate pass: check the second iteration alone against the oracle started from the
+    # state the first one left.
+    F, T, M, N, K = shape
+    mix = make_mixture(F, T, M, N, K, 11)
+    W, H, G, Q = make_state(F, T, M, N, K, 11)
+    ctx = fm.Context(mix.X, N, K, precision=fm.PREC_BF16)
+    ctx.set_state(W, H, G, Q)
+    ctx.iterate(1)
+    st1 = ctx.get_state()
+    ctx.iterate(1)
+    ll = ctx.loglik()
+    Wg, Hg, Gg, Qg = ctx.get_state()
+    ctx.close()
+    X64 = mix.X.astype(np.complex128)
+    Wr, Hr, Gr, Qr, tr = O.iterate(X64, *as64(*st1), n_iter=1)
+    err = {"W": rel(Wg, Wr), "H": rel(Hg, Hr), "G": rel(Gg, Gr), "Q": rel(Qg, Qr),
+           "LL": ll_rel(ll, tr[-1], X64, Wr, Hr, Gr, Qr)}
+    print("second iteration", shape, json.dumps({k: f"{v:.2e}" for k, v in err.items()}))
+    assert max(err.values()) < TOL_MIXED, err
