@@ -94,7 +94,9 @@ def test_mixed_tuned_shapes(fm, scale):
     assert max(err[k] for k in ("W", "H", "G", "Q", "LL", "separated")) < TOL_MIXED, err
 
 
-SECOND = [(37, 150, 3, 3, 5), (33, 200, 8, 6, 20), (20, 1100, 4, 3, 8)]
+# (24, 700, 8): the IP kernel's prefetch does not fit (67 KB), so it forms P, R from the g~
+# it wrote to memory; (20, 1100, 4): more than 1024 frames, P, R from the x~ kernel
+SECOND = [(37, 150, 3, 3, 5), (33, 200, 8, 6, 20), (24, 700, 8, 4, 8), (20, 1100, 4, 3, 8)]
 
 
 @pytest.mark.parametrize("shape", SECOND, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in SECOND])
