@@ -158,18 +158,38 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
 
   bool ok = true;
   int c = 0;
+  using SA = StageShape<TF32, 128>;
+  using SB = StageShape<TF32, NT>;
+  // Small tiles (BF16, NT <= 32: both operands in one batch each): the loads of A and B are
+  // in flight together; with NT = 32 a chunk's loads are also issued while the previous
+  // chunk's barrier and MMAs run (held across them, the registers would cut the occupancy
+  // of the narrower tile and of wider ones).
+  constexpr bool kCombine = SA::ITEMS == SA::BATCH && SB::ITEMS == SB::BATCH && SA::ITEMS + SB::ITEMS <= 10;
+  constexpr bool kPipe = kCombine && NT == 32;
+  float va[SA::BATCH][SA::EPG], vb[SB::BATCH][SB::EPG];
+  if constexpr (kPipe) {
+    if (kbeg < kend) {
+      const int kn0 = min(kGemmKc, kend - kbeg);
+      gemm_tile_load<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, kbeg, kn0, vecA, 0, va);
+      gemm_tile_load<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, kbeg, kn0, vecB, 0, vb);
+    }
+  }
   for (int k0 = kbeg; k0 < kend; k0 += kGemmKc, ++c) {
     unsigned char* st = gsm + (c & 1) * STAGE;
     if (c >= 2) {  // the MMAs of chunk c-2 read this stage: wait for them
       if (!mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
     }
     const int kn = min(kGemmKc, kend - k0);
-    using SA = StageShape<TF32, 128>;
-    using SB = StageShape<TF32, NT>;
-    if constexpr (SA::ITEMS == SA::BATCH && SB::ITEMS == SB::BATCH && SA::ITEMS + SB::ITEMS <= 10) {
-      // both tiles in one small batch each (BF16, NT <= 32): the loads of A and B in flight
-      // together (wider tiles would need more registers than the occupancy allows)
-      float va[SA::BATCH][SA::EPG], vb[SB::BATCH][SB::EPG];
+    if constexpr (kPipe) {
+      gemm_tile_store<TF32, 128>(0, va, st);
+      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES);
+      const int k1 = k0 + kGemmKc;
+      if (k1 < kend) {
+        const int kn1 = min(kGemmKc, kend - k1);
+        gemm_tile_load<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k1, kn1, vecA, 0, va);
+        gemm_tile_load<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k1, kn1, vecB, 0, vb);
+      }
+    } else if constexpr (kCombine) {
       gemm_tile_load<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, 0, va);
       gemm_tile_load<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, 0, vb);
       gemm_tile_store<TF32, 128>(0, va, st);
