@@ -13,7 +13,9 @@
 // the process exits.  Every call shares it and it keeps the last call's contents, so the
 // counter is cleared at the start of each call; calls that overlap on the GPU race for
 // it and must be ordered by the caller (same stream, or events).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdarg>
 #include <cstdio>
@@ -35,12 +37,21 @@ constexpr size_t kNaLogdetBytes = (size_t)kNaMaxF * sizeof(double);
 constexpr size_t kNaCounterOffset = kNaLogdetBytes;  // one unsigned, padded to 256 bytes
 constexpr size_t kNaPartOffset = kNaCounterOffset + 256;
 constexpr int kNaMaxBlocks = (int)((kScratchBytes - kNaPartOffset) / sizeof(double));
-constexpr int kNaMaxDevices = 64;
+constexpr int kNaCacheSlots = 64;
 
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
+// The array's device address differs between driver contexts (the module is loaded again
+// after cudaDeviceReset, and each context that shares a device has its own copy), so the
+// cache is keyed on the current context's unique ID (cuCtxGetId: never reused within the
+// process, unlike a context handle), not on the device number.
+struct NaSlot {
+  unsigned long long id;
+  void* ptr;
+};
 std::mutex g_na_mu;
-void* g_na_ptr[kNaMaxDevices] = {};
+NaSlot g_na_cache[kNaCacheSlots] = {};
+int g_na_next = 0;
 
 // Errors are reported through fmnmf_last_error(NULL), like every context-less failure.
 fmnmf_status na_err(fmnmf_status s, const char* fmt, ...) {
@@ -53,22 +64,55 @@ fmnmf_status na_err(fmnmf_status s, const char* fmt, ...) {
   return s;
 }
 
-// Device address of the scratch array on the current device, looked up once per device
-// (with that device current) and cached.
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points (no link-time
+// libcuda dependency).
+struct CtxFns {
+  PFN_cuCtxGetCurrent_v4000 current = nullptr;
+  PFN_cuCtxGetId_v12000 id = nullptr;
+};
+const CtxFns& ctx_fns() {
+  static CtxFns fns;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fns.current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(ptr);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fns.id = reinterpret_cast<PFN_cuCtxGetId_v12000>(ptr);
+  });
+  return fns;
+}
+
+// ID of the current context (0 when the thread has none yet).
+bool current_ctx_id(unsigned long long* id) {
+  const CtxFns& f = ctx_fns();
+  CUcontext cur = nullptr;
+  if (!f.current || !f.id || f.current(&cur) != CUDA_SUCCESS) return false;
+  *id = 0;
+  return !cur || f.id(cur, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the current context: looked up with
+// cudaGetSymbolAddress the first time a context calls (with its device current) and cached
+// per context.  A thread with no current context yet gets the device's primary context
+// from that lookup (the runtime binds it), and the context is read again afterwards.
 fmnmf_status na_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_err(FMNMF_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kNaMaxDevices) return na_err(FMNMF_EINVAL, "device %d out of range", dev);
+  unsigned long long id = 0;
+  if (!current_ctx_id(&id)) return na_err(FMNMF_ECUDA, "cuCtxGetCurrent / cuCtxGetId failed");
   std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess || !p)
-      return na_err(FMNMF_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    g_na_ptr[dev] = p;
-  }
-  *out = g_na_ptr[dev];
+  if (id)
+    for (const NaSlot& s : g_na_cache)
+      if (s.ptr && s.id == id) { *out = s.ptr; return FMNMF_OK; }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+  if (e != cudaSuccess || !p) return na_err(FMNMF_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+  if (!current_ctx_id(&id) || !id) return na_err(FMNMF_ECUDA, "no current CUDA context");
+  g_na_cache[g_na_next] = NaSlot{id, p};  // the oldest slot makes room
+  g_na_next = (g_na_next + 1) % kNaCacheSlots;
+  *out = p;
   return FMNMF_OK;
 }
 
@@ -173,7 +217,8 @@ cudaError_t na_launch(const float2* X, const float* W, const float* H, const flo
   double* part = reinterpret_cast<double*>(scratch + kNaPartOffset);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);  // clear what must start at zero
   if (e != cudaSuccess) return e;
-  k_na_logdet<MAXM><<<(F + 7) / 8, kThreads, 0, st>>>(Q, F, M, logdet);
+  constexpr int kBinsPerBlock = kThreads / 32;  // one warp per bin
+  k_na_logdet<MAXM><<<(F + kBinsPerBlock - 1) / kBinsPerBlock, kThreads, 0, st>>>(Q, F, M, logdet);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_na_loglik<MAXM><<<nblk, kThreads, 0, st>>>(X, W, H, G, Q, F, T, M, N, K, logdet, part, counter, ll);
   return cudaGetLastError();

@@ -1,0 +1,75 @@
+"""The bench's own job, checked against the float64 oracle: the chosen (BF16 mixed) form on
+the paper-scale mixture (M4 N4 K32 F513 T640, 10 % of the bins with diffuse noise) from the
+seeded initial state of fmnmf_init, 100 iterations (the paper's count, Sec. IV-A), then the
+Wiener separation.
+
+* The log-likelihood is non-decreasing (Eq. 17 under the MM / IP updates, Sec. III) up to
+  the rounding of the BF16 contractions: no step falls by more than MONO_TOL of |LL|.
+* After 100 iterations the state, the log-likelihood and the images stay within stated
+  drift bounds of the oracle's own 100-iteration trajectory from the same initial state
+  (the per-iteration error of the form compounds over the iterations; the bounds are the
+  measured drift with a margin).
+* The separated images equal the oracle's Wiener filter (Eq. 3) applied to the state the
+  GPU reached, within the one-step bar of the mixed form (1e-3).
+"""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import fastmnmf_oracle as O
+from paper_1903_03237_gb300.synth import config_mixture, CONFIGS
+
+from tests._parity import rel, elem_rel, image_scale, ll_rel
+
+pytestmark = pytest.mark.gpu
+
+MONO_TOL = 1e-6      # largest allowed fall of one iteration, relative to |LL|
+DRIFT_LL = 1e-3      # |dLL| / sum|terms| after 100 iterations
+DRIFT_STATE = 5e-2   # ||a - b|| / ||b|| of W, H, g~, Q after 100 iterations
+TOL_IMG = 1e-3       # images vs the oracle's filter of the GPU's own state
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf
+    return fastmnmf
+
+
+@pytest.mark.parametrize("form", ["bf16"])
+def test_bench_job_c1_100_iterations(fm, form):
+    c = CONFIGS["c1"]
+    F, T, M, N, K, iters = c["F"], c["T"], c["M"], c["N"], c["K"], c["iters"]
+    mix = config_mixture("c1", seed=0)
+    prec = {"bf16": fm.PREC_BF16, "fp32": fm.PREC_FP32}[form]
+    ctx = fm.Context(mix.X, N, K, seed=0, precision=prec)
+    W0, H0, G0, Q0 = ctx.get_state()
+    lls = [ctx.loglik()]
+    for _ in range(iters):
+        ctx.iterate(1)
+        lls.append(ctx.loglik())
+    Wg, Hg, Gg, Qg = ctx.get_state()
+    S = ctx.separate()
+    ctx.close()
+    X64 = mix.X.astype(np.complex128)
+    Wr, Hr, Gr, Qr, tr = O.iterate(X64, W0.astype(float), H0.astype(float), G0.astype(float),
+                                   Q0.astype(complex), n_iter=iters)
+    d = np.diff(lls)
+    scale = np.abs(lls).max()
+    drift = {"W": rel(Wg, Wr), "H": rel(Hg, Hr), "G": rel(Gg, Gr), "Q": rel(Qg, Qr),
+             "LL": ll_rel(lls[-1], tr[-1], X64, Wr, Hr, Gr, Qr),
+             "LL_traj_max": max(abs(a - b) for a, b in zip(lls[1:], tr)) / O.loglik_terms_abs(X64, Wr, Hr, Gr, Qr),
+             "worst_step": float(d.min() / scale)}
+    Sg_ref = O.separate(X64, Wg.astype(float), Hg.astype(float), Gg.astype(float), Qg.astype(complex))
+    img = {"separated": rel(S, Sg_ref), "separated_el": elem_rel(S, Sg_ref, image_scale(X64, N), 1.0)}
+    print("bench job", form, json.dumps({k: f"{v:.2e}" for k, v in (drift | img).items()}))
+    assert np.all(d >= -MONO_TOL * scale), drift
+    assert lls[-1] > lls[0]
+    assert drift["LL"] < DRIFT_LL, drift
+    assert max(drift[k] for k in ("W", "H", "G", "Q")) < DRIFT_STATE, drift
+    assert max(img.values()) < TOL_IMG, img

@@ -6,8 +6,10 @@ memory in the library's static device array instead of allocating.
 Checked through the C ABI against the context entry point (fmnmf_init / fmnmf_set_state /
 fmnmf_loglik) on the same state, within the log-likelihood tolerance of the parity tests
 (1e-5 of the sum of |terms| of Eq. 17), on two calls in a row with different states so
-that the second call runs on the scratch the first one left behind.  This file is named
-to be collected last.
+that the second call runs on the scratch the first one left behind; and directly against
+the float64 oracle's Eq. 17 at the sizes of the small and the paper-scale mixtures.  The
+size and alignment checks run on the host before any launch.  This file is named to be
+collected last.
 """
 import ctypes
 
@@ -65,9 +67,39 @@ def test_noalloc_loglik_matches_context(fm, shape):
         assert abs(got - ref) / scale < TOL, (got, ref)
 
 
+@pytest.mark.parametrize("name", ["c0", "c1"])
+def test_noalloc_loglik_matches_oracle(fm, name):
+    from paper_1903_03237_gb300.synth import config_mixture, CONFIGS
+    c = CONFIGS[name]
+    F, T, M, N, K = c["F"], c["T"], c["M"], c["N"], c["K"]
+    mix = config_mixture(name, seed=3)
+    X64 = mix.X.astype(np.complex128)
+    for s in (3, 4):                        # two calls in a row, different states
+        W, H, G, Q = make_state(F, T, M, N, K, s)
+        args = (W.astype(float), H.astype(float), G.astype(float), Q.astype(complex))
+        ref = O.loglik(X64, *args)
+        got = _noalloc_ll(fm, mix.X, W, H, G, Q)
+        err = abs(got - ref) / O.loglik_terms_abs(X64, *args)
+        print(name, "noalloc vs oracle", f"{err:.2e}")
+        assert err < TOL, (got, ref)
+
+
 def test_noalloc_rejects_oversize(fm):
     lib = fm.lib()
     one = ctypes.c_void_p(1 << 20)  # never dereferenced: the size check comes first
     st = lib.fmnmf_loglik_noalloc(one, one, one, one, one, 20000, 4, 2, 1, 1, one, None)
     assert st == fm.EINVAL
     assert b"scratch limit" in lib.fmnmf_last_error(None)
+    # within the bin limit but beyond the TF-bin limit of the per-block partial sums
+    st = lib.fmnmf_loglik_noalloc(one, one, one, one, one, 16384, 8000, 2, 1, 1, one, None)
+    assert st == fm.EINVAL
+    assert b"TF bins" in lib.fmnmf_last_error(None)
+
+
+def test_noalloc_rejects_misaligned(fm):
+    lib = fm.lib()
+    one = ctypes.c_void_p(1 << 20)
+    odd = ctypes.c_void_p((1 << 20) + 1)  # never dereferenced: the alignment check comes first
+    st = lib.fmnmf_loglik_noalloc(odd, one, one, one, one, 16, 16, 2, 1, 1, one, None)
+    assert st == fm.EINVAL
+    assert b"misaligned" in lib.fmnmf_last_error(None)
