@@ -16,7 +16,11 @@ and explicit Python loops for the iterative projection).  Each function cites th
 * log-likelihood      Eq. 17, with the dropped constant -FTM log(pi) restored
 * IP update of Q_f    V_fm, (Q_f V_fm)^-1 e_m, normalisation by q^H V q   (Eqs. 18-20)
 * MU of g~            Eq. 21;   MU of W and H   Eqs. 23-24
+* MU of lambda        Eq. 22 (unconstrained source model, Sec. III-B-1: FastFCA, Sec. III-C-1)
 * Wiener separation   x_ftn = Y_ftn Y_ft^-1 x_ft                          (Sec. II-A-1, Eq. 3)
+
+The spatial-model functions take lambda[f,t,n] itself (``*_lam``); the NMF source model forms
+it by Eq. 9 and calls them, the unconstrained model passes its own lambda.
 
 Readings of points where the paper is silent (block order, scale normalisation,
 initialisation, the log-likelihood constant) are fixed in ``iterate``,
@@ -84,13 +88,29 @@ def init_state(F: int, T: int, M: int, N: int, K: int, seed: int):
     u = splitmix64_uniform(seed, 0, nw + nh)
     W = (0.1 + u[:nw]).astype(np.float32).astype(np.float64).reshape(N, K, F)
     H = (0.1 + u[nw:]).astype(np.float32).astype(np.float64).reshape(N, K, T)
+    G, Q = _init_gq(F, M, N)
+    return W, H, G, Q
+
+
+def _init_gq(F: int, M: int, N: int):
+    """g~[n,f,m] = 1 if m == n mod M else 1e-2, divided by its sum over m (float32); Q_f = I."""
     G = np.full((N, F, M), 1e-2)
     for n in range(N):
         G[n, :, n % M] = 1.0
     G = G / G.sum(axis=2, keepdims=True)
     G = G.astype(np.float32).astype(np.float64)
     Q = np.tile(np.eye(M, dtype=np.complex128), (F, 1, 1))
-    return W, H, G, Q
+    return G, Q
+
+
+def init_state_free(F: int, T: int, M: int, N: int, seed: int):
+    """Initial state of ``fmnmf_init`` for the unconstrained source model (FastFCA):
+    lambda[f,t,n] = 0.1 + u_i with i = (n F + f) T + t (the library stores lambda as
+    [N][F][T]), rounded to float32; g~ and Q as in ``init_state``."""
+    u = splitmix64_uniform(seed, 0, N * F * T)
+    lam = (0.1 + u).astype(np.float32).astype(np.float64).reshape(N, F, T).transpose(1, 2, 0)
+    G, Q = _init_gq(F, M, N)
+    return np.ascontiguousarray(lam), G, Q
 
 
 # ---------------------------------------------------------------------------
@@ -119,31 +139,45 @@ def log_det_QQH(Q):
     return 2.0 * logabs
 
 
-def loglik(X, W, H, G, Q):
+def loglik_lam(X, lam, G, Q):
     """Decorrelated log-likelihood, Eq. 17:
     sum_{f,t,m} ( -x~/y~ - log y~ ) + T sum_f log|Q_f Q_f^H|  - F T M log(pi).
     The constant -FTM log(pi), dropped by the paper's "=c", is restored so that the
     value is the true log-density of Eq. 2 under the constraint of Eq. 16."""
     F, T, M = X.shape
     xt = projected_power(Q, X)
-    yt = model_power(source_psd(W, H), G)
+    yt = model_power(lam, G)
     return (float(np.sum(-xt / yt - np.log(yt))) + T * float(np.sum(log_det_QQH(Q)))
             - F * T * M * np.log(np.pi))
 
 
+def loglik(X, W, H, G, Q):
+    """Eq. 17 for the NMF source model (lambda by Eq. 9)."""
+    return loglik_lam(X, source_psd(W, H), G, Q)
+
+
 def loglik_terms_abs(X, W, H, G, Q):
     """Sum of the absolute values of the terms of Eq. 17 (scale for relative LL errors)."""
+    return loglik_terms_abs_lam(X, source_psd(W, H), G, Q)
+
+
+def loglik_terms_abs_lam(X, lam, G, Q):
+    """Sum of the absolute values of the terms of Eq. 17, lambda given."""
     F, T, M = X.shape
     xt = projected_power(Q, X)
-    yt = model_power(source_psd(W, H), G)
+    yt = model_power(lam, G)
     return (float(np.sum(np.abs(xt / yt)) + np.sum(np.abs(np.log(yt))))
             + T * float(np.sum(np.abs(log_det_QQH(Q)))) + F * T * M * np.log(np.pi))
 
 
 def full_rank_covariances(W, H, G, Q):
+    """Full-rank covariances of the NMF source model (lambda by Eq. 9)."""
+    return full_rank_covariances_lam(source_psd(W, H), G, Q)
+
+
+def full_rank_covariances_lam(lam, G, Q):
     """Y_ftn = lambda_ftn G_nf with G_nf = Q_f^-1 Diag(g~_nf) Q_f^-H (Eq. 16 solved for
     G_nf), and Y_ft = sum_n Y_ftn (Eq. 2).  Returns (Ysrc[f,t,n,M,M], Y[f,t,M,M])."""
-    lam = source_psd(W, H)
     Qi = np.linalg.inv(Q)                                            # [F,M,M]
     Gfull = np.einsum("fij,nfj,fkj->nfik", Qi, G, Qi.conj(), optimize=True)         # Q^-1 Diag(g) Q^-H
     Ysrc = np.einsum("ftn,nfik->ftnik", lam, Gfull, optimize=True)
@@ -151,10 +185,15 @@ def full_rank_covariances(W, H, G, Q):
 
 
 def loglik_fullrank(X, W, H, G, Q):
+    """Full-rank log-density of the NMF source model (lambda by Eq. 9)."""
+    return loglik_fullrank_lam(X, source_psd(W, H), G, Q)
+
+
+def loglik_fullrank_lam(X, lam, G, Q):
     """Log-density of Eq. 2 evaluated directly: sum_{f,t} log CN(x_ft | 0, Y_ft)
     = -sum ( x^H Y^-1 x + log det(pi Y) )  (Eq. 4 with its constant), with Y_ft built
     explicitly from the full-rank SCMs.  Used only as a pin of ``loglik``."""
-    _, Y = full_rank_covariances(W, H, G, Q)
+    _, Y = full_rank_covariances_lam(lam, G, Q)
     M = X.shape[2]
     sol = np.linalg.solve(Y, X[..., None])[..., 0]
     quad = np.einsum("ftm,ftm->ft", X.conj(), sol, optimize=True).real
@@ -201,9 +240,13 @@ def update_H(xt, W, H, G):
 
 
 def mu_G_terms(xt, W, H, G):
+    """The g~ rule's terms for the NMF source model (lambda by Eq. 9)."""
+    return mu_G_terms_lam(xt, source_psd(W, H), G)
+
+
+def mu_G_terms_lam(xt, lam, G):
     """Numerator and denominator of the g~ rule (Sec. III-A-2, Eq. 21):
     num[n,f,m] = sum_t lambda_ftn x~/y~^2,  den[n,f,m] = sum_t lambda_ftn / y~."""
-    lam = source_psd(W, H)
     A, B = _aux(xt, model_power(lam, G))
     num = np.einsum("ftn,ftm->nfm", lam, A, optimize=True)
     den = np.einsum("ftn,ftm->nfm", lam, B, optimize=True)
@@ -216,6 +259,27 @@ def update_G(xt, W, H, G):
     return G * np.sqrt(num / den)
 
 
+def update_G_lam(xt, lam, G):
+    """Eq. 21 with lambda given."""
+    num, den = mu_G_terms_lam(xt, lam, G)
+    return G * np.sqrt(num / den)
+
+
+def mu_lambda_terms(xt, lam, G):
+    """Numerator and denominator of the lambda rule of the unconstrained source model
+    (Sec. III-B-1, Eq. 22): num[f,t,n] = sum_m g~_nfm x~/y~^2,  den[f,t,n] = sum_m g~_nfm / y~."""
+    A, B = _aux(xt, model_power(lam, G))
+    num = np.einsum("nfm,ftm->ftn", G, A, optimize=True)
+    den = np.einsum("nfm,ftm->ftn", G, B, optimize=True)
+    return num, den
+
+
+def update_lambda(xt, lam, G):
+    """lambda_ftn <- lambda_ftn sqrt(num/den)  (Eq. 22)."""
+    num, den = mu_lambda_terms(xt, lam, G)
+    return lam * np.sqrt(num / den)
+
+
 def weighted_scm(X, yt):
     """V_fm = (1/T) sum_t x_ft x_ft^H / y~_ftm  (Sec. III-A-2, Eq. 18).  Returns V[f,m,i,j]."""
     T = X.shape[1]
@@ -223,6 +287,11 @@ def weighted_scm(X, yt):
 
 
 def update_Q(X, W, H, G, Q, trace=None):
+    """The IP update for the NMF source model (lambda by Eq. 9)."""
+    return update_Q_lam(X, source_psd(W, H), G, Q, trace)
+
+
+def update_Q_lam(X, lam, G, Q, trace=None):
     """Iterative projection (Eqs. 18-20), rows in order m = 1..M, each using the
     current Q_f (Eq. 19 has Q_f on the right-hand side):
 
@@ -233,7 +302,7 @@ def update_Q(X, W, H, G, Q, trace=None):
     are formed once before its row loop.  ``trace`` (a list) receives, after each row
     update, (f, m, q^H V q, Q_f V_fm q_fm) for the pins."""
     F, T, M = X.shape
-    yt = model_power(source_psd(W, H), G)
+    yt = model_power(lam, G)
     V = weighted_scm(X, yt)
     Qn = Q.copy()
     for f in range(F):
@@ -314,16 +383,65 @@ def iterate(X, W, H, G, Q, n_iter=1, mask=UPDATE_ALL, do_normalise=True, block_l
     return W, H, G, Q, trace
 
 
+def normalise_free(lam, G, Q):
+    """Scale normalisation of the unconstrained source model: steps 1 and 2 of ``normalise``
+    with nu_nf scaling lambda_ftn (every t) instead of w_nkf; no step 3 (there is no W, H).
+    lambda g~ and the log-likelihood are unchanged in exact arithmetic."""
+    M = Q.shape[1]
+    phi = np.einsum("fij,fij->f", Q, Q.conj(), optimize=True).real / M
+    Q = Q / np.sqrt(phi)[:, None, None]
+    G = G / phi[None, :, None]
+    nu = G.sum(axis=2)                                               # [N,F]
+    G = G / nu[:, :, None]
+    lam = lam * nu.T[:, None, :]
+    return lam, G, Q
+
+
+def iterate_free(X, lam, G, Q, n_iter=1, mask=UPDATE_ALL, do_normalise=True, block_ll=None):
+    """n_iter FastFCA iterations (Sec. III-C-1: the unconstrained source model of Sec.
+    III-B-1 in the jointly diagonalisable spatial model, with the IP update of Q).  Block
+    order, as for FastMNMF: lambda (Eq. 22; mask bit UPDATE_W) -> g~ (Eq. 21) -> Q (Eqs.
+    18-20) -> normalise, every block from the current parameters.
+    Returns (lam, G, Q, ll_trace); lam is [F, T, N]."""
+    lam = np.array(lam, dtype=np.float64)
+    G = np.array(G, dtype=np.float64)
+    Q = np.array(Q, dtype=np.complex128)
+    X = np.asarray(X, dtype=np.complex128)
+    trace = []
+    for _ in range(n_iter):
+        xt = projected_power(Q, X)
+        if mask & UPDATE_W:
+            lam = update_lambda(xt, lam, G)
+            if block_ll is not None:
+                block_ll.append(("lambda", loglik_lam(X, lam, G, Q)))
+        if mask & UPDATE_G:
+            G = update_G_lam(xt, lam, G)
+            if block_ll is not None:
+                block_ll.append(("G", loglik_lam(X, lam, G, Q)))
+        if mask & UPDATE_Q:
+            Q = update_Q_lam(X, lam, G, Q)
+            if block_ll is not None:
+                block_ll.append(("Q", loglik_lam(X, lam, G, Q)))
+        if do_normalise:
+            lam, G, Q = normalise_free(lam, G, Q)
+        trace.append(loglik_lam(X, lam, G, Q))
+    return lam, G, Q, trace
+
+
 # ---------------------------------------------------------------------------
 # Separation
 # ---------------------------------------------------------------------------
 def separate(X, W, H, G, Q):
+    """Wiener separation for the NMF source model (lambda by Eq. 9)."""
+    return separate_lam(X, source_psd(W, H), G, Q)
+
+
+def separate_lam(X, lam, G, Q):
     """Multichannel Wiener filter of Eq. 3 in the diagonalised form.  Substituting
     G_nf = Q_f^-1 Diag(g~_nf) Q_f^-H (Eq. 16) into Y_ftn Y_ft^-1 gives
     Q_f^-1 Diag(lambda_ftn g~_nf / y~_ft) Q_f, so
         x_ftn = Q_f^-1 ( lambda_ftn g~_nf / y~_ft  (elementwise)  Q_f x_ft ).
     Returns out[n,f,t,m] (every channel of every source image)."""
-    lam = source_psd(W, H)
     yt = model_power(lam, G)
     QX = np.einsum("fmj,ftj->ftm", Q, X, optimize=True)
     Qi = np.linalg.inv(Q)
@@ -332,8 +450,13 @@ def separate(X, W, H, G, Q):
 
 
 def separate_direct(X, W, H, G, Q):
+    """Direct Wiener filter for the NMF source model (lambda by Eq. 9)."""
+    return separate_direct_lam(X, source_psd(W, H), G, Q)
+
+
+def separate_direct_lam(X, lam, G, Q):
     """Eq. 3 evaluated literally, x_ftn = Y_ftn Y_ft^-1 x_ft with explicit full-rank
     matrices (pin of ``separate``)."""
-    Ysrc, Y = full_rank_covariances(W, H, G, Q)
+    Ysrc, Y = full_rank_covariances_lam(lam, G, Q)
     sol = np.linalg.solve(Y, X[..., None])[..., 0]                   # Y_ft^-1 x_ft
     return np.einsum("ftnij,ftj->nfti", Ysrc, sol, optimize=True)
