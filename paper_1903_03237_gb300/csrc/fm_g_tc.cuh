@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t xbar[kGtcIn];
   __shared__ __align__(8) uint64_t rbar[2];
+  __shared__ __align__(8) uint64_t never_bar;  // nothing arrives here (test limit only)
+  __shared__ int s_to, s_mma_last;             // a wait ran out; last stage with committed MMAs
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int F = p.F, T = p.T, N = p.N, M = p.M;
@@ -85,6 +87,9 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
     mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1);
     for (int i = 0; i < kGtcIn; ++i) mbar_init(&xbar[i], 1);
     mbar_init(&rbar[0], kGtcThreads); mbar_init(&rbar[1], kGtcThreads);
+    mbar_init(&never_bar, 1);
+    s_to = 0;
+    s_mma_last = -1;
   }
   for (int e = tid; e < C::FG * N * MAXM; e += kGtcThreads + 32) {
     const int g = e / (N * MAXM), r = e % (N * MAXM), n = r / MAXM, m = r % MAXM;
@@ -97,6 +102,7 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
   const uint32_t tacc = tbase;
   constexpr uint32_t idesc = idesc_bf16_f32(128, C::NC);
   constexpr uint32_t kMaxTries = 1u << 22;
+  const uint32_t lim = p.wait_limit ? p.wait_limit : kMaxTries;  // consumer waits
   bool ok = true;
 
   // register accumulators: TMEM lane r = A row (ab, g, m); columns g*NP + n
@@ -126,9 +132,13 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       for (int c = 0; c < min(kGtcIn, nst); ++c) issue_in(c);
       issued = min(kGtcIn, nst) - 1;
     }
+    int mma_last = -1;
     for (int c = 0; c < nst; ++c) {
-      if (!mbar_wait(&rbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
+      uint64_t* wb = (p.wait_limit && c == 0) ? &never_bar : &rbar[c & 1];  // test limit: runs out
+      // warp-uniform decision: the lanes meet at __syncwarp below
+      if (!__all_sync(0xffffffffu, mbar_wait(wb, (uint32_t)((c >> 1) & 1), lim))) { ok = false; break; }
       tc_fence_after();
+      mma_last = c;
       if (lane == 0) {
         unsigned char* st = ssm + (c & 1) * C::OPS;
         const uint32_t acc = tacc + (uint32_t)(((c / C::SPB) & 1) * C::NC);
@@ -150,8 +160,10 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       // the MMAs first keeps them off the copies' issue time
       if (use_tma && c + kGtcIn < nst) { issue_in(c + kGtcIn); issued = c + kGtcIn; }
     }
+    if (lane == 0) s_mma_last = mma_last;
     if (!ok) {
-      if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (lane == 0) { atomicOr(p.status, ST_TIMEOUT); s_to = 1; }
+      // copies still in flight land before the CTA releases its shared memory (bounded)
       for (int c = max(0, issued - kGtcIn + 1); c <= issued; ++c)
         mbar_wait(&xbar[c % kGtcIn], (uint32_t)((c / kGtcIn) & 1), kMaxTries);
     }
@@ -183,13 +195,18 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       unsigned char* Al = st + C::A_BYTES;
       unsigned char* Bh = st + 2 * C::A_BYTES;
       unsigned char* Bl = Bh + C::B_BYTES;
-      if (c >= 2 && !mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
+      // decisions are warp-uniform at least: flush() reads TMEM with a warp-collective load
+      const bool to = c >= 2 && !__all_sync(0xffffffffu, mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), lim));
       tc_fence_after();
-      if (c >= 2 && (c - 2) % C::SPB == C::SPB - 1) flush((c - 2) / C::SPB);
+      if (!to && c >= 2 && (c - 2) % C::SPB == C::SPB - 1) flush((c - 2) / C::SPB);
       float* xs = xbuf(c);
       float* ls = lbuf(c);
       if (use_tma) {
-        if (!mbar_wait(&xbar[c % kGtcIn], (uint32_t)((c / kGtcIn) & 1), kMaxTries)) { ok = false; break; }
+        // no barrier among the formation warps on this path: each may leave on its own
+        if (to || !__all_sync(0xffffffffu, mbar_wait(&xbar[c % kGtcIn], (uint32_t)((c / kGtcIn) & 1), lim))) {
+          ok = false;
+          break;
+        }
       } else {
         for (int e = tid; e < nbins * nt * M; e += kGtcThreads) {
           const int g = e / (nt * M), j = e - g * (nt * M);
@@ -199,7 +216,15 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
           const int gn = e / nt, t = e - gn * nt, g = gn / N, n = gn % N;
           ls[(n * C::FG + g) * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
         }
-        asm volatile("bar.sync 1, %0;\n" ::"n"(kGtcThreads) : "memory");
+        // barrier 1 over the formation warps, with the OR of their timeout flags: they leave
+        // together
+        uint32_t any;
+        asm volatile(
+            "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(any)
+            : "r"(to ? 1u : 0u), "n"(kGtcThreads)
+            : "memory");
+        if (any) { ok = false; break; }
       }
       // ---- A rows: x~/y~^2 and 1/y~ for 8 frames of (bin, channel); rows (ab, g, m) ----
       for (int e = tid; e < C::NA_ITEMS; e += kGtcThreads) {
@@ -272,7 +297,8 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
     }
     const int ndone = c;
     if (ok && ndone >= 1) {
-      if (!mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), kMaxTries)) ok = false;
+      if (!__all_sync(0xffffffffu, mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), lim)))
+        ok = false;
       tc_fence_after();
       if (ok) {
         const int last = (ndone - 1) / C::SPB;
@@ -281,8 +307,7 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
       }
     }
     if (!ok) {
-      if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-      if (ndone >= 1) mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), kMaxTries);
+      if (lane == 0) { atomicOr(p.status, ST_TIMEOUT); s_to = 1; }
     } else if (rg < nbins && rm < M) {
       // partials in the layout of the g~ sweep: part[s][(ab*N + n)*F + f][m]
       const size_t psz = (size_t)2 * N * F * M;
@@ -296,6 +321,14 @@ __global__ void __launch_bounds__(kGtcThreads + 32, 4) k_g_tc(Prob p, int S, int
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (s_to) {
+    // after a timeout: the MMAs the MMA warp committed land before the TMEM is freed
+    const int last = s_mma_last;
+    if (tid == 0 && last >= 0) mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1), kMaxTries);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
   if (warp == 0) tmem_dealloc(tacc, C::TCOLS);
 
   // the last split of this bin group to finish applies g~ <- g~ sqrt(num / den)

@@ -10,7 +10,9 @@
 // (MMA M = 128, N = NT), looping over its split of the K dimension in chunks of 64; two shared-memory stages let the
 // threads fill one stage while the tensor core works on the other.  One thread issues the
 // MMAs and commits them to an mbarrier per stage; every wait is bounded and reports
-// ST_TIMEOUT instead of hanging.
+// ST_TIMEOUT instead of hanging.  The CTA takes a timeout decision together (a barrier with
+// an OR of the threads' results), then waits, with the full bound, for the MMAs it committed
+// before it frees its TMEM.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -29,6 +31,7 @@ struct GemmArgs {
   float* C; long long sCs, sCb, sCi, sCj;   // output (split s, batch b, row i, column j)
   int Mr, Nc, Kd, batch, ksplit, kspan;      // kspan = K elements per split (multiple of kGemmKc)
   unsigned* status;
+  unsigned wait_limit;                       // test limit of the consumer waits (0: normal), see Prob
 };
 
 __host__ __device__ inline int gemm_stage_bytes(int nt, bool tf32) {
@@ -135,6 +138,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   constexpr int STAGE = A_BYTES + B_BYTES;
   constexpr uint32_t TCOLS = NT < 32 ? 32 : NT;      // TMEM columns (power of two >= 32)
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t never_bar;  // nothing arrives here (test limit only)
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.x * 128, j0 = blockIdx.y * NT;
@@ -148,13 +152,14 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   const bool vecB = g.sBk == 1 && (g.sBj & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
 
   if (warp == 0) { tmem_alloc(&tbase, TCOLS); tmem_relinquish(); }
-  if (tid == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
+  if (tid == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); mbar_init(&never_bar, 1); }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tacc = tbase;
   constexpr uint32_t idesc = TF32 ? idesc_tf32_f32(128, NT) : idesc_bf16_f32(128, NT);
   constexpr uint32_t kMaxTries = 1u << 22;
+  const uint32_t lim = g.wait_limit ? g.wait_limit : kMaxTries;  // consumer waits
 
   bool ok = true;
   int c = 0;
@@ -176,9 +181,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   }
   for (int k0 = kbeg; k0 < kend; k0 += kGemmKc, ++c) {
     unsigned char* st = gsm + (c & 1) * STAGE;
-    if (c >= 2) {  // the MMAs of chunk c-2 read this stage: wait for them
-      if (!mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
-    }
+    // the MMAs of chunk c-2 read this stage: wait for them (after a timeout the stores below
+    // may overwrite operands still being read: results are then flagged, memory stays in bounds)
+    const bool to = c >= 2 && !mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), lim);
     const int kn = min(kGemmKc, kend - k0);
     if constexpr (kPipe) {
       gemm_tile_store<TF32, 128>(0, va, st);
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
     }
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
+    if (__syncthreads_or(to ? 1 : 0)) { ok = false; break; }  // the whole CTA leaves together
     tc_fence_after();
     if (tid == 0) {
       const uint32_t sa = smem_u32(st), sb = smem_u32(st + A_BYTES);
@@ -215,10 +220,17 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       umma_commit(&mbar[c & 1]);
     }
   }
-  const int nchunks = c;
+  const int nchunks = c;  // chunks whose MMAs were committed (the same in every thread)
   // wait for the last one or two chunks
-  if (ok && nchunks >= 2 && !mbar_wait(&mbar[(nchunks - 2) & 1], (uint32_t)(((nchunks - 2) >> 1) & 1), kMaxTries)) ok = false;
-  if (ok && nchunks >= 1 && !mbar_wait(&mbar[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1), kMaxTries)) ok = false;
+  bool to = !ok;
+  if (!to && g.wait_limit) to = !mbar_wait(&never_bar, 0u, lim);  // test limit: runs out
+  if (!to && nchunks >= 2) to = !mbar_wait(&mbar[(nchunks - 2) & 1], (uint32_t)(((nchunks - 2) >> 1) & 1), lim);
+  if (!to && nchunks >= 1) to = !mbar_wait(&mbar[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1), lim);
+  if (__syncthreads_or(to ? 1 : 0)) {
+    ok = false;
+    // drain: every committed MMA lands before TMEM is freed (completion is in issue order)
+    if (nchunks >= 1) mbar_wait(&mbar[(nchunks - 1) & 1], (uint32_t)(((nchunks - 1) >> 1) & 1), kMaxTries);
+  }
   tc_fence_after();
   float* Cb = g.C + (long long)s * g.sCs + (long long)b * g.sCb;
   if (!ok) {

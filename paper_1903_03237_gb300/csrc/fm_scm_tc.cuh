@@ -111,8 +111,17 @@ __device__ __forceinline__ void form_products(const float2* __restrict__ xg, int
   }
 }
 
-// barrier 1 over the formation warps only (the MMA warp does not take part)
-__device__ __forceinline__ void formation_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kScmThreads) : "memory"); }
+// barrier 1 over the formation warps only (the MMA warp does not take part), with the OR of
+// a per-thread flag: the formation warps take a timeout decision together at it
+__device__ __forceinline__ bool formation_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(kScmThreads)
+      : "memory");
+  return r != 0;
+}
 
 // EXACT: M == MAXM (a compile-time channel count in the address arithmetic).
 // Warps 0-3 form the operands and own the TMEM lanes (accumulator rows); warp 4 issues the
@@ -121,6 +130,9 @@ __device__ __forceinline__ void formation_sync() { asm volatile("bar.sync 1, %0;
 //   rbar[i]: the operands of the stage in operand buffer i are formed (128 arrivals), which
 //            also frees that stage's input buffer;
 //   mbar[i]: the MMAs of the stage in operand buffer i completed (tcgen05.commit).
+// A wait that runs out ends the waiting warp's loop; the CTA then meets at one barrier, and
+// one thread waits (with the full bound) for the last MMAs the MMA warp committed before the
+// TMEM is freed.
 template <int MAXM, bool EXACT>
 __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, int span, int lam_tma,
                                                                 const __grid_constant__ CUtensorMap tm_lam) {
@@ -130,6 +142,8 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t xbar[ScmCfg<MAXM>::IN];
   __shared__ __align__(8) uint64_t rbar[2];
+  __shared__ __align__(8) uint64_t never_bar;  // nothing arrives here (test limit only)
+  __shared__ int s_to, s_mma_last;             // a wait ran out; last stage with committed MMAs
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int F = p.F, T = p.T, N = p.N;
@@ -157,6 +171,9 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
     mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1);
     for (int i = 0; i < C::IN; ++i) mbar_init(&xbar[i], 1);
     mbar_init(&rbar[0], kScmThreads); mbar_init(&rbar[1], kScmThreads);
+    mbar_init(&never_bar, 1);
+    s_to = 0;
+    s_mma_last = -1;
   }
   for (int e = tid; e < C::FG * N * MAXM; e += kScmThreads + 32) {
     const int g = e / (N * MAXM), r = e % (N * MAXM), n = r / MAXM, m = r % MAXM;
@@ -169,6 +186,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
   const uint32_t tacc = tbase;
   constexpr uint32_t idesc = idesc_bf16_f32(128, C::NC);
   constexpr uint32_t kMaxTries = 1u << 22;
+  const uint32_t lim = p.wait_limit ? p.wait_limit : kMaxTries;  // consumer waits
   bool ok = true;
 
   if (warp == MMA_WARP) {
@@ -202,9 +220,13 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       for (int c = 0; c < min(C::IN, nst); ++c) issue_in(c);
       issued = min(C::IN, nst) - 1;
     }
+    int mma_last = -1;
     for (int c = 0; c < nst; ++c) {
-      if (!mbar_wait(&rbar[c & 1], (uint32_t)((c >> 1) & 1), kMaxTries)) { ok = false; break; }
+      uint64_t* wb = (p.wait_limit && c == 0) ? &never_bar : &rbar[c & 1];  // test limit: runs out
+      // warp-uniform decision: the lanes meet at __syncwarp below
+      if (!__all_sync(0xffffffffu, mbar_wait(wb, (uint32_t)((c >> 1) & 1), lim))) { ok = false; break; }
       tc_fence_after();
+      mma_last = c;
       if (lane == 0) {
         unsigned char* st = ssm + (c & 1) * C::OPS;
         const uint32_t acc = tacc + (uint32_t)(((c / C::SPB) & 1) * C::NC);
@@ -226,8 +248,9 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       // MMAs first keeps them off the copies' issue time
       if (use_tma && c + C::IN < nst) { issue_in(c + C::IN); issued = c + C::IN; }
     }
+    if (lane == 0) s_mma_last = mma_last;
     if (!ok) {
-      if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (lane == 0) { atomicOr(p.status, ST_TIMEOUT); s_to = 1; }
       // copies still in flight land before the CTA releases its shared memory (bounded)
       for (int c = max(0, issued - C::IN + 1); c <= issued; ++c)
         mbar_wait(&xbar[c % C::IN], (uint32_t)((c / C::IN) & 1), kMaxTries);
@@ -286,14 +309,19 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       unsigned char* Bh = st + 2 * C::A_BYTES;
       unsigned char* Bl = Bh + C::B_BYTES;
       // the MMAs of stage c-2 read this operand buffer (and those before it are done too)
-      if (c >= 2 && !mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kMaxTries)) { ok = false; break; }
+      // decisions are warp-uniform at least: flush() reads TMEM with a warp-collective load
+      const bool to = c >= 2 && !__all_sync(0xffffffffu, mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), lim));
       tc_fence_after();
       // the block that ended with stage c-2 goes into the registers
-      if (c >= 2 && (c - 2) % C::SPB == C::SPB - 1) flush((c - 2) / C::SPB);
+      if (!to && c >= 2 && (c - 2) % C::SPB == C::SPB - 1) flush((c - 2) / C::SPB);
       float2* xs = xbuf(c);
       float* ls = lbuf(c);
       if (use_tma) {
-        if (!mbar_wait(&xbar[c % C::IN], (uint32_t)((c / C::IN) & 1), kMaxTries)) { ok = false; break; }
+        // no barrier among the formation warps on this path: each may leave on its own
+        if (to || !__all_sync(0xffffffffu, mbar_wait(&xbar[c % C::IN], (uint32_t)((c / C::IN) & 1), lim))) {
+          ok = false;
+          break;
+        }
       } else {
         for (int e = tid; e < nbins * nt * M; e += kScmThreads) {
           const int g = e / (nt * M), j = e - g * (nt * M), t = j / M;
@@ -304,7 +332,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
             const int gn = e / nt, t = e - gn * nt, g = gn / N, n = gn % N;
             ls[(n * C::FG + g) * KC + t] = p.lam[((size_t)n * F + f0 + g) * T + t0 + t];
           }
-        formation_sync();
+        if (formation_sync_or(to)) { ok = false; break; }  // leave together
       }
 
       // ---- B operand: 1/y~ of 8 frames per (bin, channel); y~ written to the state ----
@@ -360,7 +388,8 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
     const int ndone = c;  // stages this thread formed
     if (ok && ndone >= 1) {
       // all MMAs: wait for the last stage's commit (completion is in issue order)
-      if (!mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), kMaxTries)) ok = false;
+      if (!__all_sync(0xffffffffu, mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), lim)))
+        ok = false;
       tc_fence_after();
       if (ok) {
         const int last = (ndone - 1) / C::SPB;
@@ -370,9 +399,7 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
       }
     }
     if (!ok) {
-      if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-      // MMAs still in flight complete before the CTA releases its memory (bounded)
-      if (ndone >= 1) mbar_wait(&mbar[(ndone - 1) & 1], (uint32_t)(((ndone - 1) >> 1) & 1), kMaxTries);
+      if (lane == 0) { atomicOr(p.status, ST_TIMEOUT); s_to = 1; }
     } else {
       const int f = f0 + rbin;
       if (rbin < nbins && rc < M && ra < M) {
@@ -386,6 +413,14 @@ __global__ void __launch_bounds__(kScmThreads + 32, 4) k_scm_tc(Prob p, int S, i
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (s_to) {
+    // after a timeout: the MMAs the MMA warp committed land before the TMEM is freed
+    const int last = s_mma_last;
+    if (tid == 0 && last >= 0) mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1), kMaxTries);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
   if (warp == 0) tmem_dealloc(tacc, C::TCOLS);
 }
 
