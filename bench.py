@@ -39,6 +39,11 @@ WORKLOADS = {
 }
 WORKLOAD = WORKLOADS["c1"]
 PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2}
+# timed forms: (precision, schedule).  "fused": FP32 with the bin-fused schedule (two launches
+# per iteration); "sweep": FP32 with one tiled launch per block (the plain form);
+# "bf16" / "tf32": the mixed-precision forms (tensor-core contractions).
+FORMS = {"fused": ("fp32", 2), "sweep": ("fp32", 1), "bf16": ("bf16", 0), "tf32": ("tf32", 0)}
+DTYPES = {"fused": "f32", "sweep": "f32", "bf16": "bf16", "tf32": "tf32"}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock = 80.5 TFLOP/s
 
 
@@ -53,6 +58,13 @@ def kernel_flops(kind: str, F, T, M, N, K) -> float:
         "h_update": 6 * N * K + 6 * N * M + 4 * M,
         # lambda (2NK), y~ (2NM), A, B (4M), num/den over t (4NM)
         "g_update": 2 * N * K + 6 * N * M + 4 * M,
+        # fused per-bin kernel: lambda of the bin (2NK), g~ update (y~ 2NM, A, B 4M, sums 4NM),
+        # V_fm (y~ 2NM, 1/y~ M, products 2M^2, sums 2M^3), x~ (8M^2), y~ and the log-likelihood
+        # terms (2NM + 3M), P, R of the W update (4NM + 4M), W sums over t (4NK), lambda of the
+        # new W (2NK), P, R of the H update (y~ 2NM, A, B 4M, 4NM)
+        "bin": 8 * N * K + 20 * N * M + 16 * M + 10 * M * M + 2 * M ** 3,
+        # fused H GEMM: num and den sums over f (4NK)
+        "hgemm": 4 * N * K,
         # lambda, y~, 1/y~, x x^H (3 M^2), V accumulation (2 M * M^2)
         "scm": 2 * N * K + 2 * N * M + M + 3 * mm + 2 * M * mm,
         # Q x (8 M^2), |.|^2, LL term (4M)
@@ -90,7 +102,7 @@ def kernel_bytes(kind: str, F, T, M, N, K) -> float:
 
 def roofline_for(dom, avg_ms, precision, F, T, M, N, K, workload):
     peaks = read_peaks() or {}
-    if precision == "fp32" and kernel_flops(dom, F, T, M, N, K) > 0:
+    if precision in ("fp32", "fused", "sweep") and kernel_flops(dom, F, T, M, N, K) > 0:
         achieved = kernel_flops(dom, F, T, M, N, K) / (avg_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": read_traffic(dom, workload, precision), "kernel": dom,
@@ -244,19 +256,20 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         # the same config as this arm's line (impl and dtype tell the two apart)
         "data": "synthetic",
-        "config": _config(args.precision) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": _config(args.form) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def _config(precision="fp32"):
+def _config(form="fused"):
     w = WORKLOAD
-    prec = {"fp32": "plain FP32 (float-float IP solve)",
+    prec = {"fused": "FP32, bin-fused schedule (two launches per iteration), float-float IP solve",
+            "sweep": "FP32, one tiled launch per block (plain form), float-float IP solve",
             "bf16": "mixed: BF16 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
                     "and g~ sums, FP32 accumulation, float-float IP solve",
             "tf32": "mixed: TF32 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
-                    "and g~ sums, FP32 accumulation, float-float IP solve"}[precision]
+                    "and g~ sums, FP32 accumulation, float-float IP solve"}[form]
     name = "paper-scale single mixture" if WORKLOAD is WORKLOADS["c1"] else "large mixture"
     return {"workload": f"{name} M{w['M']} N{w['N']} K{w['K']} F{w['F']} T{w['T']}, "
                         f"{w['iters']} iterations + Wiener separation per step",
@@ -264,7 +277,7 @@ def _config(precision="fp32"):
             "l2": "flushed between timed steps (512 MB write)", "precision": prec}
 
 
-def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local, sample_clocks):
+def _measure(fm, torch, mix, args, form, steps, warmup, rank, world, local, sample_clocks):
     """Times one form on the workload: each step is a whole job (fresh initial state, the
     workload's iterations, Wiener separation) with X resident in HBM; then the same job end
     to end through the C ABI with host buffers.  Returns the numbers of the bench line."""
@@ -273,7 +286,9 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
     stream = torch.cuda.Stream()
     Xd = torch.from_numpy(mix.X).cuda()
     torch.cuda.synchronize()
-    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream, precision=PRECISIONS[precision])
+    precision, schedule = FORMS[form]
+    ctx = fm.Context(Xd, N, K, seed=rank, stream=stream.cuda_stream, precision=PRECISIONS[precision],
+                     schedule=schedule)
     out = torch.empty((N, F, T, M), dtype=torch.complex64, device="cuda")
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
@@ -341,7 +356,7 @@ def _measure(fm, torch, mix, args, precision, steps, warmup, rank, world, local,
 
     # roofline of the dominant kernel, from its launches inside the timed region
     avg_ms = kt[dom][0] / kt[dom][1]
-    roofline = roofline_for(dom, avg_ms, precision, F, T, M, N, K, args.workload)
+    roofline = roofline_for(dom, avg_ms, form, F, T, M, N, K, args.workload)
     roofline["launches_timed"] = kt[dom][1]
 
     # end to end through the C ABI with host buffers: H2D mixture, iterations, D2H images
@@ -384,15 +399,34 @@ def run_ours(args):
     w = WORKLOAD
     F, T, M, N, K, iters = w["F"], w["T"], w["M"], w["N"], w["K"], w["iters"]
     mix = make_mixture(F, T, M, N, K, seed=rank, diffuse_frac=w["diffuse"])
-    res = _measure(fm, torch, mix, args, args.precision, args.steps, args.warmup, rank, world, local, True)
-    # the plain FP32 form on the same workload, for the comparison the metric names
-    plain = None
-    if args.precision != "fp32" and not args.no_compare:
-        psteps = max(2, min(args.steps, 3))
-        pr = _measure(fm, torch, mix, args, "fp32", psteps, max(3, args.warmup), rank, world, local, False)
-        plain = {"value": pr["value"], "ms_per_step": pr["ms_per_step"], "e2e_value": pr["e2e"], "steps": psteps,
-                 "autotune": pr["tune"],
-                 "dominant_kernel": pr["roofline"]["kernel"], "roofline_frac": pr["roofline"]["frac"]}
+    res = _measure(fm, torch, mix, args, args.form, args.steps, args.warmup, rank, world, local, True)
+    # the plain FP32 form (one launch per block) and the mixed BF16 form on the same
+    # workload, for the comparison the metric names
+    others = {}
+    if not args.no_compare:
+        for name, form in (("plain_fp32", "sweep"), ("mixed_bf16", "bf16")):
+            if form == args.form:
+                continue
+            psteps = max(2, min(args.steps, 3))
+            pr = _measure(fm, torch, mix, args, form, psteps, max(3, args.warmup), rank, world, local, False)
+            others[name] = {"value": pr["value"], "ms_per_step": pr["ms_per_step"], "e2e_value": pr["e2e"],
+                            "steps": psteps, "autotune": pr["tune"], "dominant_kernel": pr["roofline"]["kernel"],
+                            "roofline_frac": pr["roofline"]["frac"]}
+
+    serving = None
+    if rank == 0 and not args.no_serving:
+        # the metric's serving half, bounded: 300 requests at 20 req/s, then a saturated burst
+        # of 200 (every request queued at once), each with the one-at-a-time comparison
+        cb, fifo = serving_replay(fm, 300, 20.0, args.max_active, args.form)
+        cb2, fifo2 = serving_replay(fm, 200, 0.0, args.max_active, args.form)
+        keep = ("p50_ms", "p99_ms", "throughput", "completed", "failed")
+        serving = {"workload": "Poisson arrivals (seed 7), M4 N3 K16 F513, T lognormal (median 375, sigma 0.6, cap "
+                               "6000), 50 iterations + Wiener per request; latency = completion - arrival",
+                   "unit_throughput": UNIT, "max_active": args.max_active, "iters_per_step": 10,
+                   "rate_20_per_s": {"requests": 300, "continuous_batching": {k: cb[k] for k in keep},
+                                     "one_at_a_time": {k: fifo[k] for k in keep}},
+                   "burst_200_at_once": {"requests": 200, "continuous_batching": {k: cb2[k] for k in keep},
+                                         "one_at_a_time": {k: fifo2[k] for k in keep}}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -409,18 +443,21 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.form],
             "data": "synthetic",
-            "config": _config(args.precision) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": _config(args.form) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": res["roofline"], "cpu_baseline": cpu,
             "e2e": {"value": res["e2e"], "unit": UNIT, "h2d_bytes_per_step": F * T * M * 8,
                     "d2h_bytes_per_step": N * F * T * M * 8},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "kernel_share": res["shares"], "kernel_avg_us": res["avg_us"], "autotune": res["tune"],
         }
-        if plain is not None:
-            line["plain_fp32"] = plain
-            line["speedup_vs_plain_fp32"] = res["value"] / plain["value"]
+        for name, o in others.items():
+            line[name] = o
+        if serving is not None:
+            line["serving"] = serving
+        if "plain_fp32" in others:
+            line["speedup_vs_plain_fp32"] = res["value"] / others["plain_fp32"]["value"]
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -446,11 +483,11 @@ def run_batched(args):
     from paper_1903_03237_gb300.synth import make_mixture
     iters = 50
     inst = c3_instances(args.instances)
-    prec = PRECISIONS[args.precision]
+    prec, sched = PRECISIONS[FORMS[args.form][0]], FORMS[args.form][1]
     ctxs = []
     for (F, T, M, N, K, sd) in inst:
         mix = make_mixture(F, T, M, N, K, sd)
-        ctxs.append(fm.Context(mix.X, N, K, seed=sd, precision=prec))
+        ctxs.append(fm.Context(mix.X, N, K, seed=sd, precision=prec, schedule=sched))
     units = sum(F * T * iters for (F, T, M, N, K, sd) in inst)
     batch = fm.Batch(ctxs)
 
@@ -493,10 +530,10 @@ def run_batched(args):
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
+        "dtype": DTYPES[args.form], "data": "synthetic",
         "config": {"workload": f"batched: {len(inst)} mixtures, T ~ U{{200..4000}}, M in {{2,4,8}}, N = M, K 16, "
                                f"F 513, {iters} iterations each, one graph launch per step, autotuned split scale",
-                   "l2": "flushed between timed steps (512 MB write)", "precision": args.precision},
+                   "l2": "flushed between timed steps (512 MB write)", "form": args.form},
         "sequential_value": units * args.steps / t_s, "batched_over_sequential": t_s / t_b,
         "untuned_value": units * args.steps / t_u, "tuned_over_untuned": t_u / t_b,
         "tuner_trial_speedup": tune_speedup, "tuned_scales": ctxs[0].get_tuning(),
@@ -505,23 +542,20 @@ def run_batched(args):
     batch.close()
 
 
-def run_serving(args):
-    """Serving workload: Poisson arrivals at 20 requests/s (arrival seed 7); each request
-    M 4, N 3, K 16, F 513, T = min(6000, round(exp(ln 375 + 0.6 Z))), per-request seed
-    2000 + i, 50 iterations then the Wiener separation.  Requests are submitted at their
-    arrival times; latency = completion - arrival.  Runs the continuous-batching server and,
-    for comparison, the same arrivals served one request at a time (FIFO, max_active 1)."""
-    import torch
-    from paper_1903_03237_gb300.build import build
-    build()
-    from paper_1903_03237_gb300 import fastmnmf as fm
+def serving_replay(fm, requests, rate, max_active, form, iters=50):
+    """Serving workload: Poisson arrivals (arrival seed 7; rate 0 = every request queued at
+    once); each request M 4, N 3, K 16, F 513, T = min(6000, round(exp(ln 375 + 0.6 Z))),
+    per-request seed 2000 + i, `iters` iterations then the Wiener separation.  Requests are
+    submitted at their arrival times; latency = completion - arrival.  Runs the
+    continuous-batching server and, for comparison, the same arrivals served one request at a
+    time (FIFO, max_active 1).  Returns both summaries."""
     from paper_1903_03237_gb300.synth import make_mixture
-    R = args.requests
+    R = requests
     rng = np.random.default_rng(7)
     gaps = rng.exponential(1.0 / 20.0, size=R)
     arrivals = np.cumsum(gaps) - gaps[0]
-    if args.rate > 0:
-        arrivals = arrivals * (20.0 / args.rate)
+    if rate > 0:
+        arrivals = arrivals * (20.0 / rate)
     else:  # capacity: every request queued at once
         arrivals = np.zeros(R)
     Ts = np.minimum(6000, np.round(np.exp(np.log(375.0) + 0.6 * rng.standard_normal(R)))).astype(int)
@@ -530,15 +564,15 @@ def run_serving(args):
     pool = [make_mixture(513, int(Ts.max()), 4, 3, 16, 2000 + i).X for i in range(4)]
     reqs = [np.ascontiguousarray(pool[i % 4][:, :T, :]) for i, T in enumerate(Ts)]
 
-    def serve(max_active):
-        with fm.Server(max_active=max_active, iters_per_step=10, precision=PRECISIONS[args.precision]) as srv:
+    def serve(ma):
+        with fm.Server(max_active=ma, iters_per_step=10, precision=PRECISIONS[FORMS[form][0]]) as srv:
             ids = []
             t0 = time.perf_counter()
             for i in range(R):
                 now = time.perf_counter() - t0
                 if arrivals[i] > now:
                     time.sleep(arrivals[i] - now)
-                ids.append(srv.submit(reqs[i], 3, 16, 50, seed=2000 + i))
+                ids.append(srv.submit(reqs[i], 3, 16, iters, seed=2000 + i))
             lat, done_units, failed = [], 0.0, {}
             for i, j in enumerate(ids):
                 srv.wait(j, 600.0)
@@ -550,21 +584,29 @@ def run_serving(args):
                     failed[name] = failed.get(name, 0) + 1
                     continue
                 lat.append(l)
-                done_units += 513 * int(Ts[i]) * 50
+                done_units += 513 * int(Ts[i]) * iters
             wall = time.perf_counter() - t0
         lat = np.array(lat)
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "throughput": done_units / wall, "wall_s": wall, "completed": int(len(lat)), "failed": failed}
 
-    cb = serve(args.max_active)
-    fifo = serve(1)
+    return serve(max_active), serve(1)
+
+
+def run_serving(args):
+    """--workload c4: the serving replay at its full length (2000 requests by default)."""
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    R = args.requests
+    cb, fifo = serving_replay(fm, R, args.rate, args.max_active, args.form)
     print(json.dumps({
         "metric": METRIC, "value": cb["throughput"], "unit": UNIT, "n_gpus": 1, "steps": R, "warmup": 0,
         "ms_per_step": 1e3 * cb["wall_s"] / R, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.precision], "data": "synthetic",
+        "dtype": DTYPES[args.form], "data": "synthetic",
         "config": {"workload": f"serving: {R} requests, Poisson {args.rate:g}/s, M4 N3 K16 F513, T lognormal (median 375, "
                                "sigma 0.6, cap 6000), 50 iterations + Wiener each",
-                   "max_active": args.max_active, "iters_per_step": 10, "precision": args.precision},
+                   "max_active": args.max_active, "iters_per_step": 10, "form": args.form},
         "latency_p50_ms": cb["p50_ms"], "latency_p99_ms": cb["p99_ms"],
         "completed": cb["completed"], "failed": cb["failed"],
         "fifo": fifo,
@@ -582,7 +624,8 @@ def profile_run(args):
     w = WORKLOAD
     F = args.bins or w["F"]
     mix = make_mixture(F, w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
-    with fm.Context(mix.X, w["N"], w["K"], seed=0, precision=PRECISIONS[args.precision]) as ctx:
+    with fm.Context(mix.X, w["N"], w["K"], seed=0, precision=PRECISIONS[FORMS[args.form][0]],
+                    schedule=FORMS[args.form][1]) as ctx:
         ctx.iterate(2)
         ctx.separate()
         print("profile run ok, log-likelihood", ctx.loglik())
@@ -604,10 +647,11 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0,
                     help="c4: arrival rate in requests/s (the same arrival pattern, rescaled); 0 = all at once")
     ap.add_argument("--instances", type=int, default=64, help="c3: number of mixtures")
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
-                    help="form to time: bf16 (default, the mixed-precision form), tf32, or fp32 (plain)")
+    ap.add_argument("--form", choices=sorted(FORMS), default="fused",
+                    help="form to time: fused (default: FP32, bin-fused schedule), sweep (plain FP32), bf16, tf32")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planned launch shapes (no tuner run)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving replay of the default run")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])

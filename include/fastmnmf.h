@@ -64,10 +64,33 @@ typedef enum {
 enum { FMNMF_UPDATE_W = 1, FMNMF_UPDATE_H = 2, FMNMF_UPDATE_G = 4, FMNMF_UPDATE_Q = 8,
        FMNMF_UPDATE_ALL = 15 };
 
-/* Arithmetic of the contractions.  FP32: every sum in float32 on CUDA cores, the M x M
- * IP solves and log|det Q_f|^2 in float64.  BF16 / TF32: the NMF and SCM contractions on
- * the tensor cores with float32 accumulation (same float64 IP). */
+/* Arithmetic of the contractions.  FP32: every sum in float32 on CUDA cores.  BF16 / TF32:
+ * the NMF and SCM contractions on the tensor cores with float32 accumulation.  In every form
+ * the M x M IP solves (Eqs. 19-20), their normalisation and log|det Q_f|^2 run in float-float
+ * arithmetic (an unevaluated sum of two float32 values, about 48 significand bits) on the
+ * FP32 pipes, not in float64: GB300's float64 rate is a small fraction of its float32 rate.
+ * Only the per-bin preparation of a newly set Q (its inverse and log-determinant) uses
+ * float64.  The per-sum operations and their error bounds are those of the error-free
+ * transformations (TwoSum, TwoProduct by FMA) and of one Newton step for the reciprocal and
+ * the reciprocal square root; the log-determinant adds log(s) of the row updates with log(hi)
+ * correct to float32 rounding plus the first-order lo/hi term. */
 enum { FMNMF_PREC_FP32 = 0, FMNMF_PREC_BF16 = 1, FMNMF_PREC_TF32 = 2 };
+
+/* Launch schedule of the FP32 form.
+ *  SWEEP: one tiled launch per block of the iteration (W, H, g~, V_fm, IP, x~): six launches.
+ *  FUSED: two launches per iteration.  Every block but the H update (Eq. 24, a sum over bins)
+ *         is independent per frequency bin, so one kernel runs, per bin, the g~ update, V_fm
+ *         and the IP update, the normalisation, x~, the bin's log-likelihood terms and the W
+ *         update of the next iteration; a second kernel runs the H update over tiles of
+ *         frames and refreshes lambda.  Needs N*K <= 256 and N*M <= 256.
+ *  AUTO:  FUSED when it applies, else SWEEP.  The mixed-precision forms ignore the field. */
+enum { FMNMF_SCHED_AUTO = 0, FMNMF_SCHED_SWEEP = 1, FMNMF_SCHED_FUSED = 2 };
+
+/* Source model (Sec. III-B).  NMF: lambda_ftn = sum_k w_nkf h_nkt (Eq. 9): FastMNMF (Sec.
+ * III-C-2).  FREE: the unconstrained source model, lambda_ftn estimated directly by the
+ * multiplicative rule of Eq. 22 (K is ignored): FastFCA (Sec. III-C-1) with the IP update of
+ * Q.  FREE runs in the FP32 form with the fused schedule only. */
+enum { FMNMF_SOURCE_NMF = 0, FMNMF_SOURCE_FREE = 1 };
 
 typedef struct {
   int precision;          /* FMNMF_PREC_*                                      (default FP32) */
@@ -75,6 +98,8 @@ typedef struct {
   int normalise;          /* 1: scale normalisation after each iteration       (default 1)    */
   void* stream;           /* cudaStream_t for all device work; NULL = a private stream        */
   size_t hbm_budget;      /* 0 = unlimited; else init fails with ENOMEM above it              */
+  int schedule;           /* FMNMF_SCHED_*                                     (default AUTO) */
+  int source_model;       /* FMNMF_SOURCE_*                                    (default NMF)  */
 } fmnmf_opts;
 
 /* Fills *opts with the defaults above. */
@@ -125,6 +150,13 @@ fmnmf_status fmnmf_restart(fmnmf_ctx* ctx);
  *     w_nkf scaled to match; w_nk /= sum_f w_nkf with h_nk scaled to match
  *   (these leave every y~ and the log-likelihood unchanged);
  *   log-likelihood of the new state (Eq. 17).
+ * With the unconstrained source model (FastFCA, Sec. III-C-1) the W and H updates are
+ * replaced by  lambda_ftn <- lambda_ftn * sqrt(num/den)  (Eq. 22, every point) and the nu
+ * normalisation scales lambda_ftn instead of w_nkf (update_mask bit W selects the lambda
+ * update, bit H is ignored).  With the fused schedule the mu normalisation is applied once
+ * at the end of each call, and of each run of at most 100 iterations within it (it commutes
+ * with every update, so the state is that of the per-iteration normalisation up to rounding;
+ * results therefore depend on how iterations are split into calls, by rounding only).
  * Asynchronous: enqueued on the context stream; device errors surface at the next
  * synchronising call.
  */
@@ -149,8 +181,18 @@ fmnmf_status fmnmf_loglik(fmnmf_ctx* ctx, double* ll);
  */
 fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device);
 
-/* Copies the state to host buffers (any may be NULL).  Synchronises. */
+/* Copies the state to host buffers (any may be NULL; W and H must be NULL for the
+ * unconstrained source model, whose lambda fmnmf_get_lambda returns).  Synchronises. */
 fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void* Q);
+
+/* Unconstrained source model (FastFCA) only.  get: copies lambda, float32 [N][F][T] (host),
+ * and, if not NULL, g~ and Q; synchronises.  set: sets lambda, g~ and Q (host; all three
+ * required, finite, lambda and g~ >= 0, Q_f non-singular), recomputes x~, y~ and the
+ * log-likelihood and clears the error word, as fmnmf_set_state does.  The initial state of
+ * fmnmf_init for this model: lambda[n][f][t] = 0.1 + u_{(nF + f)T + t} (the SplitMix64
+ * uniforms of fmnmf_init), g~ and Q as for the NMF model. */
+fmnmf_status fmnmf_get_lambda(fmnmf_ctx* ctx, float* lam, float* G, void* Q);
+fmnmf_status fmnmf_set_lambda(fmnmf_ctx* ctx, const float* lam, const float* G, const void* Q);
 
 /* Sets the state from host buffers (all four required, finite, W/H/G >= 0, Q_f
  * non-singular), recomputes x~, y~ and the log-likelihood and clears the error word. */
@@ -227,8 +269,9 @@ fmnmf_status fmnmf_set_tuning(fmnmf_ctx* ctx, const float* scales);
  *    step), and new arrivals are admitted between steps;
  *  - separates a request that has run its iterations (Eq. 3) into a host buffer, frees
  *    its device memory and marks it done.
- * A request's results equal those of a context running it alone (fmnmf_init,
- * fmnmf_iterate, fmnmf_separate with the same seed).  Latency = completion - submission.
+ * A request's results equal those of a context running it alone (fmnmf_init, fmnmf_iterate
+ * with iters_per_step iterations per call, fmnmf_separate, the same seed).  Latency =
+ * completion - submission.
  *  hbm_budget      device bytes for admitted requests (0 = 70 % of the free memory at
  *                  creation); a request larger than it is rejected with FMNMF_ENOMEM.
  *  max_active      resident requests (0 = 16); iters_per_step (0 = 10); precision FMNMF_PREC_*.
@@ -271,12 +314,15 @@ long long fmnmf_launch_count(const fmnmf_ctx* ctx);
  *                 the call is asynchronous.
  * The working memory is one static device array of 1 MiB that the library holds on every
  * device it is loaded on, until the process exits: the call rejects F > 16384 bins or
- * F*T > 117,407,744 TF bins with FMNMF_EINVAL (message via fmnmf_last_error(NULL)).  Every
- * call shares that array and it keeps the last call's contents (the call clears what must
- * start at zero), so calls that overlap on the GPU race: order them on one stream or with
- * events.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture begins on the device.
+ * F*T > 117,407,744 TF bins with FMNMF_EINVAL (message via fmnmf_last_error(NULL)), and so
+ * it does pointers of X, Q or ll not aligned to 8 bytes or of W, H, G not aligned to 4.
+ * Every call shares that array and it keeps the last call's contents (the call clears what
+ * must start at zero), so calls that overlap on the GPU race: order them on one stream or
+ * with events.  The first call in a CUDA context (for the primary context: the first call
+ * on a device) looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it for that context; make that first call before any stream capture
+ * begins on the device.  No status word is read back: a singular Q_f or a non-finite state
+ * shows up as -inf or NaN in *ll.
  */
 fmnmf_status fmnmf_loglik_noalloc(const void* X, const float* W, const float* H, const float* G,
                                   const void* Q, int F, int T, int M, int N, int K, double* ll,

@@ -10,12 +10,15 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "fastmnmf.h"
+#include "fm_fused.cuh"
 #include "fm_gemm.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
@@ -32,7 +35,7 @@ constexpr int kSmemMax = 220 * 1024;     // hard ceiling (227 KB per CTA on sm_1
 
 const char* kKindNames[KK_COUNT] = {"w_update", "h_update", "g_update", "scm", "xt_loglik",
                                     "prep_q", "wiener", "ip", "gemm_lambda", "gemm_w", "gemm_h",
-                                    "pr", "apply"};
+                                    "pr", "apply", "bin", "hgemm"};
 
 // One tensor-core GEMM of the mixed form, planned once per context.
 struct GemmPlan {
@@ -63,6 +66,13 @@ struct fmnmf_ctx {
   int n_pt_blocks = 0, n_mu_blocks = 0;
   size_t ipSmem = 0;  // the IP kernel's prefetch buffers (0: none)
   bool fusedPR = false;  // the kernel that forms x~ also forms P, R of the next W update
+  // fused FP32 schedule (k_hgemm + k_bin per iteration) and the unconstrained source model
+  bool fused = false, free_model = false;
+  int hgS = 1, hgSpan = 32;        // H GEMM: bin splits and bins per split
+  int hgBaseS = 1;                 // the planned split count (the tuner scales it)
+  size_t binSm = 0;                // k_bin's dynamic shared memory
+  unsigned ctrHG = 0;              // first arrival counter of the H GEMM tiles
+  float* lam0 = nullptr;           // restart copy of lambda (unconstrained model)
   unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
   // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
   float* W0 = nullptr;
@@ -146,12 +156,25 @@ int occupancy(int maxm, KernelKind k, size_t smem) {
   }
 }
 
+// The dynamic shared-memory limit is a property of each kernel function (per device), shared
+// by every context: it is only ever raised, so that a context that needs less never lowers it
+// under another's launches.
 cudaError_t configure(int maxm, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> set_to;  // (device, bucket) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  int& cur = set_to[{dev, maxm}];
+  if (bytes <= cur) return cudaSuccess;
   switch (maxm) {
-    case 2: return configure_m2(bytes);
-    case 4: return configure_m4(bytes);
-    default: return configure_m8(bytes);
+    case 2: e = configure_m2(bytes); break;
+    case 4: e = configure_m4(bytes); break;
+    default: e = configure_m8(bytes); break;
   }
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 // Tiling of a sweep over an own extent SO (tiles of kOT) and an inner extent SI split
@@ -216,14 +239,18 @@ size_t sep_smem_bytes(int N, int K, int M, int maxm, int ic, bool lam_mem = fals
 // (see enqueue_tail).
 constexpr int kFuseXtFrames = 1024;
 
+void apply_fused_shape(fmnmf_ctx* c);
+
 fmnmf_status plan(fmnmf_ctx* ctx) {
   const int F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K, mx = ctx->maxm;
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int caps[4];
-  // the mixed form reads lambda in the g~ and y~ sweeps: no factor tiles there
-  auto lm = [&](int mode) { return ctx->mixed && (mode == MODE_G || mode == MODE_Y); };
+  // the mixed form (and the unconstrained source model) reads lambda in the g~ and y~
+  // sweeps: no factor tiles there
+  const bool lam_ctx = ctx->mixed || ctx->free_model;
+  auto lm = [&](int mode) { return lam_ctx && (mode == MODE_G || mode == MODE_Y); };
   for (int mode = 0; mode < 4; ++mode) {
     int cap = ic_cap_for(mode, N, K, M, mx, kSmemTarget, lm(mode));
     if (cap == 0) cap = ic_cap_for(mode, N, K, M, mx, kSmemMax, lm(mode));
@@ -246,8 +273,8 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   ctx->smH = smem_bytes(MODE_H, N, K, M, mx, ctx->gH.IC);
   ctx->smG = smem_bytes(MODE_G, N, K, M, mx, ctx->gG.IC, lm(MODE_G));
   ctx->smY = smem_bytes(MODE_Y, N, K, M, mx, ctx->gY.IC, lm(MODE_Y));
-  // the Wiener filter reads the materialised lambda in the mixed form
-  const bool sep_lm = ctx->mixed;
+  // the Wiener filter reads the materialised lambda in the mixed form and the free model
+  const bool sep_lm = lam_ctx;
   int sep_cap = 0;
   for (int ic = 256; ic >= 4; ic -= 4)
     if (sep_smem_bytes(N, K, M, mx, ic, sep_lm) <= (size_t)kSmemTarget) { sep_cap = ic; break; }
@@ -338,18 +365,56 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     // iteration (the IP kernel for short mixtures, else k_xt_ll) forms P, R
     ctx->fusedPR = ctx->mixed && (ctx->opts.update_mask & FMNMF_UPDATE_W);
   }
+  {
+    // fused schedule (FP32): per-bin kernel + H kernel, when its pair limits and shared
+    // memory allow; the unconstrained source model runs only there
+    const int Kf = ctx->free_model ? 1 : K;
+    const size_t bsm = (size_t)bin_smem(N, Kf, mx).total * 4;
+    bool ok = !ctx->mixed && N * Kf <= kFuMaxPairs && N * M <= kFuMaxPairs && bsm <= (size_t)kSmemMax;
+    // H GEMM: bin splits for about four CTAs per SM, at least 32 bins (one chunk) a split
+    const int hg_tiles = ((T + kHgTT - 1) / kHgTT) * ((K + kHgKT - 1) / kHgKT) * N;
+    int hgS = std::max(1, std::min((F + kHgFC - 1) / kHgFC, (4 * sms + hg_tiles - 1) / hg_tiles));
+    const int sched = ctx->opts.schedule;
+    if (ctx->free_model && !ok)
+      return set_err(ctx, FMNMF_EINVAL, "the unconstrained source model needs the fused FP32 schedule (N*M <= %d)",
+                     kFuMaxPairs);
+    if (sched == FMNMF_SCHED_FUSED && !ok)
+      return set_err(ctx, FMNMF_EINVAL, "fused schedule not available for this shape/precision (FP32, N*K and N*M <= %d)",
+                     kFuMaxPairs);
+    ctx->fused = ok && (ctx->free_model || sched != FMNMF_SCHED_SWEEP);
+    if (ctx->fused) {
+      ctx->hgBaseS = hgS;
+      ctx->binSm = bsm;
+      mx_cap_smem = std::max(mx_cap_smem, ctx->binSm);
+      CK(configure(mx, (int)mx_cap_smem));
+    }
+  }
   for (int mode = 0; mode < 4; ++mode) ctx->caps[mode] = caps[mode];
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
                               ctx->mixed ? ctx->gpW.g.ksplit : 1, ctx->mixed ? ctx->gpH.g.ksplit : 1};
   for (int t = 0; t < TU_COUNT; ++t) { ctx->baseS[t] = base[t]; ctx->tscale[t] = 1.f; }
+  // fused schedule: tuning entry 1 (the H sweep's, unused there) scales the H GEMM's splits
+  if (ctx->fused) ctx->baseS[TU_H] = ctx->hgBaseS;
+  apply_fused_shape(ctx);
   return FMNMF_OK;
+}
+
+// The fused schedule's H GEMM: its bin splits (planned count times the tuner's scale) and
+// bins per split (whole chunks of 32).
+void apply_fused_shape(fmnmf_ctx* c) {
+  if (!c->fused) return;
+  const int S0 = std::max(1, (int)std::lround(c->baseS[TU_H] * c->tscale[TU_H]));
+  const int nch = (c->F + kHgFC - 1) / kHgFC;
+  const int per = (nch + std::min(S0, nch) - 1) / std::min(S0, nch);
+  c->hgSpan = per * kHgFC;
+  c->hgS = (c->F + c->hgSpan - 1) / c->hgSpan;
 }
 
 // Re-derives the tunable launch shapes from the planned split counts and the tuner's scales.
 void apply_shapes(fmnmf_ctx* c) {
   const int F = c->F, T = c->T, M = c->M, N = c->N, K = c->K, mx = c->maxm;
   auto S_of = [&](int t, int smin) { return std::max(smin, (int)std::lround(c->baseS[t] * c->tscale[t])); };
-  auto lm = [&](int mode) { return c->mixed && (mode == MODE_G || mode == MODE_Y); };
+  auto lm = [&](int mode) { return (c->mixed || c->free_model) && (mode == MODE_G || mode == MODE_Y); };
   c->gW = make_geom_S(F, T, c->caps[MODE_W], S_of(TU_W, 1));
   c->gH = make_geom_S(T, F, c->caps[MODE_H], S_of(TU_H, 1));
   c->gG = make_geom_S(F, T, c->caps[MODE_G], S_of(TU_G, 1));
@@ -358,6 +423,7 @@ void apply_shapes(fmnmf_ctx* c) {
   c->smH = smem_bytes(MODE_H, N, K, M, mx, c->gH.IC);
   c->smG = smem_bytes(MODE_G, N, K, M, mx, c->gG.IC, lm(MODE_G));
   c->smY = smem_bytes(MODE_Y, N, K, M, mx, c->gY.IC, lm(MODE_Y));
+  apply_fused_shape(c);
   if (!c->mixed) return;
   auto frames = [&](int S, int kc, int& span, int& outS) {
     const int nst = (T + kc - 1) / kc;
@@ -392,13 +458,17 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
   part = std::max(part, (size_t)ctx->gY.S * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   if (ctx->mixed) part = std::max(part, (size_t)ctx->scmS * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   if (ctx->mixed && ctx->gtcNP > 0) part = std::max(part, (size_t)ctx->gtcS * tile_part_floats(MODE_G, F, T, M, N, K, mx));
+  // the H GEMM's split partials, sized for the planned split count (the tuner only lowers it)
+  if (ctx->fused && !ctx->free_model) part = std::max(part, (size_t)ctx->hgBaseS * 2 * N * K * T);
+  const unsigned hg_tiles = ctx->fused ? (unsigned)(((T + kHgTT - 1) / kHgTT) * ((K + kHgKT - 1) / kHgKT) * N) : 0u;
   const unsigned nctr = ctx->gW.n_own_tiles + ctx->gH.n_own_tiles + ctx->gG.n_own_tiles +
-                        ctx->gY.n_own_tiles + 1;
+                        ctx->gY.n_own_tiles + 1 + hg_tiles;
   ctx->ctrW = 0;
   ctx->ctrH = ctx->ctrW + ctx->gW.n_own_tiles;
   ctx->ctrG = ctx->ctrH + ctx->gH.n_own_tiles;
   ctx->ctrY = ctx->ctrG + ctx->gG.n_own_tiles;
   ctx->ctrLL = ctx->ctrY + ctx->gY.n_own_tiles;
+  ctx->ctrHG = ctx->ctrLL + 1;
   struct Slot { void** dst; size_t bytes; };
   Prob& p = ctx->p;
   void* X = nullptr;
@@ -425,6 +495,11 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
       {(void**)&ctx->G0, N * F * M * 4},
       {(void**)&ctx->Q0, F * M * M * sizeof(float4)},
   };
+  if (ctx->fused) {
+    slots.push_back({(void**)&ctx->lam, N * F * T * 4});
+    if (!ctx->free_model) slots.push_back({(void**)&ctx->PR, 2 * N * F * T * 4});
+    else slots.push_back({(void**)&ctx->lam0, N * F * T * 4});
+  }
   if (ctx->mixed) {
     const size_t cg = std::max((size_t)ctx->gpW.grid.z * ctx->gpW.g.Mr * ctx->gpW.g.Nc,
                                (size_t)ctx->gpH.grid.z * ctx->gpH.g.Mr * ctx->gpH.g.Nc);
@@ -457,16 +532,19 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
     w.B = p.H; w.sBb = (long long)K * T; w.sBj = T; w.sBk = 1; w.bmodB = (int)N;
     w.C = ctx->Cg; w.sCs = 2LL * N * F * K; w.sCb = (long long)F * K; w.sCi = K; w.sCj = 1;
     w.status = p.status;
+    w.wait_limit = p.wait_limit;
     GemmArgs& h = ctx->gpH.g;   // [P;R]_n^T (t x f) . W_n (k x f)^T
     h.A = ctx->PR; h.sAb = FT; h.sAi = 1; h.sAk = T;
     h.B = p.W; h.sBb = (long long)K * F; h.sBj = F; h.sBk = 1; h.bmodB = (int)N;
     h.C = ctx->Cg; h.sCs = 2LL * N * T * K; h.sCb = (long long)T * K; h.sCi = K; h.sCj = 1;
     h.status = p.status;
+    h.wait_limit = p.wait_limit;
     GemmArgs& l = ctx->gpL.g;   // W_n^T (f x k) . H_n^T (t x k)^T = lambda_n (f x t)
     l.A = p.W; l.sAb = (long long)K * F; l.sAi = 1; l.sAk = F;
     l.B = p.H; l.sBb = (long long)K * T; l.sBj = 1; l.sBk = T; l.bmodB = (int)N;
     l.C = ctx->lam; l.sCs = 0; l.sCb = FT; l.sCi = T; l.sCj = 1;
     l.status = p.status;
+    l.wait_limit = p.wait_limit;
     Prob q = p;
     q.lam = ctx->lam;
     if (ctx->gtcNP > 0) ctx->gtcTma = gtc_tensor_maps(ctx->maxm, q, &ctx->gtcTmX, &ctx->gtcTmL);
@@ -649,8 +727,71 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
   return enqueue_tail(c, rec, yflags, ipS, norm);
 }
 
+LaunchArgs hgemm_args(fmnmf_ctx* c) {
+  LaunchArgs a;
+  a.p = c->p; a.st = c->st; a.pr = c->PR; a.ctr = c->ctrHG;
+  a.g.S = c->hgS; a.g.span = c->hgSpan;
+  a.grid = dim3((c->T + kHgTT - 1) / kHgTT, (c->K + kHgKT - 1) / kHgKT, c->N * c->hgS);
+  return a;
+}
+
+// A run of n iterations in the fused FP32 schedule (fm_fused.cuh):
+//   k_bin (prologue)               lambda of the bin, the first W update (Eq. 23) and P, R of
+//                                  the first H update, when W or H is updated
+//   n times: k_hgemm, k_bin        the H update (Eq. 24); per bin lambda, the g~ update,
+//                                  V_fm + IP, normalisation, x~, the terms of Eq. 17 and, but
+//                                  in the last iteration, the next W update and the next H
+//                                  update's P, R
+//   k_xt_ll (mu + log-likelihood)  the mu normalisation and the sum of Eq. 17
+// With the unconstrained source model k_bin starts with the lambda update of Eq. 22 and there
+// is no H update.
+cudaError_t enqueue_fused_chunk(fmnmf_ctx* c, Recorder& rec, int n) {
+  const unsigned mask = c->opts.update_mask;
+  const bool norm = c->opts.normalise != 0;
+  const bool fm = c->free_model;
+  const bool upW = !fm && (mask & FMNMF_UPDATE_W), upH = !fm && (mask & FMNMF_UPDATE_H);
+  cudaError_t e;
+  auto bin = [&](int flags) {
+    LaunchArgs a;
+    a.p = c->p; a.st = c->st; a.grid = dim3(c->F); a.smem = c->binSm; a.flags = flags;
+    a.lam = c->lam; a.pr = c->PR;
+    return rec.run(KK_BIN, a);
+  };
+  const int lam0 = fm ? 0 : FU_LAM0;
+  const int base = ((mask & FMNMF_UPDATE_G) ? FU_G : 0) | ((mask & FMNMF_UPDATE_Q) ? FU_Q : 0) |
+                   (norm ? FU_NORM : 0) | (fm ? FU_FREE : 0) | ((fm && (mask & FMNMF_UPDATE_W)) ? FU_LAM : 0) | lam0;
+  if ((upW || upH) && (e = bin(FU_WONLY | lam0 | (upW ? FU_W : 0) | (upH ? FU_PH : 0))) != cudaSuccess) return e;
+  for (int i = 0; i < n; ++i) {
+    if (upH && (e = rec.run(KK_HGEMM, hgemm_args(c))) != cudaSuccess) return e;
+    const bool last = i == n - 1;
+    int fl = base;
+    if (upW && !last) fl |= FU_W;
+    if (upH && !last) fl |= FU_PH;
+    // lambda * nu in memory: the unconstrained model's state, or the next H update's lambda
+    // when W is not updated
+    if (fm || (upH && !upW && !last)) fl |= FU_LAMWB;
+    if ((e = bin(fl)) != cudaSuccess) return e;
+  }
+  LaunchArgs x;
+  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+  x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = (norm && !fm) ? 1 : 0; x.ll_bins = 1;
+  x.grid = dim3((x.do_mu ? c->n_mu_blocks : 0) + 1);
+  return rec.run(KK_XT, x);
+}
+
+// n iterations of a context, enqueued on its stream (under capture).
+cudaError_t enqueue_chunk(fmnmf_ctx* c, Recorder& rec, int n) {
+  if (c->fused) return enqueue_fused_chunk(c, rec, n);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_iteration(c, rec);
+  return e;
+}
+
+void sync_wait_limit(fmnmf_ctx* ctx);
+
 // x~, y~, log-det and log-likelihood of the state currently on the device.
 fmnmf_status refresh_state(fmnmf_ctx* ctx) {
+  sync_wait_limit(ctx);
   LaunchArgs a;
   a.p = ctx->p; a.st = ctx->st;
   a.grid = dim3((ctx->F + 7) / 8);
@@ -659,6 +800,11 @@ fmnmf_status refresh_state(fmnmf_ctx* ctx) {
     // lambda on the tensor cores, then y~ from it (the launch geometry of the mixed form)
     ctx->launches++;
     CK(launch_gemm(ctx->gpL.g, ctx->tf32, ctx->gpL.nt, ctx->gpL.grid, ctx->st));
+    LaunchArgs y = tile_args(ctx, ctx->gY, ctx->smY, FLAG_LAM_MEM, ctx->ctrY);
+    y.p.lam = ctx->lam;
+    CK(launch(ctx, KK_Y, y));
+  } else if (ctx->free_model) {
+    // y~ from the lambda state
     LaunchArgs y = tile_args(ctx, ctx->gY, ctx->smY, FLAG_LAM_MEM, ctx->ctrY);
     y.p.lam = ctx->lam;
     CK(launch(ctx, KK_Y, y));
@@ -688,6 +834,9 @@ fmnmf_status snapshot(fmnmf_ctx* ctx, bool restore) {
   for (auto& e : c)
     CK(cudaMemcpyAsync(restore ? e.live : e.snap, restore ? e.snap : e.live, e.bytes,
                        cudaMemcpyDeviceToDevice, ctx->st));
+  if (ctx->free_model)
+    CK(cudaMemcpyAsync(restore ? ctx->lam : ctx->lam0, restore ? ctx->lam0 : ctx->lam, N * F * T * 4,
+                       cudaMemcpyDeviceToDevice, ctx->st));
   return FMNMF_OK;
 }
 
@@ -695,9 +844,11 @@ fmnmf_status check_status(fmnmf_ctx* ctx) {
   unsigned st = 0;
   CK(cudaMemcpyAsync(&st, ctx->p.status, 4, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  // a wait that ran out leaves results undefined downstream (which may then look singular or
+  // non-finite): it is the cause to report
+  if (st & ST_TIMEOUT) return set_err(ctx, FMNMF_ETIMEOUT, "device wait timed out (status 0x%x)", st);
   if (st & ST_SINGULAR) return set_err(ctx, FMNMF_ESINGULAR, "singular IP system or diagonaliser (device status 0x%x)", st);
   if (st & ST_NONFINITE) return set_err(ctx, FMNMF_ENONFINITE, "non-finite value produced on the device (status 0x%x)", st);
-  if (st & ST_TIMEOUT) return set_err(ctx, FMNMF_ETIMEOUT, "device wait timed out (status 0x%x)", st);
   return FMNMF_OK;
 }
 
@@ -762,10 +913,39 @@ fmnmf_status seed_state(fmnmf_ctx* ctx, uint64_t seed) {
   CK(cudaMemcpyAsync(ctx->p.H, H.data(), nh * 4, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->p.G, G.data(), G.size() * 4, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->p.Qx, Q.data(), Q.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  std::vector<float> L;
+  if (ctx->free_model) {
+    // lambda[n][f][t] = 0.1 + u_{(nF + f)T + t}
+    const size_t nl = (size_t)N * F * T;
+    L.resize(nl);
+    for (size_t i = 0; i < nl; ++i) L[i] = (float)(0.1 + (double)(sm64(seed, i) >> 11) * 0x1.0p-53);
+    CK(cudaMemcpyAsync(ctx->lam, L.data(), nl * 4, cudaMemcpyHostToDevice, ctx->st));
+  }
   CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
   // the host vectors die at return: wait for the copies
   CK(cudaStreamSynchronize(ctx->st));
   return FMNMF_OK;
+}
+
+// Failure-detection tests only: FMNMF_TEST_WAIT_LIMIT (a count of tries) replaces the bound
+// of the tensor-core kernels' consumer waits, and one of their waits then goes to an mbarrier
+// nothing arrives at, so that their timeout path runs (the CTA leaves its loop, drains the
+// copies and MMAs it issued with the full bound, reports ST_TIMEOUT and frees its TMEM).
+// Read at context creation and at every fmnmf_iterate; unset (the normal case) it is 0.
+unsigned test_wait_limit() {
+  const char* wl = std::getenv("FMNMF_TEST_WAIT_LIMIT");
+  return wl ? (unsigned)std::strtoul(wl, nullptr, 10) : 0u;
+}
+
+void clear_graphs(fmnmf_ctx* ctx);
+
+// Picks up a changed test wait limit before a call launches kernels (graphs recaptured).
+void sync_wait_limit(fmnmf_ctx* ctx) {
+  const unsigned wl = test_wait_limit();
+  if (wl == ctx->p.wait_limit) return;
+  clear_graphs(ctx);
+  ctx->p.wait_limit = wl;
+  ctx->gpW.g.wait_limit = ctx->gpH.g.wait_limit = ctx->gpL.g.wait_limit = wl;
 }
 
 // Drops the captured graphs (their launch shapes changed).
@@ -793,7 +973,7 @@ fmnmf_status save_state(fmnmf_ctx* ctx, SavedState& sv) {
                {p.Qx, F * M * M * sizeof(float4)}, {p.Qix, F * M * M * sizeof(float4)},
                {p.Qf, F * M * M * sizeof(float2)}, {p.Qinv, F * M * M * sizeof(float2)},
                {p.logdet, F * 8}, {p.phi, F * 4}, {p.xt, F * T * M * 4}, {p.yt, F * T * M * 4}, {p.ll, 8}};
-  if (ctx->mixed) sv.arrays.push_back({ctx->lam, N * F * T * 4});
+  if (ctx->mixed || ctx->fused) sv.arrays.push_back({ctx->lam, N * F * T * 4});
   if (ctx->fusedPR) sv.arrays.push_back({ctx->PR, 2 * N * F * T * 4});  // P, R of the next W update
   size_t tot = 0;
   for (auto& a : sv.arrays) { sv.off.push_back(tot); tot += (a.second + 255) & ~(size_t)255; }
@@ -847,6 +1027,8 @@ fmnmf_status fmnmf_default_opts(fmnmf_opts* opts) {
   opts->normalise = 1;
   opts->stream = nullptr;
   opts->hbm_budget = 0;
+  opts->schedule = FMNMF_SCHED_AUTO;
+  opts->source_model = FMNMF_SOURCE_NMF;
   return FMNMF_OK;
 }
 
@@ -860,11 +1042,19 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
   if (!X) return set_err(nullptr, FMNMF_EINVAL, "X is NULL");
   if (opts && (opts->precision < FMNMF_PREC_FP32 || opts->precision > FMNMF_PREC_TF32))
     return set_err(nullptr, FMNMF_EINVAL, "unknown precision %d", opts->precision);
+  if (opts && (opts->schedule < FMNMF_SCHED_AUTO || opts->schedule > FMNMF_SCHED_FUSED))
+    return set_err(nullptr, FMNMF_EINVAL, "unknown schedule %d", opts->schedule);
+  if (opts && (opts->source_model < FMNMF_SOURCE_NMF || opts->source_model > FMNMF_SOURCE_FREE))
+    return set_err(nullptr, FMNMF_EINVAL, "unknown source model %d", opts->source_model);
+  if (opts && opts->source_model == FMNMF_SOURCE_FREE && opts->precision != FMNMF_PREC_FP32)
+    return set_err(nullptr, FMNMF_EINVAL, "the unconstrained source model runs in the FP32 form only");
   fmnmf_ctx* ctx = new fmnmf_ctx();
   ctx->F = F; ctx->T = T; ctx->M = M; ctx->N = N; ctx->K = K; ctx->maxm = bucket(M);
   if (opts) ctx->opts = *opts; else fmnmf_default_opts(&ctx->opts);
   ctx->mixed = ctx->opts.precision != FMNMF_PREC_FP32;
   ctx->tf32 = ctx->opts.precision == FMNMF_PREC_TF32;
+  ctx->free_model = ctx->opts.source_model == FMNMF_SOURCE_FREE;
+  ctx->p.wait_limit = test_wait_limit();
   if (ctx->opts.update_mask & ~(unsigned)FMNMF_UPDATE_ALL) {
     const unsigned bad = ctx->opts.update_mask;
     delete ctx;
@@ -898,6 +1088,7 @@ fmnmf_status fmnmf_footprint(int F, int T, int M, int N, int K, const fmnmf_opts
   if (opts) tmp.opts = *opts; else fmnmf_default_opts(&tmp.opts);
   tmp.mixed = tmp.opts.precision != FMNMF_PREC_FP32;
   tmp.tf32 = tmp.opts.precision == FMNMF_PREC_TF32;
+  tmp.free_model = tmp.opts.source_model == FMNMF_SOURCE_FREE;
   fmnmf_status s = plan(&tmp);
   if (s == FMNMF_OK) s = allocate(&tmp, true);
   if (s != FMNMF_OK) { g_thread_err = tmp.err; return s; }
@@ -927,6 +1118,7 @@ fmnmf_status fmnmf_restart(fmnmf_ctx* ctx) {
 fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
   if (n_iter < 0) return set_err(ctx, FMNMF_EINVAL, "n_iter < 0");
+  sync_wait_limit(ctx);
   while (n_iter > 0) {
     const int chunk = std::min(n_iter, kMaxChunk);
     auto key = std::make_pair(chunk, ctx->timing);
@@ -937,8 +1129,7 @@ fmnmf_status fmnmf_iterate(fmnmf_ctx* ctx, int n_iter) {
       CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
       Recorder rec{ctx, ctx->timing ? &ge.ev : nullptr};
       const long long before = ctx->launches;
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = enqueue_iteration(ctx, rec);
+      cudaError_t e = enqueue_chunk(ctx, rec, chunk);
       ge.launches = (int)(ctx->launches - before);
       ctx->launches = before;
       cudaError_t e2 = cudaStreamEndCapture(ctx->st, &g);
@@ -999,6 +1190,7 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
     dst = tmp;
   }
   // Q_f^-1 is kept current by the IP update (and by the preparation of a set state)
+  sync_wait_limit(ctx);
   Recorder rec{ctx, ctx->timing ? &ctx->pending : nullptr};
   LaunchArgs a;
   a.p = ctx->p; a.g = ctx->gS; a.smem = ctx->smS; a.st = ctx->st; a.out = dst;
@@ -1014,6 +1206,8 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
       return set_err(ctx, FMNMF_ECUDA, "lambda GEMM launch: %s", cudaGetErrorString(el));
     }
     a.p.lam = ctx->lam;
+  } else if (ctx->free_model) {
+    a.p.lam = ctx->lam;  // the lambda state (nu already applied)
   }
   a.grid = dim3(ctx->gS.n_own_tiles, ctx->gS.S);
   cudaError_t e = rec.run(KK_SEP, a);
@@ -1031,6 +1225,8 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
 
 fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void* Q) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (ctx->free_model && (W || H))
+    return set_err(ctx, FMNMF_EINVAL, "the unconstrained source model has no W, H (use fmnmf_get_lambda)");
   CK(cudaStreamSynchronize(ctx->st));
   const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
   if (W) CK(cudaMemcpyAsync(W, ctx->p.W, N * K * F * 4, cudaMemcpyDeviceToHost, ctx->st));
@@ -1040,8 +1236,55 @@ fmnmf_status fmnmf_get_state(fmnmf_ctx* ctx, float* W, float* H, float* G, void*
   return check_status(ctx);
 }
 
+// Validates g~ and Q from the host and converts Q to the float-float storage form.
+static fmnmf_status check_gq(fmnmf_ctx* ctx, const float* G, const void* Q, std::vector<float4>& Qx) {
+  const size_t F = ctx->F, M = ctx->M, N = ctx->N;
+  for (size_t i = 0; i < N * F * M; ++i)
+    if (!(G[i] >= 0.f) || !std::isfinite(G[i])) return set_err(ctx, FMNMF_EINVAL, "g~ must be finite and nonnegative");
+  const float* q = (const float*)Q;
+  Qx.resize(F * M * M);
+  for (size_t i = 0; i < F * M * M; ++i) {
+    if (!std::isfinite(q[2 * i]) || !std::isfinite(q[2 * i + 1])) return set_err(ctx, FMNMF_EINVAL, "Q must be finite");
+    Qx[i] = make_float4(q[2 * i], 0.f, q[2 * i + 1], 0.f);
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_get_lambda(fmnmf_ctx* ctx, float* lam, float* G, void* Q) {
+  if (!ctx || !lam) return set_err(ctx, FMNMF_EINVAL, "get_lambda: NULL argument");
+  if (!ctx->free_model) return set_err(ctx, FMNMF_EINVAL, "get_lambda: the context has the NMF source model");
+  CK(cudaStreamSynchronize(ctx->st));
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N;
+  CK(cudaMemcpyAsync(lam, ctx->lam, N * F * T * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (G) CK(cudaMemcpyAsync(G, ctx->p.G, N * F * M * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (Q) CK(cudaMemcpyAsync(Q, ctx->p.Qf, F * M * M * sizeof(float2), cudaMemcpyDeviceToHost, ctx->st));
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_set_lambda(fmnmf_ctx* ctx, const float* lam, const float* G, const void* Q) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (!lam || !G || !Q) return set_err(ctx, FMNMF_EINVAL, "set_lambda needs lambda, g~ and Q");
+  if (!ctx->free_model) return set_err(ctx, FMNMF_EINVAL, "set_lambda: the context has the NMF source model");
+  const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N;
+  for (size_t i = 0; i < N * F * T; ++i)
+    if (!(lam[i] >= 0.f) || !std::isfinite(lam[i])) return set_err(ctx, FMNMF_EINVAL, "lambda must be finite and nonnegative");
+  std::vector<float4> Qx;
+  fmnmf_status s = check_gq(ctx, G, Q, Qx);
+  if (s != FMNMF_OK) return s;
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpyAsync(ctx->lam, lam, N * F * T * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.G, G, N * F * M * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.Qx, Qx.data(), Qx.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // the host vector Qx goes out of scope
+  if ((s = snapshot(ctx, false)) != FMNMF_OK) return s;
+  if ((s = refresh_state(ctx)) != FMNMF_OK) return s;
+  return check_status(ctx);
+}
+
 fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, const float* G, const void* Q) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  if (ctx->free_model) return set_err(ctx, FMNMF_EINVAL, "the unconstrained source model has no W, H (use fmnmf_set_lambda)");
   if (!W || !H || !G || !Q) return set_err(ctx, FMNMF_EINVAL, "set_state needs W, H, G and Q");
   const size_t F = ctx->F, T = ctx->T, M = ctx->M, N = ctx->N, K = ctx->K;
   auto nonneg = [](const float* a, size_t n) {
@@ -1142,8 +1385,11 @@ fmnmf_status fmnmf_autotune(fmnmf_ctx* ctx, int n_iter, double* speedup) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int tun[4] = {ctx->mixed ? TU_SCM : TU_W, ctx->mixed ? TU_GTC : TU_H, ctx->mixed ? TU_GEMM_W : TU_G,
-                      ctx->mixed ? TU_GEMM_H : TU_Y};
+  // the fused schedule's one tunable launch shape is the H kernel's frame tile (entry TU_H)
+  std::vector<int> tun;
+  if (ctx->fused) tun = {TU_H};
+  else if (ctx->mixed) tun = {TU_SCM, TU_GTC, TU_GEMM_W, TU_GEMM_H};
+  else tun = {TU_W, TU_H, TU_G, TU_Y};
   const double t0 = tune_trial(ctx, sv, n_iter, e0, e1);
   double best = t0;
   // coordinate descent over the split scales, two passes
@@ -1229,7 +1475,7 @@ fmnmf_status fmnmf_batch_iterate(fmnmf_batch* b, int n_iter) {
         if ((e = cudaStreamWaitEvent(c->st, b->events[n], 0)) != cudaSuccess) break;
         Recorder rec{c, nullptr};
         const long long before = c->launches;
-        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = enqueue_iteration(c, rec);
+        e = enqueue_chunk(c, rec, chunk);
         launches += c->launches - before;
         c->launches = before;
         if (e == cudaSuccess) e = cudaEventRecord(b->events[i], c->st);

@@ -742,8 +742,9 @@ __device__ __forceinline__ void pr_point(const float (&x)[MAXM], const float (&y
 //   A[k][k] <- 1/p,  A[k][j] <- A[k][j]/p,  A[i][k] <- -A[i][k]/p,
 //   A[i][j] <- A[i][j] - A[i][k] (A[k][j]/p)          (p = A[k][k], no pivoting).
 // Returns false (on every lane) when a pivot is not positive and finite.
+// vlo (may be null): low parts of the sums, when they were accumulated in float-float.
 template <int MAXM>
-__device__ __forceinline__ bool gj_inverse(const float* v, float4* A, int M, int lane) {
+__device__ __forceinline__ bool gj_inverse(const float* v, float4* A, int M, int lane, const float* vlo = nullptr) {
   constexpr int MM = MAXM * MAXM;
   constexpr int R = MM > 32 ? MM / 32 : 1;
   constexpr int IG = 32 / MAXM;
@@ -754,13 +755,19 @@ __device__ __forceinline__ bool gj_inverse(const float* v, float4* A, int M, int
   for (int r = 0; r < R; ++r) {
     const int i = i0 + r * IG;
     own[r] = lane < MM && i < M && j < M;
-    float re = 0.f, im = 0.f;
+    float re = 0.f, im = 0.f, rl = 0.f, il = 0.f;
     if (own[r]) {
-      if (i == j) re = v[i * MAXM + i];
-      else if (i < j) { re = v[i * MAXM + j]; im = v[j * MAXM + i]; }
-      else { re = v[j * MAXM + i]; im = -v[i * MAXM + j]; }
+      const int ia = (i <= j) ? i * MAXM + j : j * MAXM + i;   // Re V_ij slot
+      const int ib = (i <= j) ? j * MAXM + i : i * MAXM + j;   // Im slot (sign below)
+      const float sg = (i <= j) ? 1.f : -1.f;
+      re = v[ia];
+      im = (i == j) ? 0.f : sg * v[ib];
+      if (vlo) {
+        rl = vlo[ia];
+        il = (i == j) ? 0.f : sg * vlo[ib];
+      }
     }
-    a[r] = cdf_make(re, im);
+    a[r] = cdf{df{re, rl}, df{im, il}};
   }
   bool ok = true;
   for (int k = 0; k < M; ++k) {

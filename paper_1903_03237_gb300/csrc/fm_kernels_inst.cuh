@@ -1,4 +1,5 @@
 // Instantiates the kernels of one channel bucket (FM_MAXM) and its launch entry points.
+#include "fm_fused.cuh"
 #include "fm_kernels.cuh"
 #include "fm_launch.h"
 
@@ -22,6 +23,8 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
     case KK_IP:
       k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
       break;
+    case KK_BIN: k_bin<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.lam, a.pr, a.flags); break;
+    case KK_HGEMM: k_hgemm<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.pr, a.g.S, a.g.span, a.ctr); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -41,6 +44,14 @@ int FM_CAT(occupancy_m, FM_MAXM)(KernelKind k, size_t smem) {
   return n > 0 ? n : 1;
 }
 
+int FM_CAT(occupancy_fused_m, FM_MAXM)(KernelKind k, size_t smem) {
+  constexpr int MX = FM_MAXM;
+  int n = 0;
+  if (k == KK_BIN) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bin<MX>, kThreads, smem);
+  else if (k == KK_HGEMM) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hgemm<MX>, kThreads, 0);
+  return n;
+}
+
 cudaError_t FM_CAT(configure_m, FM_MAXM)(int bytes) {
   constexpr int MX = FM_MAXM;
   cudaError_t e = cudaSuccess;
@@ -50,6 +61,7 @@ cudaError_t FM_CAT(configure_m, FM_MAXM)(int bytes) {
   if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_G>, A, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_tile<MX, MODE_Y>, A, bytes)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_separate<MX>, A, bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_bin<MX>, A, bytes)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ip<MX>, A, kIpPrefetchMax);
 }
 

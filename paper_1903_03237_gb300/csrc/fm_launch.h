@@ -21,7 +21,9 @@ enum KernelKind {
   KK_GH = 10,    // mixed form: H numerator / denominator GEMM
   KK_PR = 11,    // mixed form: P, R per TF bin
   KK_APPLY = 12, // mixed form: multiplicative update from the split GEMM sums
-  KK_COUNT = 13
+  KK_BIN = 13,   // fused schedule: per-bin g~ / V_fm + IP / normalisation / x~ / LL / next W update
+  KK_HGEMM = 14, // fused schedule: H update (split GEMM over bins, last-CTA update)
+  KK_COUNT = 15
 };
 
 struct LaunchArgs {
@@ -41,6 +43,7 @@ struct LaunchArgs {
   float* pr = nullptr;    // k_ip, k_xt_ll: also form P, R of the next W update here
   int ll_tail = 1;        // k_ip: the last CTA adds up the log-likelihood (0: a later kernel does)
   float2* out = nullptr;  // k_separate
+  float* lam = nullptr;   // k_bin: lambda [N][F][T]
 };
 
 cudaError_t launch_m2(KernelKind k, const LaunchArgs& a);
@@ -50,6 +53,10 @@ cudaError_t launch_m8(KernelKind k, const LaunchArgs& a);
 int occupancy_m2(KernelKind k, size_t smem);
 int occupancy_m4(KernelKind k, size_t smem);
 int occupancy_m8(KernelKind k, size_t smem);
+// Resident CTAs per SM of the fused-schedule kernels.
+int occupancy_fused_m2(KernelKind k, size_t smem);
+int occupancy_fused_m4(KernelKind k, size_t smem);
+int occupancy_fused_m8(KernelKind k, size_t smem);
 // Raises the dynamic shared-memory limit of every kernel of the bucket to `bytes`.
 cudaError_t configure_m2(int bytes);
 cudaError_t configure_m4(int bytes);

@@ -25,6 +25,8 @@ _lib = ctypes.CDLL(_LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ESINGULAR, ETIMEOUT, EBUSY = range(8)
 UPDATE_W, UPDATE_H, UPDATE_G, UPDATE_Q, UPDATE_ALL = 1, 2, 4, 8, 15
 PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2
+SCHED_AUTO, SCHED_SWEEP, SCHED_FUSED = 0, 1, 2
+SOURCE_NMF, SOURCE_FREE = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ESINGULAR",
                 6: "ETIMEOUT", 7: "EBUSY"}
 
@@ -32,6 +34,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
 EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "fmnmf_iterate", "fmnmf_sync",
            "fmnmf_query",
            "fmnmf_loglik", "fmnmf_separate", "fmnmf_get_state", "fmnmf_set_state", "fmnmf_shape",
+           "fmnmf_get_lambda", "fmnmf_set_lambda",
            "fmnmf_destroy", "fmnmf_last_error", "fmnmf_set_timing", "fmnmf_kernel_times",
            "fmnmf_kernel_name", "fmnmf_launch_count", "fmnmf_loglik_noalloc",
            "fmnmf_batch_create", "fmnmf_batch_iterate", "fmnmf_batch_sync", "fmnmf_batch_destroy",
@@ -42,7 +45,8 @@ EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("update_mask", ctypes.c_uint), ("normalise", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_size_t)]
+                ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_size_t), ("schedule", ctypes.c_int),
+                ("source_model", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -60,6 +64,8 @@ _sig = {
     "fmnmf_separate": (_S, [_P, _P, _I]),
     "fmnmf_get_state": (_S, [_P, _P, _P, _P, _P]),
     "fmnmf_set_state": (_S, [_P, _P, _P, _P, _P]),
+    "fmnmf_get_lambda": (_S, [_P, _P, _P, _P]),
+    "fmnmf_set_lambda": (_S, [_P, _P, _P, _P]),
     "fmnmf_shape": (_S, [_P] + [ctypes.POINTER(_I)] * 5),
     "fmnmf_destroy": (_S, [_P]),
     "fmnmf_last_error": (ctypes.c_char_p, [_P]),
@@ -121,14 +127,18 @@ def _host_ptr(a: np.ndarray, dtype) -> tuple[np.ndarray, int]:
 class Context:
     """One mixture's device-resident FastMNMF state (wraps fmnmf_ctx)."""
 
-    def __init__(self, X, N: int, K: int, seed: int = 0, *, update_mask: int = UPDATE_ALL,
-                 normalise: bool = True, precision: int = PREC_FP32, stream=None, hbm_budget: int = 0):
+    def __init__(self, X, N: int, K: int = 1, seed: int = 0, *, update_mask: int = UPDATE_ALL,
+                 normalise: bool = True, precision: int = PREC_FP32, stream=None, hbm_budget: int = 0,
+                 schedule: int = SCHED_AUTO, source_model: int = SOURCE_NMF):
         opts = default_opts()
         opts.update_mask = update_mask
         opts.normalise = 1 if normalise else 0
         opts.precision = precision
         opts.stream = stream
         opts.hbm_budget = hbm_budget
+        opts.schedule = schedule
+        opts.source_model = source_model
+        self.free_model = source_model == SOURCE_FREE
         self._ctx = _P()
         self._keep = None
         if torch is not None and isinstance(X, torch.Tensor) and X.is_cuda:
@@ -212,12 +222,32 @@ class Context:
         return res
 
     def get_state(self):
-        W = np.empty((self.N, self.K, self.F), np.float32)
-        H = np.empty((self.N, self.K, self.T), np.float32)
+        """(W, H, g~, Q); W and H are None for the unconstrained source model."""
         G = np.empty((self.N, self.F, self.M), np.float32)
         Q = np.empty((self.F, self.M, self.M), np.complex64)
+        if self.free_model:
+            _check(_lib.fmnmf_get_state(self._ctx, None, None, G.ctypes.data, Q.ctypes.data), self._ctx)
+            return None, None, G, Q
+        W = np.empty((self.N, self.K, self.F), np.float32)
+        H = np.empty((self.N, self.K, self.T), np.float32)
         _check(_lib.fmnmf_get_state(self._ctx, W.ctypes.data, H.ctypes.data, G.ctypes.data, Q.ctypes.data), self._ctx)
         return W, H, G, Q
+
+    def get_lambda(self):
+        """(lambda [N, F, T], g~, Q) of the unconstrained source model."""
+        L = np.empty((self.N, self.F, self.T), np.float32)
+        G = np.empty((self.N, self.F, self.M), np.float32)
+        Q = np.empty((self.F, self.M, self.M), np.complex64)
+        _check(_lib.fmnmf_get_lambda(self._ctx, L.ctypes.data, G.ctypes.data, Q.ctypes.data), self._ctx)
+        return L, G, Q
+
+    def set_lambda(self, L, G, Q):
+        L, lp = _host_ptr(L, np.float32)
+        G, gp = _host_ptr(G, np.float32)
+        Q, qp = _host_ptr(Q, np.complex64)
+        assert L.shape == (self.N, self.F, self.T) and G.shape == (self.N, self.F, self.M)
+        assert Q.shape == (self.F, self.M, self.M)
+        _check(_lib.fmnmf_set_lambda(self._ctx, lp, gp, qp), self._ctx)
 
     def set_state(self, W, H, G, Q):
         W, wp = _host_ptr(W, np.float32)

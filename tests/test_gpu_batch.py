@@ -1,5 +1,7 @@
 """Batched form: several mixtures of uneven shapes (and precisions) iterated by one CUDA
-graph launch.  Each member must end bit-identical to the same context iterated alone."""
+graph launch.  Each member must end bit-identical to the same context iterated alone with
+the same iterations per call (the fused schedule's mu normalisation runs at the end of each
+call, so call boundaries are part of the computation)."""
 import numpy as np
 import pytest
 
@@ -35,7 +37,8 @@ def test_batch_equals_alone(fm):
     got = [c.get_state() + (c.loglik(),) for c in ctxs]
     for i, (m, c) in enumerate(zip(mixes, CASES)):
         alone = fm.Context(m.X, c[3], c[4], seed=i, precision=c[5])
-        alone.iterate(7)
+        alone.iterate(4)
+        alone.iterate(3)
         ref = alone.get_state() + (alone.loglik(),)
         for a, r in zip(got[i], ref):
             np.testing.assert_array_equal(a, r)
@@ -52,7 +55,9 @@ def test_batch_then_alone_orders(fm):
         b.iterate(2)
         b.sync()
     ref = fm.Context(m.X, 3, 8, seed=1)
-    ref.iterate(5)
+    ref.iterate(2)
+    ref.iterate(1)
+    ref.iterate(2)
     for x, y in zip(a.get_state(), ref.get_state()):
         np.testing.assert_array_equal(x, y)
 

@@ -1,4 +1,5 @@
-"""The bench's own job, checked against the float64 oracle: the chosen (BF16 mixed) form on
+"""The bench's own job, checked against the float64 oracle: the timed forms (FP32 with the
+fused schedule, and the BF16 mixed form) on
 the paper-scale mixture (M4 N4 K32 F513 T640, 10 % of the bins with diffuse noise) from the
 seeded initial state of fmnmf_init, 100 iterations (the paper's count, Sec. IV-A), then the
 Wiener separation.
@@ -25,8 +26,10 @@ from tests._parity import rel, elem_rel, image_scale, ll_rel
 pytestmark = pytest.mark.gpu
 
 MONO_TOL = 1e-6      # largest allowed fall of one iteration, relative to |LL|
-DRIFT_LL = 1e-3      # |dLL| / sum|terms| after 100 iterations
-DRIFT_STATE = 5e-2   # ||a - b|| / ||b|| of W, H, g~, Q after 100 iterations
+# drift after 100 iterations (measured: BF16 W 9.2e-4, H 8.8e-4, Q 5.0e-4, LL 3.8e-8;
+# bounds = 5x the measured BF16 drift; the FP32 form drifts far less)
+DRIFT_LL = 2e-7      # |dLL| / sum|terms|
+DRIFT_STATE = 5e-3   # ||a - b|| / ||b|| of W, H, g~, Q
 TOL_IMG = 1e-3       # images vs the oracle's filter of the GPU's own state
 
 
@@ -41,7 +44,7 @@ def fm():
     return fastmnmf
 
 
-@pytest.mark.parametrize("form", ["bf16"])
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
 def test_bench_job_c1_100_iterations(fm, form):
     c = CONFIGS["c1"]
     F, T, M, N, K, iters = c["F"], c["T"], c["M"], c["N"], c["K"], c["iters"]
