@@ -68,10 +68,10 @@ struct fmnmf_ctx {
   bool fusedPR = false;  // the kernel that forms x~ also forms P, R of the next W update
   // fused FP32 schedule (k_hgemm + k_bin per iteration) and the unconstrained source model
   bool fused = false, free_model = false;
-  int hgS = 1, hgSpan = 32;        // H GEMM: bin splits and bins per split
-  int hgBaseS = 1;                 // the planned split count (the tuner scales it)
+  int hgS = 1, hgSpan = 32;        // H GEMM: bin splits (one cluster per tile) and bins per split
   size_t binSm = 0;                // k_bin's dynamic shared memory
-  unsigned ctrHG = 0;              // first arrival counter of the H GEMM tiles
+  bool prsm = false;               // k_bin keeps the W update's P, R in shared memory
+  bool lamsm = false;              // k_bin keeps the bin's lambda in shared memory
   float* lam0 = nullptr;           // restart copy of lambda (unconstrained model)
   unsigned ctrW = 0, ctrH = 0, ctrG = 0, ctrY = 0, ctrLL = 0;
   // copy of the state set by the last init / reset / set_state (for fmnmf_restart)
@@ -371,9 +371,7 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     const int Kf = ctx->free_model ? 1 : K;
     const size_t bsm = (size_t)bin_smem(N, Kf, mx).total * 4;
     bool ok = !ctx->mixed && N * Kf <= kFuMaxPairs && N * M <= kFuMaxPairs && bsm <= (size_t)kSmemMax;
-    // H GEMM: bin splits for about four CTAs per SM, at least 32 bins (one chunk) a split
-    const int hg_tiles = ((T + kHgTT - 1) / kHgTT) * ((K + kHgKT - 1) / kHgKT) * N;
-    int hgS = std::max(1, std::min((F + kHgFC - 1) / kHgFC, (4 * sms + hg_tiles - 1) / hg_tiles));
+    // H GEMM: kHgS bin splits, one thread-block cluster per tile
     const int sched = ctx->opts.schedule;
     if (ctx->free_model && !ok)
       return set_err(ctx, FMNMF_EINVAL, "the unconstrained source model needs the fused FP32 schedule (N*M <= %d)",
@@ -383,9 +381,37 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
                      kFuMaxPairs);
     ctx->fused = ok && (ctx->free_model || sched != FMNMF_SCHED_SWEEP);
     if (ctx->fused) {
-      ctx->hgBaseS = hgS;
       ctx->binSm = bsm;
       mx_cap_smem = std::max(mx_cap_smem, ctx->binSm);
+      // the W update's P, R and the bin's lambda in shared memory, when they fit without
+      // costing a resident CTA (the first of these layouts that keeps the occupancy)
+      if (!ctx->free_model) {
+        auto occ = [&](size_t b) {
+          switch (mx) {
+            case 2: return occupancy_fused_m2(KK_BIN, b);
+            case 4: return occupancy_fused_m4(KK_BIN, b);
+            default: return occupancy_fused_m8(KK_BIN, b);
+          }
+        };
+        const size_t nt = (size_t)N * T;
+        struct Cand { bool pr, lam; };
+        const Cand cands[3] = {{true, true}, {true, false}, {false, true}};
+        for (const Cand& cd : cands) {
+          if ((cd.pr && 2 * nt * 4 > 32 * 1024) || (cd.lam && nt * 4 > 16 * 1024)) continue;
+          const size_t b = 4 * (cd.lam ? (size_t)bin_smem_lam_offset(N, Kf, mx, T, cd.pr) + nt
+                                       : (size_t)bin_smem_pr_offset(N, Kf, mx) + 2 * nt);
+          if (b > (size_t)kSmemMax) continue;
+          CK(configure(mx, (int)std::max(mx_cap_smem, b)));
+          const int o0 = occ(bsm), o1 = occ(b);
+          if (o1 >= o0 && o1 > 0) {
+            ctx->prsm = cd.pr;
+            ctx->lamsm = cd.lam;
+            ctx->binSm = b;
+            mx_cap_smem = std::max(mx_cap_smem, b);
+            break;
+          }
+        }
+      }
       CK(configure(mx, (int)mx_cap_smem));
     }
   }
@@ -393,21 +419,15 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
   const int base[TU_COUNT] = {ctx->gW.S, ctx->gH.S, ctx->gG.S, ctx->gY.S, ctx->scmS, ctx->gtcS,
                               ctx->mixed ? ctx->gpW.g.ksplit : 1, ctx->mixed ? ctx->gpH.g.ksplit : 1};
   for (int t = 0; t < TU_COUNT; ++t) { ctx->baseS[t] = base[t]; ctx->tscale[t] = 1.f; }
-  // fused schedule: tuning entry 1 (the H sweep's, unused there) scales the H GEMM's splits
-  if (ctx->fused) ctx->baseS[TU_H] = ctx->hgBaseS;
   apply_fused_shape(ctx);
   return FMNMF_OK;
 }
 
-// The fused schedule's H GEMM: its bin splits (planned count times the tuner's scale) and
-// bins per split (whole chunks of 32).
+// The fused schedule's H GEMM: bins per split (kHgS splits, the CTAs of one cluster).
 void apply_fused_shape(fmnmf_ctx* c) {
   if (!c->fused) return;
-  const int S0 = std::max(1, (int)std::lround(c->baseS[TU_H] * c->tscale[TU_H]));
-  const int nch = (c->F + kHgFC - 1) / kHgFC;
-  const int per = (nch + std::min(S0, nch) - 1) / std::min(S0, nch);
-  c->hgSpan = per * kHgFC;
-  c->hgS = (c->F + c->hgSpan - 1) / c->hgSpan;
+  c->hgS = kHgS;
+  c->hgSpan = (c->F + kHgS - 1) / kHgS;
 }
 
 // Re-derives the tunable launch shapes from the planned split counts and the tuner's scales.
@@ -458,17 +478,13 @@ fmnmf_status allocate(fmnmf_ctx* ctx, bool dry_run = false) {
   part = std::max(part, (size_t)ctx->gY.S * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   if (ctx->mixed) part = std::max(part, (size_t)ctx->scmS * tile_part_floats(MODE_Y, F, T, M, N, K, mx));
   if (ctx->mixed && ctx->gtcNP > 0) part = std::max(part, (size_t)ctx->gtcS * tile_part_floats(MODE_G, F, T, M, N, K, mx));
-  // the H GEMM's split partials, sized for the planned split count (the tuner only lowers it)
-  if (ctx->fused && !ctx->free_model) part = std::max(part, (size_t)ctx->hgBaseS * 2 * N * K * T);
-  const unsigned hg_tiles = ctx->fused ? (unsigned)(((T + kHgTT - 1) / kHgTT) * ((K + kHgKT - 1) / kHgKT) * N) : 0u;
   const unsigned nctr = ctx->gW.n_own_tiles + ctx->gH.n_own_tiles + ctx->gG.n_own_tiles +
-                        ctx->gY.n_own_tiles + 1 + hg_tiles;
+                        ctx->gY.n_own_tiles + 1;
   ctx->ctrW = 0;
   ctx->ctrH = ctx->ctrW + ctx->gW.n_own_tiles;
   ctx->ctrG = ctx->ctrH + ctx->gH.n_own_tiles;
   ctx->ctrY = ctx->ctrG + ctx->gG.n_own_tiles;
   ctx->ctrLL = ctx->ctrY + ctx->gY.n_own_tiles;
-  ctx->ctrHG = ctx->ctrLL + 1;
   struct Slot { void** dst; size_t bytes; };
   Prob& p = ctx->p;
   void* X = nullptr;
@@ -729,7 +745,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
 
 LaunchArgs hgemm_args(fmnmf_ctx* c) {
   LaunchArgs a;
-  a.p = c->p; a.st = c->st; a.pr = c->PR; a.ctr = c->ctrHG;
+  a.p = c->p; a.st = c->st; a.pr = c->PR;
   a.g.S = c->hgS; a.g.span = c->hgSpan;
   a.grid = dim3((c->T + kHgTT - 1) / kHgTT, (c->K + kHgKT - 1) / kHgKT, c->N * c->hgS);
   return a;
@@ -757,7 +773,7 @@ cudaError_t enqueue_fused_chunk(fmnmf_ctx* c, Recorder& rec, int n) {
     a.lam = c->lam; a.pr = c->PR;
     return rec.run(KK_BIN, a);
   };
-  const int lam0 = fm ? 0 : FU_LAM0;
+  const int lam0 = fm ? 0 : (FU_LAM0 | (c->prsm ? FU_PRSM : 0) | (c->lamsm ? FU_LAMSM : 0));
   const int base = ((mask & FMNMF_UPDATE_G) ? FU_G : 0) | ((mask & FMNMF_UPDATE_Q) ? FU_Q : 0) |
                    (norm ? FU_NORM : 0) | (fm ? FU_FREE : 0) | ((fm && (mask & FMNMF_UPDATE_W)) ? FU_LAM : 0) | lam0;
   if ((upW || upH) && (e = bin(FU_WONLY | lam0 | (upW ? FU_W : 0) | (upH ? FU_PH : 0))) != cudaSuccess) return e;
@@ -1387,7 +1403,7 @@ fmnmf_status fmnmf_autotune(fmnmf_ctx* ctx, int n_iter, double* speedup) {
   CK(cudaEventCreate(&e1));
   // the fused schedule's one tunable launch shape is the H kernel's frame tile (entry TU_H)
   std::vector<int> tun;
-  if (ctx->fused) tun = {TU_H};
+  if (ctx->fused) tun = {};  // no tunable launch shape (bins per CTA and splits are fixed)
   else if (ctx->mixed) tun = {TU_SCM, TU_GTC, TU_GEMM_W, TU_GEMM_H};
   else tun = {TU_W, TU_H, TU_G, TU_Y};
   const double t0 = tune_trial(ctx, sv, n_iter, e0, e1);

@@ -20,7 +20,11 @@
 // sum), which gives the state the per-iteration normalisation gives, up to rounding.
 // Every sum has a fixed order (no atomics), so results are bitwise reproducible.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "fm_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fm {
 
@@ -36,6 +40,8 @@ enum : int {
   FU_FREE = 128,   // unconstrained source model: lambda is the state (no W, H)
   FU_LAM0 = 256,   // form lambda of the bin from W, H first (NMF model)
   FU_PH = 512,     // end with P, R of the next H update (from the lambda of the new W)
+  FU_PRSM = 1024,  // the W update's P, R in shared memory (2 N T floats after the layout)
+  FU_LAMSM = 2048, // the bin's lambda in shared memory (N T floats after P, R) instead of lam
 };
 
 constexpr int kFuTC = 256;          // frames per chunk of k_bin (one per thread)
@@ -62,42 +68,134 @@ __host__ __device__ inline BinSmem bin_smem(int N, int K, int maxm) {
   s.total = o;                         // the reductions reuse a..xi (>= 4 MAXM TCP floats)
   return s;
 }
+// With FU_PRSM the W update's P, R [2N][T] follow the layout (16-byte aligned); with FU_LAMSM
+// the bin's lambda [N][T] follows them (after the P, R space when FU_PRSM is set).
+__host__ __device__ inline int bin_smem_pr_offset(int N, int K, int maxm) { return (bin_smem(N, K, maxm).total + 3) & ~3; }
+__host__ __device__ inline int bin_smem_lam_offset(int N, int K, int maxm, int T, bool prsm) {
+  return bin_smem_pr_offset(N, K, maxm) + (prsm ? ((2 * N * T + 3) & ~3) : 0);
+}
 
 // Correctly rounded reciprocal (the ratios of every MU rule).
 __device__ __forceinline__ float fu_rcp(float y) { return __frcp_rn(y); }
 
 // lambda_ftn = sum_k w_nkf h_nkt (Eq. 9) for the bin's frames, w of the bin in shared memory,
-// into out[n FT + t] (out = lam + f T).  Four consecutive frames a thread (16-byte rows of H)
-// when T is a multiple of 4; the k sum in order.
+// into out[n * FT + t] (the bin's rows of lam, or of a shared-memory copy with FT = T).  Work
+// items are (4-frame group, source) pairs (16-byte rows of H) when T is a multiple of 4, else
+// (frame, source) pairs; the k sum in order.
 __device__ __forceinline__ void bin_lambda(const Prob& p, const float* ws, float* out, size_t FT) {
   const int T = p.T, N = p.N, K = p.K, tid = threadIdx.x;
   if ((T & 3) == 0) {
-    for (int t4 = 4 * tid; t4 < T; t4 += 4 * kThreads)
-      for (int n = 0; n < N; ++n) {
-        const float* hr = p.H + (size_t)n * K * T + t4;
-        const float* w = ws + n * K;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    // one (4-frame group, source) pair a thread at a time: every thread has work
+    const int ng = T >> 2;
+    for (int e = tid; e < ng * N; e += kThreads) {
+      const int n = e / ng, t4 = 4 * (e - n * ng);
+      const float* hr = p.H + (size_t)n * K * T + t4;
+      const float* w = ws + n * K;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
-        for (int k = 0; k < K; ++k) {
-          const float4 h = __ldg(reinterpret_cast<const float4*>(hr + (size_t)k * T));
-          const float wk = w[k];
-          a.x = fmaf(wk, h.x, a.x);
-          a.y = fmaf(wk, h.y, a.y);
-          a.z = fmaf(wk, h.z, a.z);
-          a.w = fmaf(wk, h.w, a.w);
-        }
-        *reinterpret_cast<float4*>(out + n * FT + t4) = a;
+      for (int k = 0; k < K; ++k) {
+        const float4 h = __ldg(reinterpret_cast<const float4*>(hr + (size_t)k * T));
+        const float wk = w[k];
+        a.x = fmaf(wk, h.x, a.x);
+        a.y = fmaf(wk, h.y, a.y);
+        a.z = fmaf(wk, h.z, a.z);
+        a.w = fmaf(wk, h.w, a.w);
       }
+      *reinterpret_cast<float4*>(out + n * FT + t4) = a;
+    }
   } else {
-    for (int t = tid; t < T; t += kThreads)
-      for (int n = 0; n < N; ++n) {
-        const float* hr = p.H + (size_t)n * K * T + t;
-        const float* w = ws + n * K;
-        float a = 0.f;
+    for (int e = tid; e < T * N; e += kThreads) {
+      const int n = e / T, t = e - n * T;
+      const float* hr = p.H + (size_t)n * K * T + t;
+      const float* w = ws + n * K;
+      float a = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < K; ++k) a = fmaf(w[k], __ldg(hr + (size_t)k * T), a);
-        out[n * FT + t] = a;
+      for (int k = 0; k < K; ++k) a = fmaf(w[k], __ldg(hr + (size_t)k * T), a);
+      out[n * FT + t] = a;
+    }
+  }
+}
+
+// The W update's sums for one bin (Eq. 23) and the update itself: num/den[n][k] = sum_t h_nkt
+// {P, R}_nt, w_nk <- w_nk sqrt(num/den) (into W and into ws).  Warp w owns k = w + 8 j,
+// j < KW (KW a compile-time bound; invalid k are skipped per warp), for every source.  With T a
+// multiple of 4 a lane takes 16-byte groups of frames, U groups (U * 128 frames) a step, so that
+// U * KW row loads are in flight; otherwise single frames.
+template <int KW>
+__device__ __forceinline__ void w_sums(const Prob& p, const float* Pw, size_t pws, float* ws, int f) {
+  constexpr int nwarps = kThreads / 32;
+  constexpr int U = KW <= 2 ? 4 : KW <= 4 ? 2 : 1;
+  const int T = p.T, N = p.N, K = p.K, F = p.F;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec = (T & 3) == 0;
+  for (int kb = 0; kb < K; kb += nwarps * KW) {
+    const int k0 = kb + warp;
+    if (k0 >= K) continue;
+    const int kv = min(KW, (K - k0 + nwarps - 1) / nwarps);  // valid k of this warp
+    for (int n = 0; n < N; ++n) {
+      const float* Pn = Pw + n * pws;
+      const float* Rn = Pw + (N + n) * pws;
+      const float* __restrict__ Hn = p.H + ((size_t)n * K + k0) * T;
+      float an[KW], ad[KW];
+#pragma unroll
+      for (int j = 0; j < KW; ++j) { an[j] = 0.f; ad[j] = 0.f; }
+      if (vec) {
+        for (int t0 = 4 * lane; t0 < T; t0 += 128 * U) {
+          float4 Pv[U], Rv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int t4 = t0 + 128 * u;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            Pv[u] = t4 < T ? *reinterpret_cast<const float4*>(Pn + t4) : z4;
+            Rv[u] = t4 < T ? *reinterpret_cast<const float4*>(Rn + t4) : z4;
+          }
+#pragma unroll
+          for (int j = 0; j < KW; ++j) {
+            if (j >= kv) break;
+            const float* hj = Hn + (size_t)j * nwarps * T;
+            float4 h[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int t4 = t0 + 128 * u;
+              h[u] = t4 < T ? __ldg(reinterpret_cast<const float4*>(hj + t4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              an[j] = fmaf(h[u].x, Pv[u].x, fmaf(h[u].y, Pv[u].y, fmaf(h[u].z, Pv[u].z, fmaf(h[u].w, Pv[u].w, an[j]))));
+              ad[j] = fmaf(h[u].x, Rv[u].x, fmaf(h[u].y, Rv[u].y, fmaf(h[u].z, Rv[u].z, fmaf(h[u].w, Rv[u].w, ad[j]))));
+            }
+          }
+        }
+      } else {
+        for (int t = lane; t < T; t += 32) {
+          const float Pv = Pn[t], Rv = Rn[t];
+#pragma unroll
+          for (int j = 0; j < KW; ++j) {
+            if (j >= kv) break;
+            const float h = __ldg(Hn + (size_t)j * nwarps * T + t);
+            an[j] = fmaf(h, Pv, an[j]);
+            ad[j] = fmaf(h, Rv, ad[j]);
+          }
+        }
       }
+#pragma unroll
+      for (int j = 0; j < KW; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          an[j] += __shfl_xor_sync(0xffffffffu, an[j], o);
+          ad[j] += __shfl_xor_sync(0xffffffffu, ad[j], o);
+        }
+      if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < KW; ++j) {
+          if (j >= kv) break;
+          const int k = k0 + j * nwarps;
+          const float w = ws[n * K + k] * sqrtf(an[j] / ad[j]);
+          if (!isfinite(w)) flag(p.status, ST_NONFINITE);
+          p.W[((size_t)n * K + k) * F + f] = w;
+          ws[n * K + k] = w;  // this warp owns (n, k): the lambda of the new W reads it
+        }
+    }
   }
 }
 
@@ -138,6 +236,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
   float* red = bsm + L.a;
   const size_t FT = (size_t)F * T;
   const size_t fT = (size_t)f * T;
+  // the W update's P, R: rows of T in shared memory, or rows of the bin in PR (stride F T)
+  const bool prsm = (flags & FU_PRSM) != 0;
+  float* Pw = prsm ? bsm + bin_smem_pr_offset(N, K, MAXM) : PR + fT;
+  const size_t pws = prsm ? (size_t)T : FT;
+  // the bin's lambda: rows of T in shared memory, or rows of the bin in lam (stride F T)
+  const bool lamsm = (flags & FU_LAMSM) != 0;
+  float* lb = lamsm ? bsm + bin_smem_lam_offset(N, K, MAXM, T, prsm) : lam + fT;
+  const size_t ls = lamsm ? (size_t)T : FT;
   const float2* __restrict__ Xf = p.X + fT * M;
   float* __restrict__ xtf = p.xt + fT * M;
   const bool free_model = (flags & FU_FREE) != 0;
@@ -163,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
   }
   __syncthreads();
   if (!free_model && (flags & FU_LAM0)) {
-    bin_lambda(p, ws, lam + fT, FT);
+    bin_lambda(p, ws, lb, ls);
     __syncthreads();  // the bin's lambda (global) is read by this CTA's threads below
   }
 
@@ -177,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
         x[m] = (m < M) ? xtf[(size_t)t * M + m] : 0.f;
       }
       for (int n = 0; n < N; ++n) {
-        const float l = lam[n * FT + fT + t];
+        const float l = lb[n * ls + t];
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
           if (m < M) y[m] = fmaf(l, gs[n * MAXM + m], y[m]);
@@ -196,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
             P = fmaf(gs[n * MAXM + m], A[m], P);
             R = fmaf(gs[n * MAXM + m], B[m], R);
           }
-        float* lp = lam + n * FT + fT + t;
+        float* lp = lb + n * ls + t;
         const float l = *lp * sqrtf(P / R);
         if (!isfinite(l)) flag(p.status, ST_NONFINITE);
         *lp = l;
@@ -221,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) y[m] = 0.f;
         for (int n = 0; n < N; ++n) {
-          const float l = lam[n * FT + fT + t];
+          const float l = lb[n * ls + t];
           lamc[n * kFuTCP + tid] = l;
 #pragma unroll
           for (int m = 0; m < MAXM; ++m)
@@ -289,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) y[m] = 0.f;
         for (int n = 0; n < N; ++n) {
-          const float l = lam[n * FT + fT + t];
+          const float l = lb[n * ls + t];
 #pragma unroll
           for (int m = 0; m < MAXM; ++m)
             if (m < M) y[m] = fmaf(l, gs[n * MAXM + m], y[m]);
@@ -465,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) y[m] = 0.f;
     for (int n = 0; n < N; ++n) {
-      float* lp = lam + n * FT + fT + t;
+      float* lp = lb + n * ls + t;
       const float l = *lp * nus[n];
       if (lamwb) *lp = l;
 #pragma unroll
@@ -491,8 +597,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
             P = fmaf(gs[n * MAXM + m], A[m], P);
             R = fmaf(gs[n * MAXM + m], B[m], R);
           }
-        PR[n * FT + fT + t] = P;
-        PR[(N + n) * FT + fT + t] = R;
+        Pw[n * pws + t] = P;
+        Pw[(N + n) * pws + t] = R;
       }
     }
   }
@@ -510,73 +616,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
   }
 
   // ---- W update of the next iteration (Eq. 23): num/den[n][k] = sum_t h_nkt {P, R}_nft.
-  // Warp w owns k = w, w + 8, ... of every source; lanes stride the frames (coalesced H rows;
-  // four consecutive frames a lane as 16-byte loads when T is a multiple of 4, else four
-  // strided frames); the lane sums are added by a butterfly (fixed order).
+  // Warp w owns k = w, w + 8, ... of every source (KW = ceil(K/8) of them, a compile-time count
+  // in w_sums); lanes stride the frames (coalesced H rows).  The lane sums are added by a
+  // butterfly (fixed order).
   if (doW) {
-    constexpr int KG = 8;  // k values per warp per pass (registers: 2 KG accumulators)
-    const int nwarps = kThreads / 32;
-    const bool vec = (T & 3) == 0;
-    for (int n = 0; n < N; ++n) {
-      const float* __restrict__ Pn = PR + n * FT + fT;
-      const float* __restrict__ Rn = PR + (N + n) * FT + fT;
-      for (int k0 = warp; k0 < K; k0 += nwarps * KG) {
-        float an[KG], ad[KG];
-#pragma unroll
-        for (int j = 0; j < KG; ++j) { an[j] = 0.f; ad[j] = 0.f; }
-        const float* __restrict__ Hn = p.H + ((size_t)n * K + k0) * T;
-        if (vec) {
-          for (int t4 = 4 * lane; t4 < T; t4 += 128) {
-            const float4 Pv = *reinterpret_cast<const float4*>(Pn + t4);
-            const float4 Rv = *reinterpret_cast<const float4*>(Rn + t4);
-#pragma unroll
-            for (int j = 0; j < KG; ++j)
-              if (k0 + j * nwarps < K) {
-                const float4 h = __ldg(reinterpret_cast<const float4*>(Hn + (size_t)j * nwarps * T + t4));
-                an[j] = fmaf(h.x, Pv.x, fmaf(h.y, Pv.y, fmaf(h.z, Pv.z, fmaf(h.w, Pv.w, an[j]))));
-                ad[j] = fmaf(h.x, Rv.x, fmaf(h.y, Rv.y, fmaf(h.z, Rv.z, fmaf(h.w, Rv.w, ad[j]))));
-              }
-          }
-        } else {
-          for (int tb = 0; tb < T; tb += 128) {
-            float Pv[4], Rv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int t = tb + lane + 32 * u;
-              Pv[u] = (t < T) ? Pn[t] : 0.f;
-              Rv[u] = (t < T) ? Rn[t] : 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < KG; ++j)
-              if (k0 + j * nwarps < K)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const int t = tb + lane + 32 * u;
-                  const float h = (t < T) ? __ldg(Hn + (size_t)j * nwarps * T + t) : 0.f;
-                  an[j] = fmaf(h, Pv[u], an[j]);
-                  ad[j] = fmaf(h, Rv[u], ad[j]);
-                }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < KG; ++j)
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            an[j] += __shfl_xor_sync(0xffffffffu, an[j], o);
-            ad[j] += __shfl_xor_sync(0xffffffffu, ad[j], o);
-          }
-        if (lane == 0)
-#pragma unroll
-          for (int j = 0; j < KG; ++j) {
-            const int k = k0 + j * nwarps;
-            if (k < K) {
-              const float w = ws[n * K + k] * sqrtf(an[j] / ad[j]);
-              if (!isfinite(w)) flag(p.status, ST_NONFINITE);
-              p.W[((size_t)n * K + k) * F + f] = w;
-              ws[n * K + k] = w;  // this warp owns (n, k): the lambda of the new W reads it
-            }
-          }
-      }
+    const int KW = (K + 7) / 8;
+    switch (KW) {
+      case 1: w_sums<1>(p, Pw, pws, ws, f); break;
+      case 2: w_sums<2>(p, Pw, pws, ws, f); break;
+      case 3: w_sums<3>(p, Pw, pws, ws, f); break;
+      case 4: w_sums<4>(p, Pw, pws, ws, f); break;
+      case 5: case 6: w_sums<6>(p, Pw, pws, ws, f); break;
+      default: w_sums<8>(p, Pw, pws, ws, f); break;  // K <= 64 here; larger K loops inside
     }
   } else if (!free_model && !wonly && (flags & FU_NORM)) {
     for (int e = tid; e < N * K; e += kThreads) p.W[(size_t)e * F + f] = ws[e];
@@ -588,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
   if (!free_model && (flags & FU_PH)) {
     __syncthreads();  // the W sums have read PR; the new w is in ws
     if (doW) {
-      bin_lambda(p, ws, lam + fT, FT);
+      bin_lambda(p, ws, lb, ls);
       __syncthreads();
     }
     for (int t = tid; t < T; t += kThreads) {
@@ -596,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) y[m] = 0.f;
       for (int n = 0; n < N; ++n) {
-        const float l = lam[n * FT + fT + t];
+        const float l = lb[n * ls + t];
 #pragma unroll
         for (int m = 0; m < MAXM; ++m)
           if (m < M) y[m] = fmaf(l, gs[n * MAXM + m], y[m]);
@@ -625,26 +676,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 // k_hgemm: the H update of Eq. 24 as a register-tiled FP32 GEMM per source n,
 //   num[k][t] = sum_f w_nkf P_nft,   den[k][t] = sum_f w_nkf R_nft,
 // with P, R (the H update's per-point factors, from the lambda of the new W) written by the
-// bins' kernel.  CTA tile: 32 bases x 64 frames of one source, over one of S splits of the
-// bins in chunks of 32; thread (ty, tx) owns bases 2ty, 2ty+1 and frames 4tx..4tx+3 (16
-// accumulators; per bin one 8-byte W load and two 16-byte P, R loads feed 16 FMAs).  The
-// splits' partial sums go to `part` ([S][2][N][K][T]); the last CTA of a tile to arrive adds
-// them in split order and applies h <- h sqrt(num/den).
+// bins' kernel.  A tile is 32 bases x 64 frames of one source; its bins are split over the
+// kHgS CTAs of one thread-block cluster, each summing its bins in chunks of 72 (thread
+// (ty, tx) owns bases 2ty, 2ty+1 and frames 4tx..4tx+3: per bin one 8-byte W load and two
+// 16-byte P, R loads feed 16 FMAs).  The CTAs leave their partial tiles in shared memory;
+// after a cluster barrier CTA r adds rows 4r..4r+3 of all of them, in rank order, through
+// distributed shared memory and applies h <- h sqrt(num/den); a second cluster barrier
+// keeps every partial tile alive until it has been read.
 // ---------------------------------------------------------------------------------------
-constexpr int kHgKT = 32, kHgTT = 64, kHgFC = 32;
+constexpr int kHgKT = 32, kHgTT = 64, kHgFC = 72;  // bins per chunk: 1/8 of 513-576 bins in one
+constexpr int kHgS = 8;           // bin splits = CTAs per cluster
 constexpr int kHgWS = kHgKT + 2;  // W chunk row (even, for 8-byte loads)
 
 template <int MAXM>  // one instance per channel-bucket translation unit (MAXM is not used)
-__global__ void __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restrict__ PR, int S, int span,
-                                                     unsigned ctr_base) {
+__global__ void __cluster_dims__(1, 1, kHgS) __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restrict__ PR,
+                                                                               int span) {
   __shared__ __align__(16) float Ws[kHgFC][kHgWS];
-  __shared__ __align__(16) float Ps[kHgFC][kHgTT];
-  __shared__ __align__(16) float Rs[kHgFC][kHgTT];
+  __shared__ __align__(16) float Ps[kHgFC][kHgTT];  // P chunk, then this CTA's num tile (rows < 32)
+  __shared__ __align__(16) float Rs[kHgFC][kHgTT];  // R chunk, then this CTA's den tile
+  cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
   const int F = p.F, T = p.T, N = p.N, K = p.K;
-  const int n = blockIdx.z / S, s = blockIdx.z % S;
+  const int n = blockIdx.z / kHgS, s = (int)cluster.block_rank();
   const int k0 = blockIdx.y * kHgKT, t0 = blockIdx.x * kHgTT;
-  const int fbeg = s * span, fend = min(F, fbeg + span);
+  const int fbeg = min(F, s * span), fend = min(F, fbeg + span);
   const size_t FT = (size_t)F * T;
   const int ty = tid >> 4, tx = tid & 15;
   const bool vecT = (T & 3) == 0;
@@ -658,35 +713,34 @@ __global__ void __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restr
   for (int f0 = fbeg; f0 < fend; f0 += kHgFC) {
     const int fc = min(kHgFC, fend - f0);
     __syncthreads();  // the previous chunk's readers are done
-#pragma unroll
-    for (int i = 0; i < (kHgFC * kHgKT) / kThreads; ++i) {
-      const int e = tid + i * kThreads, kk = e / kHgFC, ff = e % kHgFC;
-      const int k = k0 + kk;
-      Ws[ff][kk] = (ff < fc && k < K) ? __ldg(p.W + ((size_t)n * K + k) * F + f0 + ff) : 0.f;
+    // every copy of the chunk in flight at once (cp.async; zero fill outside the tile)
+    for (int e = tid; e < kHgFC * kHgKT; e += kThreads) {
+      const int kk = e / kHgFC, ff = e % kHgFC;
+      const bool ok = ff < fc && k0 + kk < K;
+      cpa4(&Ws[ff][kk], p.W + (ok ? ((size_t)n * K + k0 + kk) * F + f0 + ff : 0), ok);
     }
     if (vecT) {
-#pragma unroll
-      for (int i = 0; i < (kHgFC * kHgTT / 4) / kThreads; ++i) {
-        const int e = tid + i * kThreads, ff = e / (kHgTT / 4), q = (e % (kHgTT / 4)) * 4;
-        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), rv = pv;
+      for (int e = tid; e < kHgFC * kHgTT / 4; e += kThreads) {
+        const int ff = e / (kHgTT / 4), q = (e % (kHgTT / 4)) * 4;
         if (ff < fc && t0 + q < T) {
           const size_t o = (size_t)(f0 + ff) * T + t0 + q;
-          pv = __ldg(reinterpret_cast<const float4*>(Pn + o));
-          rv = __ldg(reinterpret_cast<const float4*>(Rn + o));
+          cpa16(&Ps[ff][q], Pn + o);
+          cpa16(&Rs[ff][q], Rn + o);
+        } else {
+          *reinterpret_cast<float4*>(&Ps[ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(&Rs[ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        *reinterpret_cast<float4*>(&Ps[ff][q]) = pv;
-        *reinterpret_cast<float4*>(&Rs[ff][q]) = rv;
       }
     } else {
-#pragma unroll
-      for (int i = 0; i < (kHgFC * kHgTT) / kThreads; ++i) {
-        const int e = tid + i * kThreads, ff = e / kHgTT, q = e % kHgTT;
+      for (int e = tid; e < kHgFC * kHgTT; e += kThreads) {
+        const int ff = e / kHgTT, q = e % kHgTT;
         const bool ok = ff < fc && t0 + q < T;
-        const size_t o = (size_t)(f0 + ff) * T + t0 + q;
-        Ps[ff][q] = ok ? __ldg(Pn + o) : 0.f;
-        Rs[ff][q] = ok ? __ldg(Rn + o) : 0.f;
+        const size_t o = ok ? (size_t)(f0 + ff) * T + t0 + q : 0;
+        cpa4(&Ps[ff][q], Pn + o, ok);
+        cpa4(&Rs[ff][q], Rn + o, ok);
       }
     }
+    cpa_wait_all();
     __syncthreads();
 #pragma unroll 4
     for (int ff = 0; ff < fc; ++ff) {
@@ -703,34 +757,34 @@ __global__ void __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restr
       }
     }
   }
-  // this split's partial sums
-  const size_t psz = (size_t)2 * N * K * T;
-  float* part = p.part + (size_t)s * psz;
+  // this CTA's partial tiles into its shared memory (row = base within the tile)
+  __syncthreads();
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    const int k = k0 + 2 * ty + a;
-    if (k >= K) continue;
+    *reinterpret_cast<float4*>(&Ps[2 * ty + a][4 * tx]) = make_float4(num[a][0], num[a][1], num[a][2], num[a][3]);
+    *reinterpret_cast<float4*>(&Rs[2 * ty + a][4 * tx]) = make_float4(den[a][0], den[a][1], den[a][2], den[a][3]);
+  }
+  cluster.sync();
+  {
+    // rows 4s..4s+3 of the tile: one (base, frame) per thread, the splits added in rank order
+    const int kk = 4 * s + tid / kHgTT, tt = tid % kHgTT;
+    float sn = 0.f, sd = 0.f;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int t = t0 + 4 * tx + b;
-      if (t >= T) continue;
-      part[((size_t)n * K + k) * T + t] = num[a][b];
-      part[((size_t)(N + n) * K + k) * T + t] = den[a][b];
+    for (int q = 0; q < kHgS; ++q) {
+      const float* rp = cluster.map_shared_rank(&Ps[0][0], q);
+      const float* rr = cluster.map_shared_rank(&Rs[0][0], q);
+      sn += rp[kk * kHgTT + tt];
+      sd += rr[kk * kHgTT + tt];
+    }
+    const int k = k0 + kk, t = t0 + tt;
+    if (k < K && t < T) {
+      const size_t i = ((size_t)n * K + k) * T + t;
+      const float h = p.H[i] * sqrtf(sn / sd);
+      if (!isfinite(h)) flag(p.status, ST_NONFINITE);
+      p.H[i] = h;
     }
   }
-  const unsigned tile = ((unsigned)n * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  if (!arrive_last(p.counters + ctr_base + tile, (unsigned)S)) return;
-  // last CTA of the tile: sum the splits in order, apply the update
-  for (int e = tid; e < kHgKT * kHgTT; e += kThreads) {
-    const int k = k0 + e / kHgTT, t = t0 + e % kHgTT;
-    if (k >= K || t >= T) continue;
-    const size_t i = ((size_t)n * K + k) * T + t;
-    const float sn = sum_splits(p.part + i, psz, S);
-    const float sd = sum_splits(p.part + (size_t)N * K * T + i, psz, S);
-    const float h = p.H[i] * sqrtf(sn / sd);
-    if (!isfinite(h)) flag(p.status, ST_NONFINITE);
-    p.H[i] = h;
-  }
+  cluster.sync();  // the other CTAs may still be reading this CTA's tiles
 }
 
 }  // namespace fm

@@ -24,7 +24,7 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
       k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
       break;
     case KK_BIN: k_bin<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.lam, a.pr, a.flags); break;
-    case KK_HGEMM: k_hgemm<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.pr, a.g.S, a.g.span, a.ctr); break;
+    case KK_HGEMM: k_hgemm<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.pr, a.g.span); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -1,9 +1,9 @@
 """The bin-fused FP32 schedule and the unconstrained source model (FastFCA) against the
 float64 oracle, through the C ABI.
 
-The fused schedule runs an iteration as two launches (the H update over tiles of frames;
-everything else per bin, with the W update of the next iteration at the end of the bin's
-kernel) and applies the mu normalisation once at the end of a call, so several iterations
+The fused schedule runs an iteration as two launches (the H update as a GEMM whose bin
+splits are the CTAs of a thread-block cluster; everything else per bin, with the W update of
+the next iteration and the next H update's per-point factors at the end of the bin's kernel) and applies the mu normalisation once at the end of a call, so several iterations
 in one call exercise paths one iteration does not: they are checked against the oracle's
 same iterations.  Bar: 1e-5 per iteration of the plain FP32 form (per tensor and per
 element, as in test_gpu_parity), scaled by the number of iterations for multi-iteration
@@ -35,14 +35,10 @@ def fm():
     return fastmnmf
 
 
-def _nmf_case(fm, F, T, M, N, K, n_iter, seed=1, mask=O.UPDATE_ALL, normalise=True, tile=None):
+def _nmf_case(fm, F, T, M, N, K, n_iter, seed=1, mask=O.UPDATE_ALL, normalise=True):
     mix = make_mixture(F, T, M, N, K, seed)
     W, H, G, Q = make_state(F, T, M, N, K, seed)
     ctx = fm.Context(mix.X, N, K, update_mask=mask, normalise=normalise, schedule=fm.SCHED_FUSED)
-    if tile is not None:  # tuning entry 1 selects the H kernel's frame tile: 1 -> 2, 0.5 -> 4, 0.25 -> 8
-        sc = ctx.get_tuning()
-        sc[1] = {2: 1.0, 4: 0.5, 8: 0.25}[tile]
-        ctx.set_tuning(sc)
     ctx.set_state(W, H, G, Q)
     ctx.iterate(n_iter)
     ll = ctx.loglik()
@@ -68,9 +64,14 @@ def test_fused_iterations_match_oracle(fm, shape, n_iter):
     assert max(err.values()) < n_iter * TOL, err
 
 
-@pytest.mark.parametrize("tile", [2, 4, 8])
-def test_fused_frame_tiles(fm, tile):
-    err = _nmf_case(fm, 70, 303, 4, 3, 16, n_iter=2, seed=4, tile=tile)
+# several base tiles of the H GEMM (K > 32), frames not a multiple of 4 (scalar paths) or of
+# the 64-frame tile, fewer bins than splits
+HG_SHAPES = [(70, 303, 4, 3, 40), (33, 128, 2, 2, 70), (5, 64, 3, 2, 33), (70, 301, 8, 3, 16)]
+
+
+@pytest.mark.parametrize("shape", HG_SHAPES, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in HG_SHAPES])
+def test_fused_h_gemm_tiles(fm, shape):
+    err = _nmf_case(fm, *shape, n_iter=2, seed=4)
     assert max(err.values()) < 2 * TOL, err
 
 
