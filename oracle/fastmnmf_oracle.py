@@ -18,6 +18,9 @@ and explicit Python loops for the iterative projection).  Each function cites th
 * MU of g~            Eq. 21;   MU of W and H   Eqs. 23-24
 * MU of lambda        Eq. 22 (unconstrained source model, Sec. III-B-1: FastFCA, Sec. III-C-1)
 * Wiener separation   x_ftn = Y_ftn Y_ft^-1 x_ft                          (Sec. II-A-1, Eq. 3)
+* front end           STFT with a 1024-point window and a 256-point shift, F = 513 (Sec. IV-A),
+                      its inverse by weighted overlap-add, and the initialisation of g~ and Q by
+                      spectral decomposition of the initial SCMs (Sec. IV-A)
 
 The spatial-model functions take lambda[f,t,n] itself (``*_lam``); the NMF source model forms
 it by Eq. 9 and calls them, the unconstrained model passes its own lambda.
@@ -460,3 +463,78 @@ def separate_direct_lam(X, lam, G, Q):
     Ysrc, Y = full_rank_covariances_lam(lam, G, Q)
     sol = np.linalg.solve(Y, X[..., None])[..., 0]                   # Y_ft^-1 x_ft
     return np.einsum("ftnij,ftj->nfti", Ysrc, sol, optimize=True)
+
+
+# ---------------------------------------------------------------------------
+# Front end (Sec. IV-A): the STFT of the paper's experiments (window of 1024 points, F = 513,
+# shift of 256 points), its inverse, and the initialisation of g~ and Q by spectral
+# decomposition.  The paper names neither the window nor the framing: a periodic Hann window,
+# frames starting at sample t * hop with zeros past the end, and synthesis with the same window
+# normalised by the overlap-added squared window are this library's reading.
+# ---------------------------------------------------------------------------
+def stft_frames(S: int, L: int = 1024, hop: int = 256) -> int:
+    """Number of frames of a signal of S samples: 1 + ceil((S - L) / hop), at least 1."""
+    return 1 if S <= L else 1 + -(-(S - L) // hop)
+
+
+def hann(L: int) -> np.ndarray:
+    """Periodic Hann window w_j = (1 - cos(2 pi j / L)) / 2."""
+    return 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(L) / L)
+
+
+def stft(x, L: int = 1024, hop: int = 256):
+    """X[f, t, m] = sum_j w_j x_m[t hop + j] exp(-2 pi i f j / L), f = 0..L/2 (x: [M, S] real;
+    samples past S are zero).  The DFT of each windowed frame is numpy's rfft."""
+    x = np.asarray(x, dtype=np.float64)
+    M, S = x.shape
+    T = stft_frames(S, L, hop)
+    pad = np.zeros((M, (T - 1) * hop + L))
+    pad[:, :S] = x
+    w = hann(L)
+    frames = np.stack([pad[:, t * hop:t * hop + L] * w for t in range(T)], axis=1)   # [M, T, L]
+    return np.fft.rfft(frames, axis=2).transpose(2, 1, 0)                              # [F, T, M]
+
+
+def istft(Y, S: int, L: int = 1024, hop: int = 256):
+    """Inverse of ``stft`` for a batch Y[b, f, t, m]: each frame's inverse real DFT (numpy's
+    irfft) times the window, overlap-added, divided by the overlap-added squared window
+    sum_t w_{s - t hop}^2 (samples where that sum is below 1e-10 of its largest value are
+    zero).  Returns y[b, m, s], s < S."""
+    Y = np.asarray(Y, dtype=np.complex128)
+    B, F, T, M = Y.shape
+    w = hann(L)
+    frames = np.fft.irfft(Y.transpose(0, 3, 2, 1), n=L, axis=3) * w                 # [B, M, T, L]
+    n_out = (T - 1) * hop + L
+    y = np.zeros((B, M, n_out))
+    den = np.zeros(n_out)
+    for t in range(T):
+        y[:, :, t * hop:t * hop + L] += frames[:, :, t]
+        den[t * hop:t * hop + L] += w * w
+    ok = den > 1e-10 * den.max()
+    y[:, :, ok] /= den[ok]
+    y[:, :, ~ok] = 0.0
+    return y[:, :, :S]
+
+
+def spectral_init(X, N: int):
+    """Initial g~ and Q by spectral decomposition (Sec. IV-A): G_1f = (1/T) sum_t x_ft x_ft^H
+    (the average observed SCM), G_nf = I for n >= 2; with G_1f = U_f Diag(e_f) U_f^H (numpy's
+    eigh, eigenvalues ordered largest first), Q_f = U_f^H jointly diagonalises every G_nf:
+    g~_1f = e_f and g~_nf = 1 (Q_f I Q_f^H = I).  Returns G[n, f, m] (before the nu
+    normalisation) and Q[f, m, j]."""
+    X = np.asarray(X, dtype=np.complex128)
+    F, T, M = X.shape
+    R = np.einsum("fti,ftj->fij", X, X.conj(), optimize=True) / T
+    e, U = np.linalg.eigh(R)                       # ascending
+    e, U = e[:, ::-1], U[:, :, ::-1]
+    Q = U.conj().transpose(0, 2, 1)                # rows = conjugated eigenvectors
+    G = np.ones((N, F, M))
+    G[0] = e
+    return G, Q
+
+
+def spectral_init_state(X, W, G, Q):
+    """The spectral initialisation with the library's nu normalisation: g~_nf /= sum_m g~_nfm
+    and w_nkf *= that sum (lambda g~ unchanged); Q_f is unitary, so phi_f = 1."""
+    nu = G.sum(axis=2)
+    return W * nu[:, None, :], G / nu[:, :, None], Q
