@@ -199,6 +199,46 @@ fmnmf_status fmnmf_set_lambda(fmnmf_ctx* ctx, const float* lam, const float* G, 
 fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, const float* G,
                              const void* Q);
 
+/*
+ * Spectral initialisation of g~ and Q (Sec. IV-A): the SCM of source 1 starts as the
+ * average observed SCM G_1f = (1/T) sum_t x_ft x_ft^H and the others as the identity; with
+ * G_1f = U_f Diag(e_f) U_f^H (eigenvalues in descending order), Q_f = U_f^H diagonalises
+ * them all: g~_1f = e_f, g~_nf = 1 for n >= 2.  The nu normalisation of fmnmf_iterate then
+ * divides g~_nf by its sum over m and multiplies w_nkf (lambda_ftn for the unconstrained
+ * source model) by it; H is kept.  The eigendecomposition runs on the device in float64
+ * (cyclic complex Jacobi rotations, one thread per bin); Q_f is unitary up to rounding.
+ * Like fmnmf_set_state it recomputes x~, y~ and the log-likelihood, clears the error word
+ * and makes this the state fmnmf_restart returns to.  A bin whose average SCM has no
+ * positive eigenvalue (no observed power) is reported as FMNMF_ESINGULAR.  Synchronises.
+ */
+fmnmf_status fmnmf_init_spectral(fmnmf_ctx* ctx);
+
+/*
+ * Front end: the STFT that produces X from multichannel signals and its inverse, which
+ * turns separated images back into signals (Sec. IV-A: window of L = 1024 points, shift
+ * of 256).  The paper names neither window nor framing; here w_j = (1 - cos(2 pi j/L))/2
+ * (periodic Hann), frame t covers samples t*hop .. t*hop + L - 1 (zeros past the end),
+ *   X[f][t][m] = sum_j w_j x_m[t*hop + j] exp(-2 pi i f j / L),  f = 0 .. L/2 (F = L/2+1),
+ * and the number of frames is T = 1 if S <= L, else 1 + ceil((S - L) / hop)
+ * (fmnmf_stft_frames).  The inverse takes each frame's inverse real DFT (the imaginary
+ * parts of bins 0 and L/2 are ignored), multiplies it by w, overlap-adds the frames and
+ * divides every sample by sum_t w_{s - t hop}^2; samples where that sum is below 1e-10 of
+ * its largest value are 0.
+ *  L     power of two in [16, 4096]; hop in [1, L]; S >= 1 samples.
+ *  x     device float32 [M][S] signals (4-byte aligned); X  device complex64 [F][T][M].
+ *  Y     device complex64 [B][F][T][M] (B batches of images, e.g. the [N][F][T][M] output
+ *        of fmnmf_separate); y device float32 [B][M][S]; (T - 1) * hop + L >= S.
+ *  stream  cudaStream_t for the work (NULL = legacy default stream); asynchronous.
+ * Computation in float32 (radix-2 FFT in shared memory; twiddles exact-argument sincospi).
+ * fmnmf_istft takes B*M*T*L*4 bytes of stream-ordered scratch (cudaMallocAsync) and
+ * returns FMNMF_ENOMEM if that fails.  Argument errors return FMNMF_EINVAL and launch
+ * nothing (message via fmnmf_last_error(NULL)).
+ */
+fmnmf_status fmnmf_stft_frames(int S, int L, int hop, int* T);
+fmnmf_status fmnmf_stft(const float* x, int M, int S, int L, int hop, void* X, void* stream);
+fmnmf_status fmnmf_istft(const void* Y, int B, int F, int T, int M, int S, int L, int hop, float* y,
+                         void* stream);
+
 /* Shapes of a context (any pointer may be NULL). */
 fmnmf_status fmnmf_shape(const fmnmf_ctx* ctx, int* F, int* T, int* M, int* N, int* K);
 

@@ -1329,6 +1329,22 @@ fmnmf_status fmnmf_set_state(fmnmf_ctx* ctx, const float* W, const float* H, con
   return check_status(ctx);
 }
 
+// Spectral initialisation (Sec. IV-A): g~ and Q from the eigendecomposition of the average
+// observed SCM (one float64 Jacobi solve per bin on the device), then the nu normalisation
+// with W (or lambda) scaled to match; H is kept.  Replaces the state like fmnmf_set_state.
+fmnmf_status fmnmf_init_spectral(fmnmf_ctx* ctx) {
+  if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  ctx->launches++;
+  CK(launch_spec_init(ctx->p, ctx->free_model ? ctx->lam : nullptr, ctx->st));
+  fmnmf_status s = check_status(ctx);
+  if (s != FMNMF_OK) return s;
+  if ((s = snapshot(ctx, false)) != FMNMF_OK) return s;
+  if ((s = refresh_state(ctx)) != FMNMF_OK) return s;
+  return check_status(ctx);
+}
+
 fmnmf_status fmnmf_shape(const fmnmf_ctx* ctx, int* F, int* T, int* M, int* N, int* K) {
   if (!ctx) return set_err(nullptr, FMNMF_EINVAL, "ctx is NULL");
   if (F) *F = ctx->F;

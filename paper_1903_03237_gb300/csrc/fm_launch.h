@@ -67,6 +67,8 @@ struct GemmArgs;
 cudaError_t launch_gemm(const GemmArgs& g, bool tf32, int nt, dim3 grid, cudaStream_t st);
 cudaError_t configure_gemm();
 cudaError_t launch_pr(int maxm, const Prob& p, float* PR, int mode, cudaStream_t st);
+// Spectral initialisation of g~ and Q (front end): writes G, Qx and scales W (or lambda).
+cudaError_t launch_spec_init(const Prob& p, float* lam, cudaStream_t st);
 // V_fm split sums on the tensor cores (and y~), grid (ceil(F / bins per CTA), S).
 // tl: tensor map of lambda from scm_tensor_map, or null (per-row copies or plain loads)
 cudaError_t launch_scm_tc(int maxm, const Prob& p, int S, int span, const CUtensorMap* tl, cudaStream_t st);

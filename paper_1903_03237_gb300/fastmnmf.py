@@ -40,7 +40,8 @@ EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "
            "fmnmf_batch_create", "fmnmf_batch_iterate", "fmnmf_batch_sync", "fmnmf_batch_destroy",
            "fmnmf_autotune", "fmnmf_batch_autotune", "fmnmf_get_tuning", "fmnmf_set_tuning",
            "fmnmf_footprint", "fmnmf_server_create", "fmnmf_server_submit", "fmnmf_server_poll",
-           "fmnmf_server_wait", "fmnmf_server_result", "fmnmf_server_stats", "fmnmf_server_destroy"]
+           "fmnmf_server_wait", "fmnmf_server_result", "fmnmf_server_stats", "fmnmf_server_destroy",
+           "fmnmf_init_spectral", "fmnmf_stft_frames", "fmnmf_stft", "fmnmf_istft"]
 
 
 class Opts(ctypes.Structure):
@@ -90,6 +91,10 @@ _sig = {
     "fmnmf_server_result": (_S, [_P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_double)]),
     "fmnmf_server_stats": (_S, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 4 + [ctypes.POINTER(ctypes.c_size_t)]),
     "fmnmf_server_destroy": (_S, [_P]),
+    "fmnmf_init_spectral": (_S, [_P]),
+    "fmnmf_stft_frames": (_S, [_I, _I, _I, ctypes.POINTER(_I)]),
+    "fmnmf_stft": (_S, [_P, _I, _I, _I, _I, _P, _P]),
+    "fmnmf_istft": (_S, [_P, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -249,6 +254,11 @@ class Context:
         assert Q.shape == (self.F, self.M, self.M)
         _check(_lib.fmnmf_set_lambda(self._ctx, lp, gp, qp), self._ctx)
 
+    def init_spectral(self):
+        """g~ and Q from the eigendecomposition of the average observed SCM (Sec. IV-A), nu
+        normalised with W (or lambda) scaled to match; H kept.  Becomes the restart state."""
+        _check(_lib.fmnmf_init_spectral(self._ctx), self._ctx)
+
     def set_state(self, W, H, G, Q):
         W, wp = _host_ptr(W, np.float32)
         H, hp = _host_ptr(H, np.float32)
@@ -337,6 +347,41 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def stft_frames(S: int, L: int = 1024, hop: int = 256) -> int:
+    """Frames of a signal of S samples: 1 if S <= L, else 1 + ceil((S - L) / hop)."""
+    T = ctypes.c_int()
+    _check(_lib.fmnmf_stft_frames(S, L, hop, ctypes.byref(T)))
+    return T.value
+
+
+def _cuda_stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def stft(x, L: int = 1024, hop: int = 256):
+    """STFT of device signals x (torch float32 CUDA tensor [M, S]) on torch's current stream:
+    X[f, t, m] (complex64 [L/2 + 1, T, M]) with a periodic Hann window, frames at t * hop."""
+    assert torch is not None and isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32
+    x = x.contiguous()
+    M, S = x.shape
+    T = stft_frames(S, L, hop)
+    X = torch.empty((L // 2 + 1, T, M), dtype=torch.complex64, device=x.device)
+    _check(_lib.fmnmf_stft(x.data_ptr(), M, S, L, hop, X.data_ptr(), _cuda_stream(x.device)))
+    return X
+
+
+def istft(Y, S: int, L: int = 1024, hop: int = 256):
+    """Inverse of ``stft`` for device images Y (torch complex64 CUDA [B, F, T, M] or [F, T, M])
+    on torch's current stream: y[B, M, S] float32 (weighted overlap-add)."""
+    assert torch is not None and isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.complex64
+    squeeze = Y.dim() == 3
+    Y = (Y[None] if squeeze else Y).contiguous()
+    B, F, T, M = Y.shape
+    y = torch.empty((B, M, S), dtype=torch.float32, device=Y.device)
+    _check(_lib.fmnmf_istft(Y.data_ptr(), B, F, T, M, S, L, hop, y.data_ptr(), _cuda_stream(Y.device)))
+    return y[0] if squeeze else y
 
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3

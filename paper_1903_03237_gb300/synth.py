@@ -75,6 +75,29 @@ def make_state(F: int, T: int, M: int, N: int, K: int, seed: int):
     return W, H, G, Q
 
 
+def make_signals(M: int, S: int, n_src: int, seed: int, taps: int = 64) -> np.ndarray:
+    """Seeded time-domain multichannel recordings for the front end (STFT, its inverse and
+    the spectral initialisation), float32 [M, S]: n_src sources, each white Gaussian noise
+    under a slowly varying nonnegative envelope (a bounded random walk, so the source power
+    changes over frames as a speech or noise source does), reach every microphone through
+    its own impulse response of ``taps`` samples (Gaussian taps under an exponential decay
+    of time constant taps / 4, like a short room response); plus white sensor noise of
+    1e-3 of the source level."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((M, S))
+    decay = np.exp(-np.arange(taps) / (taps / 4.0))
+    for _ in range(n_src):
+        steps = rng.standard_normal(S // 256 + 2) * 0.3
+        env = np.exp(np.clip(np.cumsum(steps), -3.0, 3.0))
+        env = np.repeat(env, 256)[:S]
+        src = rng.standard_normal(S) * env
+        for m in range(M):
+            h = rng.standard_normal(taps) * decay
+            x[m] += np.convolve(src, h)[:S]
+    x += 1e-3 * x.std() * rng.standard_normal((M, S))
+    return x.astype(np.float32)
+
+
 # Workload shapes (M channels, N sources, K bases, F bins, T frames, iterations).
 CONFIGS = {
     "c0": dict(M=2, N=2, K=8, F=257, T=200, iters=20, diffuse=0.0),

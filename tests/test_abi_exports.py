@@ -48,3 +48,27 @@ def test_host_side_argument_errors():
     assert lib.fmnmf_iterate(None, 1) == fm.EINVAL
     o = fm.default_opts()
     assert o.update_mask == 15 and o.normalise == 1 and o.precision == 0
+
+
+def test_front_end_host_side():
+    # frame count against the oracle's, and argument errors caught before any device call
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    from oracle import fastmnmf_oracle as O
+    for S, L, hop in [(1, 16, 1), (16, 16, 4), (17, 16, 4), (5000, 1024, 256), (1024, 1024, 256),
+                      (164608, 1024, 256), (777, 64, 16), (10, 4096, 4096)]:
+        assert fm.stft_frames(S, L, hop) == O.stft_frames(S, L, hop)
+    lib = fm.lib()
+    T = ctypes.c_int()
+    assert lib.fmnmf_stft_frames(100, 1000, 250, ctypes.byref(T)) == fm.EINVAL      # L not a power of two
+    assert lib.fmnmf_stft_frames(100, 8192, 256, ctypes.byref(T)) == fm.EINVAL      # L too large
+    assert lib.fmnmf_stft_frames(100, 1024, 0, ctypes.byref(T)) == fm.EINVAL
+    assert lib.fmnmf_stft_frames(100, 1024, 2048, ctypes.byref(T)) == fm.EINVAL     # hop > L
+    assert lib.fmnmf_stft_frames(0, 1024, 256, ctypes.byref(T)) == fm.EINVAL
+    assert lib.fmnmf_stft(None, 2, 100, 64, 16, None, None) == fm.EINVAL
+    assert lib.fmnmf_istft(None, 1, 33, 4, 2, 100, 64, 16, None, None) == fm.EINVAL  # NULL
+    assert lib.fmnmf_istft(None, 1, 32, 4, 2, 100, 64, 16, None, None) == fm.EINVAL  # F != L/2 + 1
+    assert b"F" in lib.fmnmf_last_error(None)
+    assert lib.fmnmf_istft(None, 1, 33, 4, 2, 200, 64, 16, None, None) == fm.EINVAL  # frames too short
+    assert lib.fmnmf_init_spectral(None) == fm.EINVAL
