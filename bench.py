@@ -219,17 +219,24 @@ def job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
     return units_per_rank * world / max_seconds
 
 
-def oracle_iteration_rate(mix, W, H, G, Q, n_iter: int):
-    """Times the float64 oracle (as it stands) on the host; returns (rate, cores, seconds)."""
+def oracle_iteration_rate(mix, W, H, G, Q, n_iter: int, min_seconds: float = 0.0, max_iter: int = 100):
+    """Times the float64 oracle (as it stands) on the host: n_iter iterations, continued in
+    runs of n_iter from the state reached until min_seconds have passed (at most max_iter);
+    returns (rate, cores, seconds, iterations)."""
     from oracle import fastmnmf_oracle as O
     X = mix.X.astype(np.complex128)
+    W, H, G, Q = W.astype(np.float64), H.astype(np.float64), G.astype(np.float64), Q.astype(np.complex128)
     c0, t0 = time.process_time(), time.perf_counter()
-    O.iterate(X, W.astype(np.float64), H.astype(np.float64), G.astype(np.float64), Q.astype(np.complex128),
-              n_iter=n_iter)
+    done = 0
+    while True:
+        W, H, G, Q, _ = O.iterate(X, W, H, G, Q, n_iter=n_iter)
+        done += n_iter
+        if time.perf_counter() - t0 >= min_seconds or done + n_iter > max_iter:
+            break
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
     F, T = X.shape[0], X.shape[1]
-    return F * T * n_iter / wall, max(1, int(math.ceil(cpu / wall - 0.05))), wall
+    return F * T * done / wall, max(1, int(math.ceil(cpu / wall - 0.05))), wall, done
 
 
 def run_reference(args):
@@ -244,7 +251,7 @@ def run_reference(args):
         oracle_iteration_rate(mix, W, H, G, Q, 1)
     rates, secs, cores = [], [], 1
     for _ in range(args.steps):
-        r, c, s = oracle_iteration_rate(mix, W, H, G, Q, 1)
+        r, c, s, _ = oracle_iteration_rate(mix, W, H, G, Q, 1)
         rates.append(r)
         secs.append(s)
         cores = max(cores, c)
@@ -434,10 +441,10 @@ def run_ours(args):
         Fs = F if F * T <= 513 * 640 else 96
         sub = type(mix)(X=mix.X[:Fs], W=None, H=None, G=None, Q=None, noisy_bins=None)
         W0, H0, G0, Q0 = make_state(Fs, T, M, N, K, 0)
-        nit = 2 if Fs == F else 1
-        r, cores, secs = oracle_iteration_rate(sub, W0, H0, G0, Q0, nit)
+        r, cores, secs, nit = oracle_iteration_rate(sub, W0, H0, G0, Q0, 2, min_seconds=10.0)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{nit} oracle iteration(s) of {Fs} of the {F} bins x {T} frames of the same mixture ({secs:.1f} s)"}
+               "sample": f"{nit} oracle iterations (runs of 2 until 10 s had passed) of {Fs} of the {F} bins x {T} "
+                         f"frames of the same mixture ({secs:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -458,6 +465,14 @@ def run_ours(args):
             line["serving"] = serving
         if "plain_fp32" in others:
             line["speedup_vs_plain_fp32"] = res["value"] / others["plain_fp32"]["value"]
+        # the whole iteration against HBM by the minimum traffic of one iteration with lambda,
+        # y~, A, B, P, R on chip (X read twice, x~ written once and read three times: 32 F T M
+        # bytes), over the step time per iteration (restart and Wiener filter included)
+        hbm = float((read_peaks() or {}).get("hbm_gbs", 6800.0))
+        it_us = 1e3 * res["ms_per_step"] / iters
+        it_gbs = 32.0 * F * T * M / (it_us * 1e-6) / 1e9
+        line["iteration_hbm_equiv"] = {"bytes_per_iteration": 32 * F * T * M, "us_per_iteration": it_us,
+                                       "achieved_gbs": it_gbs, "peak_gbs": hbm, "frac": it_gbs / hbm}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -614,7 +629,7 @@ def run_serving(args):
 
 
 def profile_run(args):
-    """A short run of the same workload for ncu captures: context, 2 iterations, separation
+    """A short run of the same workload for ncu captures: context, 3 iterations, separation
     (``--bins`` overrides F to keep the device footprint of a capture small)."""
     import torch
     from paper_1903_03237_gb300.build import build
@@ -626,7 +641,7 @@ def profile_run(args):
     mix = make_mixture(F, w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
     with fm.Context(mix.X, w["N"], w["K"], seed=0, precision=PRECISIONS[FORMS[args.form][0]],
                     schedule=FORMS[args.form][1]) as ctx:
-        ctx.iterate(2)
+        ctx.iterate(3)
         ctx.separate()
         print("profile run ok, log-likelihood", ctx.loglik())
 

@@ -222,6 +222,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
   __shared__ double llred_s[kThreads / 32];
   const int f = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the warp index as a value the compiler knows to be warp-uniform: branches on it are not
+  // treated as divergent, so the shuffle-heavy single-warp stretches (Gauss-Jordan, IP row
+  // sweep, phi normalisation) need no reconvergence handling.  In a build with clock64
+  // stamps at the phase boundaries the row sweep took four to five times longer with the
+  // plain index; in this kernel the launch time is the same either way (the other CTAs on
+  // the SM fill the issue slots the single warp leaves).
+  const int warp_u = __shfl_sync(0xffffffffu, warp, 0);
   const int F = p.F, T = p.T, M = p.M, N = p.N, K = p.K;
   if (f >= F) return;
   const BinSmem L = bin_smem(N, K, MAXM);
@@ -449,12 +456,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
       vlo_s[m][(ee / M) * MAXM + ee % M] = s.lo;
     }
     __syncthreads();
-    if (warp < M) {
-      const bool ok = gj_inverse<MAXM>(vsum_s[warp], A_s[warp], M, lane, vlo_s[warp]);
+    if (warp_u < M) {
+      const bool ok = gj_inverse<MAXM>(vsum_s[warp_u], A_s[warp_u], M, lane, vlo_s[warp_u]);
       if (!ok && lane == 0) bad_s = 1;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp_u == 0) {
       int bad = 0;
       const df ld_add = ip_rows<MAXM>(A_s, Q_s, Qi_s, M, df_make((float)T), lane, bad);
       if (lane == 0) {
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
         Qi_s[r * MAXM + c] = p.Qix[(size_t)f * M * M + e];
       }
     __syncthreads();
-    if (warp == 0) {
+    if (warp_u == 0) {
       df ph = df_make(1.f), sq = df_make(1.f), isq = df_make(1.f);
       if (flags & FU_NORM) {
         df tr = df{0.f, 0.f};

@@ -810,8 +810,8 @@ __device__ __forceinline__ bool gj_inverse(const float* v, float4* A, int M, int
 //   r = 1/sqrt(s),  row m of Q_f <- (q r)^H,
 //   Q_f^-1 <- Q_f^-1 - c (r u~ - e_m^T) r       (Sherman-Morrison),  log|det Q_f|^2 += log s.
 // Entries outside M x M are zero and stay zero.  Q_f^-1 goes back to Qi_s at the end;
-// returns the sum of log s in float-float (lane 0), sets bad when some s is not positive
-// and finite.
+// returns the sum of log s in float-float (on every lane), sets bad when some s is not
+// positive and finite.
 template <int MAXM>
 __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q_s, float4* Qi_s, int M,
                                       df Tdf, int lane, int& bad) {
@@ -828,7 +828,7 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
     ok[r] = lane < MM && i < M && j < M;
     qi[r] = ok[r] ? cdf_unpack(Qi_s[i * MAXM + j]) : cdf_zero();
   }
-  df ld_add = df{0.f, 0.f};
+  df s_row = df_make(1.f);  // lane m keeps s of row m (its log is taken after the sweep)
   for (int m = 0; m < M; ++m) {
     cdf v[R];
 #pragma unroll
@@ -866,7 +866,7 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
     df sv = a;
     if (!(sv.hi > 0.f) || !isfinite(sv.hi)) { bad = 1; sv = df_make(1.f); }
     const df rs = df_rsqrt(sv);
-    if (lane == 0) ld_add = df_add(ld_add, df_logf(sv));
+    if (lane == m) s_row = sv;
     if (j == 0)
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -879,6 +879,10 @@ __device__ __forceinline__ df ip_rows(const float4 (*Vi)[MAXM * MAXM], float4* Q
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (ok[r]) Qi_s[(i0 + r * IG) * MAXM + j] = cdf_pack(qi[r]);
+  // the M logs in parallel (lanes >= M hold log 1 = 0), added in row order on every lane
+  const df lg = df_logf(s_row);
+  df ld_add = df{0.f, 0.f};
+  for (int m = 0; m < M; ++m) ld_add = df_add(ld_add, shfl_df(lg, m));
   return ld_add;
 }
 
@@ -902,6 +906,9 @@ __global__ void __launch_bounds__(32 * MAXM, 32 / MAXM) k_ip(Prob p, int S, int 
   __shared__ int bad_s;
   const int f = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // warp index the compiler knows to be warp-uniform (branches on it need no reconvergence
+  // handling around the shuffles of the single-warp stretches)
+  const int warp_u = __shfl_sync(0xffffffffu, warp, 0);
   const int M = p.M, N = p.N, K = p.K, F = p.F;
   if (f >= F) return;
   // prefetch buffers: X row [T*M] complex, y~ row [T*M], g~ [N][M], W [N][K]
@@ -943,12 +950,12 @@ __global__ void __launch_bounds__(32 * MAXM, 32 / MAXM) k_ip(Prob p, int S, int 
     for (int e = tid; e < M * MM; e += blockDim.x)
       vsum_s[e / MM][e % MM] = sum_splits(p.part + (size_t)f * M * MM + e, psz, S);
     __syncthreads();
-    if (warp < M) {
-      const bool ok = gj_inverse<MAXM>(vsum_s[warp], A_s[warp], M, lane);
+    if (warp_u < M) {
+      const bool ok = gj_inverse<MAXM>(vsum_s[warp_u], A_s[warp_u], M, lane);
       if (!ok && lane == 0) bad_s = 1;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp_u == 0) {
       int bad = 0;
       const df ld_add = ip_rows<MAXM>(A_s, Q_s, Qi_s, M, df_make((float)p.T), lane, bad);
       if (lane == 0) {
@@ -964,7 +971,7 @@ __global__ void __launch_bounds__(32 * MAXM, 32 / MAXM) k_ip(Prob p, int S, int 
   __shared__ float phi_s;
   __shared__ float nu_s[64];
   __shared__ float2 qf_s[MM];  // the normalised Q_f in float32 (x~ of this bin's frames)
-  if (warp == 0) {
+  if (warp_u == 0) {
     df ph = df_make(1.f), sq = df_make(1.f), isq = df_make(1.f);
     if (flags & FLAG_NORMALISE) {
       df tr = df{0.f, 0.f};
