@@ -82,7 +82,8 @@ enum { FMNMF_PREC_FP32 = 0, FMNMF_PREC_BF16 = 1, FMNMF_PREC_TF32 = 2 };
  *         is independent per frequency bin, so one kernel runs, per bin, the g~ update, V_fm
  *         and the IP update, the normalisation, x~, the bin's log-likelihood terms and the W
  *         update of the next iteration; a second kernel runs the H update over tiles of
- *         frames and refreshes lambda.  Needs N*K <= 256 and N*M <= 256.
+ *         frames and refreshes lambda.  Needs N*M <= 256 and the bin's tiles (about
+ *         4 (N*K + 260 N + 1030 MAXM) bytes, MAXM the channel bucket 2, 4 or 8) within shared memory.
  *  AUTO:  FUSED when it applies, else SWEEP.  The mixed-precision forms ignore the field. */
 enum { FMNMF_SCHED_AUTO = 0, FMNMF_SCHED_SWEEP = 1, FMNMF_SCHED_FUSED = 2 };
 

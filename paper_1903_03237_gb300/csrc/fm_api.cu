@@ -370,15 +370,15 @@ fmnmf_status plan(fmnmf_ctx* ctx) {
     // memory allow; the unconstrained source model runs only there
     const int Kf = ctx->free_model ? 1 : K;
     const size_t bsm = (size_t)bin_smem(N, Kf, mx).total * 4;
-    bool ok = !ctx->mixed && N * Kf <= kFuMaxPairs && N * M <= kFuMaxPairs && bsm <= (size_t)kSmemMax;
+    bool ok = !ctx->mixed && N * M <= kFuMaxNM && bsm <= (size_t)kSmemMax;
     // H GEMM: kHgS bin splits, one thread-block cluster per tile
     const int sched = ctx->opts.schedule;
     if (ctx->free_model && !ok)
       return set_err(ctx, FMNMF_EINVAL, "the unconstrained source model needs the fused FP32 schedule (N*M <= %d)",
-                     kFuMaxPairs);
+                     kFuMaxNM);
     if (sched == FMNMF_SCHED_FUSED && !ok)
-      return set_err(ctx, FMNMF_EINVAL, "fused schedule not available for this shape/precision (FP32, N*K and N*M <= %d)",
-                     kFuMaxPairs);
+      return set_err(ctx, FMNMF_EINVAL, "fused schedule not available for this shape/precision (FP32, N*M <= %d, "
+                     "per-bin tiles within shared memory)", kFuMaxNM);
     ctx->fused = ok && (ctx->free_model || sched != FMNMF_SCHED_SWEEP);
     if (ctx->fused) {
       ctx->binSm = bsm;

@@ -47,7 +47,7 @@ enum : int {
 constexpr int kFuTC = 256;          // frames per chunk of k_bin (one per thread)
 constexpr int kFuTCP = kFuTC + 1;   // padded chunk row: rows of different sources / channels
                                     // fall on different banks
-constexpr int kFuMaxPairs = 256;    // N*K and N*M limits of the fused schedule
+constexpr int kFuMaxNM = 256;       // N*M limit of the fused schedule (the g~ sums: one thread per pair)
 
 // Dynamic shared memory of k_bin, in floats.
 struct BinSmem {

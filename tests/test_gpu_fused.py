@@ -75,6 +75,31 @@ def test_fused_h_gemm_tiles(fm, shape):
     assert max(err.values()) < 2 * TOL, err
 
 
+# N*K above 256 (the W sums loop over bases in passes of 64 per warp; the H GEMM tiles K by
+# 32): the large mixture's source shape (M8 N6 K64) on small F, T, and K beyond 128
+LARGE_NK_SHAPES = [(20, 130, 8, 6, 64), (33, 301, 4, 5, 100), (17, 64, 2, 3, 130), (9, 257, 6, 8, 40)]
+
+
+@pytest.mark.parametrize("shape", LARGE_NK_SHAPES, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in LARGE_NK_SHAPES])
+def test_fused_many_bases(fm, shape):
+    err = _nmf_case(fm, *shape, n_iter=2, seed=6)
+    assert max(err.values()) < 2 * TOL, err
+
+
+def test_fused_pair_limit(fm):
+    # N*M above 256: the fused schedule is refused when asked for and not chosen otherwise
+    mix = make_mixture(5, 20, 8, 33, 2, 1)
+    with pytest.raises(fm.FastMNMFError) as ei:
+        fm.Context(mix.X, 33, 2, seed=1, schedule=fm.SCHED_FUSED)
+    assert ei.value.status == fm.EINVAL
+    ctx = fm.Context(mix.X, 33, 2, seed=1)
+    ctx.set_timing(True)
+    ctx.iterate(1)
+    kt = ctx.kernel_times()
+    assert kt["bin"][1] == 0 and kt["w_update"][1] > 0      # the sweep schedule ran
+    assert np.isfinite(ctx.loglik())
+
+
 @pytest.mark.parametrize("mask", [O.UPDATE_W, O.UPDATE_H, O.UPDATE_G, O.UPDATE_Q, O.UPDATE_W | O.UPDATE_H,
                                   O.UPDATE_G | O.UPDATE_Q], ids=["W", "H", "G", "Q", "WH", "GQ"])
 @pytest.mark.parametrize("normalise", [False, True], ids=["raw", "norm"])
