@@ -684,27 +684,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
 //   num[k][t] = sum_f w_nkf P_nft,   den[k][t] = sum_f w_nkf R_nft,
 // with P, R (the H update's per-point factors, from the lambda of the new W) written by the
 // bins' kernel.  A tile is 32 bases x 64 frames of one source; its bins are split over the
-// kHgS CTAs of one thread-block cluster, each summing its bins in chunks of 72 (thread
-// (ty, tx) owns bases 2ty, 2ty+1 and frames 4tx..4tx+3: per bin one 8-byte W load and two
-// 16-byte P, R loads feed 16 FMAs).  The CTAs leave their partial tiles in shared memory;
-// after a cluster barrier CTA r adds rows 4r..4r+3 of all of them, in rank order, through
-// distributed shared memory and applies h <- h sqrt(num/den); a second cluster barrier
-// keeps every partial tile alive until it has been read.
+// S CTAs of one thread-block cluster (S set at launch: even, at most 8, the grid within about
+// two CTAs per SM), each summing its bins in chunks of 32 with two chunks in flight
+// (cp.async into alternating buffers, so the next chunk's loads overlap this chunk's FMAs;
+// thread (ty, tx) owns bases 2ty, 2ty+1 and frames 4tx..4tx+3: per bin one 8-byte W load and
+// two 16-byte P, R loads feed 16 FMAs).  The CTAs leave their partial tiles in shared memory;
+// after a cluster barrier CTA r adds rows r, r + S, ... of all of them, in rank order,
+// through distributed shared memory and applies h <- h sqrt(num/den); a second cluster
+// barrier keeps every partial tile alive until it has been read.
 // ---------------------------------------------------------------------------------------
-constexpr int kHgKT = 32, kHgTT = 64, kHgFC = 72;  // bins per chunk: 1/8 of 513-576 bins in one
-constexpr int kHgS = 8;           // bin splits = CTAs per cluster
+constexpr int kHgKT = 32, kHgTT = 64, kHgFC = 32;  // tile bases, tile frames, bins per chunk
+constexpr int kHgMaxS = 8;        // bin splits = CTAs per cluster (the portable cluster size)
 constexpr int kHgWS = kHgKT + 2;  // W chunk row (even, for 8-byte loads)
 
 template <int MAXM>  // one instance per channel-bucket translation unit (MAXM is not used)
-__global__ void __cluster_dims__(1, 1, kHgS) __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restrict__ PR,
-                                                                               int span) {
-  __shared__ __align__(16) float Ws[kHgFC][kHgWS];
-  __shared__ __align__(16) float Ps[kHgFC][kHgTT];  // P chunk, then this CTA's num tile (rows < 32)
-  __shared__ __align__(16) float Rs[kHgFC][kHgTT];  // R chunk, then this CTA's den tile
+__global__ void __launch_bounds__(kThreads) k_hgemm(Prob p, const float* __restrict__ PR, int span) {
+  __shared__ __align__(16) float Ws[2][kHgFC][kHgWS];
+  __shared__ __align__(16) float Ps[2][kHgFC][kHgTT];  // P chunks; buffer 0 then this CTA's num tile
+  __shared__ __align__(16) float Rs[2][kHgFC][kHgTT];  // R chunks; buffer 0 then this CTA's den tile
+  static_assert(kHgFC >= kHgKT, "buffer 0 must hold a 32-row partial tile");
   cg::cluster_group cluster = cg::this_cluster();
+  const int S = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
   const int F = p.F, T = p.T, N = p.N, K = p.K;
-  const int n = blockIdx.z / kHgS, s = (int)cluster.block_rank();
+  const int n = blockIdx.z / S, s = (int)cluster.block_rank();
   const int k0 = blockIdx.y * kHgKT, t0 = blockIdx.x * kHgTT;
   const int fbeg = min(F, s * span), fend = min(F, fbeg + span);
   const size_t FT = (size_t)F * T;
@@ -717,25 +720,23 @@ __global__ void __cluster_dims__(1, 1, kHgS) __launch_bounds__(kThreads) k_hgemm
     for (int b = 0; b < 4; ++b) { num[a][b] = 0.f; den[a][b] = 0.f; }
   const float* __restrict__ Pn = PR + (size_t)n * FT;
   const float* __restrict__ Rn = PR + (size_t)(N + n) * FT;
-  for (int f0 = fbeg; f0 < fend; f0 += kHgFC) {
-    const int fc = min(kHgFC, fend - f0);
-    __syncthreads();  // the previous chunk's readers are done
-    // every copy of the chunk in flight at once (cp.async; zero fill outside the tile)
+  // the copies of one chunk into buffer b, as one cp.async group (zero fill outside the tile)
+  auto load = [&](int f0, int fc, int b) {
     for (int e = tid; e < kHgFC * kHgKT; e += kThreads) {
       const int kk = e / kHgFC, ff = e % kHgFC;
       const bool ok = ff < fc && k0 + kk < K;
-      cpa4(&Ws[ff][kk], p.W + (ok ? ((size_t)n * K + k0 + kk) * F + f0 + ff : 0), ok);
+      cpa4(&Ws[b][ff][kk], p.W + (ok ? ((size_t)n * K + k0 + kk) * F + f0 + ff : 0), ok);
     }
     if (vecT) {
       for (int e = tid; e < kHgFC * kHgTT / 4; e += kThreads) {
         const int ff = e / (kHgTT / 4), q = (e % (kHgTT / 4)) * 4;
         if (ff < fc && t0 + q < T) {
           const size_t o = (size_t)(f0 + ff) * T + t0 + q;
-          cpa16(&Ps[ff][q], Pn + o);
-          cpa16(&Rs[ff][q], Rn + o);
+          cpa16(&Ps[b][ff][q], Pn + o);
+          cpa16(&Rs[b][ff][q], Rn + o);
         } else {
-          *reinterpret_cast<float4*>(&Ps[ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(&Rs[ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(&Ps[b][ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(&Rs[b][ff][q]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     } else {
@@ -743,52 +744,69 @@ __global__ void __cluster_dims__(1, 1, kHgS) __launch_bounds__(kThreads) k_hgemm
         const int ff = e / kHgTT, q = e % kHgTT;
         const bool ok = ff < fc && t0 + q < T;
         const size_t o = ok ? (size_t)(f0 + ff) * T + t0 + q : 0;
-        cpa4(&Ps[ff][q], Pn + o, ok);
-        cpa4(&Rs[ff][q], Rn + o, ok);
+        cpa4(&Ps[b][ff][q], Pn + o, ok);
+        cpa4(&Rs[b][ff][q], Rn + o, ok);
       }
     }
-    cpa_wait_all();
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  const int nch = (fend - fbeg + kHgFC - 1) / kHgFC;
+  if (nch > 0) load(fbeg, min(kHgFC, fend - fbeg), 0);
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    const int f0 = fbeg + c * kHgFC, fc = min(kHgFC, fend - f0);
+    if (c + 1 < nch) {
+      load(f0 + kHgFC, min(kHgFC, fend - f0 - kHgFC), b ^ 1);  // buffer b^1 was released below
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // chunk c visible to every thread
 #pragma unroll 4
     for (int ff = 0; ff < fc; ++ff) {
-      const float2 w = *reinterpret_cast<const float2*>(&Ws[ff][2 * ty]);
-      const float4 pv = *reinterpret_cast<const float4*>(&Ps[ff][4 * tx]);
-      const float4 rv = *reinterpret_cast<const float4*>(&Rs[ff][4 * tx]);
+      const float2 w = *reinterpret_cast<const float2*>(&Ws[b][ff][2 * ty]);
+      const float4 pv = *reinterpret_cast<const float4*>(&Ps[b][ff][4 * tx]);
+      const float4 rv = *reinterpret_cast<const float4*>(&Rs[b][ff][4 * tx]);
       const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, ra[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        num[0][b] = fmaf(w.x, pa[b], num[0][b]);
-        num[1][b] = fmaf(w.y, pa[b], num[1][b]);
-        den[0][b] = fmaf(w.x, ra[b], den[0][b]);
-        den[1][b] = fmaf(w.y, ra[b], den[1][b]);
+      for (int q = 0; q < 4; ++q) {
+        num[0][q] = fmaf(w.x, pa[q], num[0][q]);
+        num[1][q] = fmaf(w.y, pa[q], num[1][q]);
+        den[0][q] = fmaf(w.x, ra[q], den[0][q]);
+        den[1][q] = fmaf(w.y, ra[q], den[1][q]);
       }
     }
+    __syncthreads();  // buffer b is read: the load two chunks on may overwrite it
   }
-  // this CTA's partial tiles into its shared memory (row = base within the tile)
-  __syncthreads();
+  // this CTA's partial tiles into buffer 0 (row = base within the tile)
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    *reinterpret_cast<float4*>(&Ps[2 * ty + a][4 * tx]) = make_float4(num[a][0], num[a][1], num[a][2], num[a][3]);
-    *reinterpret_cast<float4*>(&Rs[2 * ty + a][4 * tx]) = make_float4(den[a][0], den[a][1], den[a][2], den[a][3]);
+    *reinterpret_cast<float4*>(&Ps[0][2 * ty + a][4 * tx]) = make_float4(num[a][0], num[a][1], num[a][2], num[a][3]);
+    *reinterpret_cast<float4*>(&Rs[0][2 * ty + a][4 * tx]) = make_float4(den[a][0], den[a][1], den[a][2], den[a][3]);
   }
   cluster.sync();
   {
-    // rows 4s..4s+3 of the tile: one (base, frame) per thread, the splits added in rank order
-    const int kk = 4 * s + tid / kHgTT, tt = tid % kHgTT;
-    float sn = 0.f, sd = 0.f;
+    // rows s, s + S, ... of the tile: one (base, frame) per thread and pass, the splits added
+    // in rank order
+    const int tt = tid % kHgTT;
+    for (int kk = s + (tid / kHgTT) * S; kk < kHgKT; kk += (kThreads / kHgTT) * S) {
+      float sn = 0.f, sd = 0.f;
 #pragma unroll
-    for (int q = 0; q < kHgS; ++q) {
-      const float* rp = cluster.map_shared_rank(&Ps[0][0], q);
-      const float* rr = cluster.map_shared_rank(&Rs[0][0], q);
-      sn += rp[kk * kHgTT + tt];
-      sd += rr[kk * kHgTT + tt];
-    }
-    const int k = k0 + kk, t = t0 + tt;
-    if (k < K && t < T) {
-      const size_t i = ((size_t)n * K + k) * T + t;
-      const float h = p.H[i] * sqrtf(sn / sd);
-      if (!isfinite(h)) flag(p.status, ST_NONFINITE);
-      p.H[i] = h;
+      for (int q = 0; q < kHgMaxS; ++q) {
+        if (q < S) {
+          const float* rp = cluster.map_shared_rank(&Ps[0][0][0], q);
+          const float* rr = cluster.map_shared_rank(&Rs[0][0][0], q);
+          sn += rp[kk * kHgTT + tt];
+          sd += rr[kk * kHgTT + tt];
+        }
+      }
+      const int k = k0 + kk, t = t0 + tt;
+      if (k < K && t < T) {
+        const size_t i = ((size_t)n * K + k) * T + t;
+        const float h = p.H[i] * sqrtf(sn / sd);
+        if (!isfinite(h)) flag(p.status, ST_NONFINITE);
+        p.H[i] = h;
+      }
     }
   }
   cluster.sync();  // the other CTAs may still be reading this CTA's tiles

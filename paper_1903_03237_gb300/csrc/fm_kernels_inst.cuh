@@ -24,7 +24,22 @@ cudaError_t FM_CAT(launch_m, FM_MAXM)(KernelKind k, const LaunchArgs& a) {
       k_ip<MX><<<a.grid, MX * 32, a.smem, a.st>>>(a.p, a.S, a.flags, a.xt_mode, a.ctr, a.smem > 0 ? 1 : 0, a.pr, a.ll_tail);
       break;
     case KK_BIN: k_bin<MX><<<a.grid, kThreads, a.smem, a.st>>>(a.p, a.lam, a.pr, a.flags); break;
-    case KK_HGEMM: k_hgemm<MX><<<a.grid, kThreads, 0, a.st>>>(a.p, a.pr, a.g.span); break;
+    case KK_HGEMM: {
+      // cluster of a.g.S CTAs along z (the bin splits of one tile), set at launch
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = a.grid;
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = a.st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = (unsigned)a.g.S;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_hgemm<MX>, a.p, (const float*)a.pr, a.g.span);
+    }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

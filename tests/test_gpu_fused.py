@@ -65,8 +65,11 @@ def test_fused_iterations_match_oracle(fm, shape, n_iter):
 
 
 # several base tiles of the H GEMM (K > 32), frames not a multiple of 4 (scalar paths) or of
-# the 64-frame tile, fewer bins than splits
-HG_SHAPES = [(70, 303, 4, 3, 40), (33, 128, 2, 2, 70), (5, 64, 3, 2, 33), (70, 301, 8, 3, 16)]
+# the 64-frame tile, fewer bins than splits; the split counts 8 (few tiles), 6 (40 tiles, the
+# paper-scale source shape), 2 (80 tiles) and 1 (396 tiles: one CTA per tile, no cluster
+# partners), with bins left over in the last chunk of 32
+HG_SHAPES = [(70, 303, 4, 3, 40), (33, 128, 2, 2, 70), (5, 64, 3, 2, 33), (70, 301, 8, 3, 16),
+             (100, 640, 4, 4, 32), (71, 1280, 4, 4, 32), (40, 2049, 2, 6, 40)]
 
 
 @pytest.mark.parametrize("shape", HG_SHAPES, ids=[f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}" for s in HG_SHAPES])
