@@ -323,12 +323,10 @@ def _measure(fm, torch, mix, args, form, steps, warmup, rank, world, local, samp
     dom = max((k for k in cal if cal[k][1] > 0), key=lambda k: cal[k][0])
     shares = {k: round(v[0] / max(1e-12, sum(x[0] for x in cal.values())), 4) for k, v in cal.items() if v[1]}
     avg_all = {k: round(1e3 * v[0] / v[1], 2) for k, v in cal.items() if v[1]}
-    # the timed region brackets the dominant kernel's launches only
-    ctx.set_timing([dom])
-    for _ in range(warmup):  # capture that graph variant before the timed region
+    ctx.set_timing(False)
+    for _ in range(warmup):  # the graph variant without timing events
         step()
     ctx.sync()
-    ctx.kernel_times()
     dev_id = None
     try:
         dev_id = str(torch.cuda.get_device_properties(local).uuid)
@@ -336,6 +334,15 @@ def _measure(fm, torch, mix, args, form, steps, warmup, rank, world, local, samp
     except Exception:
         dev_id = None
 
+    def timed_steps(evs):
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+
+    # value: the steps as a user runs them (no events between the library's kernels)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = ctx.launch_count()
     if world > 1:
@@ -345,26 +352,34 @@ def _measure(fm, torch, mix, args, form, steps, warmup, rank, world, local, samp
         # NVTX range "timed" (main form only): lets ncu capture exactly the timed launches
         if sample_clocks:
             torch.cuda.nvtx.range_push("timed")
-        for i in range(steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(i))
-            evs[i][0].record(stream)
-            step()
-            evs[i][1].record(stream)
+        timed_steps(evs)
         torch.cuda.synchronize()
         if sample_clocks:
             torch.cuda.nvtx.range_pop()
     ctx.sync()
     launches = ctx.launch_count() - launches0
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    kt = ctx.kernel_times()
     total_ms = reduce_max(total_ms, "cuda")
     value = job_rate(F * T * iters * steps, world, total_ms / 1e3)
 
-    # roofline of the dominant kernel, from its launches inside the timed region
+    # roofline of the dominant kernel: the same steps again, each of its launches bracketed by
+    # events on the context stream (event nodes inside the captured graph)
+    ctx.set_timing([dom])
+    for _ in range(warmup):  # capture that graph variant first
+        step()
+    ctx.sync()
+    ctx.kernel_times()
+    evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    timed_steps(evs2)
+    torch.cuda.synchronize()
+    ctx.sync()
+    kt = ctx.kernel_times()
+    bracketed_ms = sum(a.elapsed_time(b) for a, b in evs2) / steps
     avg_ms = kt[dom][0] / kt[dom][1]
     roofline = roofline_for(dom, avg_ms, form, F, T, M, N, K, args.workload)
     roofline["launches_timed"] = kt[dom][1]
+    roofline["ms_per_step_with_kernel_events"] = bracketed_ms
 
     # end to end through the C ABI with host buffers: H2D mixture, iterations, D2H images
     ctx.set_timing(False)
