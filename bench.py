@@ -269,12 +269,12 @@ def run_reference(args):
     }), flush=True)
 
 
-def _config(form="fused"):
+def _config(form="bf16"):
     w = WORKLOAD
     prec = {"fused": "FP32, bin-fused schedule (two launches per iteration), float-float IP solve",
             "sweep": "FP32, one tiled launch per block (plain form), float-float IP solve",
-            "bf16": "mixed: BF16 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
-                    "and g~ sums, FP32 accumulation, float-float IP solve",
+            "bf16": "mixed: split-BF16 (hi + lo, three MMAs) tcgen05 contractions for lambda, the W/H sums, V_fm "
+                    "and the g~ sums, FP32 accumulation in TMEM, float-float IP solve",
             "tf32": "mixed: TF32 tensor-core GEMMs for lambda and the W/H sums, split-BF16 tensor-core V_fm "
                     "and g~ sums, FP32 accumulation, float-float IP solve"}[form]
     name = "paper-scale single mixture" if WORKLOAD is WORKLOADS["c1"] else "large mixture"
@@ -426,7 +426,7 @@ def run_ours(args):
     # workload, for the comparison the metric names
     others = {}
     if not args.no_compare:
-        for name, form in (("plain_fp32", "sweep"), ("mixed_bf16", "bf16")):
+        for name, form in (("plain_fp32", "sweep"), ("fused_fp32", "fused"), ("mixed_bf16", "bf16")):
             if form == args.form:
                 continue
             psteps = max(2, min(args.steps, 3))
@@ -677,8 +677,9 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0,
                     help="c4: arrival rate in requests/s (the same arrival pattern, rescaled); 0 = all at once")
     ap.add_argument("--instances", type=int, default=64, help="c3: number of mixtures")
-    ap.add_argument("--form", choices=sorted(FORMS), default="fused",
-                    help="form to time: fused (default: FP32, bin-fused schedule), sweep (plain FP32), bf16, tf32")
+    ap.add_argument("--form", choices=sorted(FORMS), default="bf16",
+                    help="form to time: bf16 (default: split-BF16 tensor-core contractions), fused (FP32, bin-fused "
+                         "schedule), sweep (plain FP32), tf32")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planned launch shapes (no tuner run)")
     ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving replay of the default run")

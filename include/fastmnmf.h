@@ -65,7 +65,10 @@ enum { FMNMF_UPDATE_W = 1, FMNMF_UPDATE_H = 2, FMNMF_UPDATE_G = 4, FMNMF_UPDATE_
        FMNMF_UPDATE_ALL = 15 };
 
 /* Arithmetic of the contractions.  FP32: every sum in float32 on CUDA cores.  BF16 / TF32:
- * the NMF and SCM contractions on the tensor cores with float32 accumulation.  In every form
+ * the NMF and SCM contractions on the tensor cores with float32 accumulation; BF16 splits
+ * every operand into BF16 hi and lo parts and takes each product as hi*hi + hi*lo + lo*hi
+ * (about 16 significant bits per operand), TF32 rounds the NMF operands to TF32 (11 bits) and
+ * splits the SCM operands like BF16.  In every form
  * the M x M IP solves (Eqs. 19-20), their normalisation and log|det Q_f|^2 run in float-float
  * arithmetic (an unevaluated sum of two float32 values, about 48 significand bits) on the
  * FP32 pipes, not in float64: GB300's float64 rate is a small fraction of its float32 rate.

@@ -1219,10 +1219,11 @@ fmnmf_status fmnmf_separate(fmnmf_ctx* ctx, void* out, int out_on_device) {
   a.p = ctx->p; a.g = ctx->gS; a.smem = ctx->smS; a.st = ctx->st; a.out = dst;
   if (ctx->mixed) {
     // lambda of the current W and H (the normalisation rescaled W after the last GEMM),
-    // with TF32 operands in either mixed form: the images scale with lambda directly
+    // with split-BF16 operands (about 16 significant bits) in either mixed form: the images
+    // scale with lambda directly
     cudaError_t el = rec.run_fn(KK_GL, [&] {
       ctx->launches++;
-      return launch_gemm(ctx->gpL.g, true, ctx->gpL.nt, ctx->gpL.grid, ctx->st);
+      return launch_gemm(ctx->gpL.g, false, ctx->gpL.nt, ctx->gpL.grid, ctx->st);
     });
     if (el != cudaSuccess) {
       if (tmp) cudaFreeAsync(tmp, ctx->st);

@@ -5,7 +5,10 @@
 // A and B are read from global memory (float32) through arbitrary element strides, rounded
 // to the MMA operand type and staged by the CTA's threads into shared memory in the
 // K-major core-matrix layout (k-groups outermost); a transposed source is therefore as
-// cheap as a contiguous one.  The epilogue goes through shared memory so that every store
+// cheap as a contiguous one.  BF16 operands are split: v = hi + lo with hi = bf16(v) and
+// lo = bf16(v - hi), and each product is taken as hi*hi + hi*lo + lo*hi (three MMAs into
+// the same accumulator; the lo*lo term is below 2^-16 of the product), which carries about
+// 16 significant bits of each operand; the two tiles take the bytes one TF32 tile takes.  The epilogue goes through shared memory so that every store
 // instruction writes whole row segments of C.  One CTA computes a 128 x NT tile of C
 // (MMA M = 128, N = NT), looping over its split of the K dimension in chunks of 64; two shared-memory stages let the
 // threads fill one stage while the tensor core works on the other.  One thread issues the
@@ -34,9 +37,10 @@ struct GemmArgs {
   unsigned wait_limit;                       // test limit of the consumer waits (0: normal), see Prob
 };
 
+// Bytes of one pipeline stage: the A and B tiles (TF32), or their hi and lo BF16 tiles.
 __host__ __device__ inline int gemm_stage_bytes(int nt, bool tf32) {
-  const int es = tf32 ? 4 : 2;
-  return (128 + nt) * kGemmKc * es;
+  (void)tf32;
+  return (128 + nt) * kGemmKc * 4;
 }
 
 // Stages a rows x kGemmKc tile of src(r0 + r, k0 + k) (zero outside [rlim) x [kn)) as BF16 or
@@ -83,29 +87,39 @@ __device__ __forceinline__ void gemm_tile_load(const float* __restrict__ src, lo
   }
 }
 
-// Rounds the loaded rows to BF16 / TF32 and stores them as core rows.
+// Rounds the loaded rows to TF32, or splits them into BF16 hi and lo parts (lo tile at
+// dst + lo_off), and stores them as core rows.
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 template <bool TF32, int ROWS>
 __device__ __forceinline__ void gemm_tile_store(int i0, const float (&v)[StageShape<TF32, ROWS>::BATCH][StageShape<TF32, ROWS>::EPG],
-                                                unsigned char* dst) {
+                                                unsigned char* dst, int lo_off) {
   using Sh = StageShape<TF32, ROWS>;
   constexpr int EPG = Sh::EPG;
 #pragma unroll
   for (int u = 0; u < Sh::BATCH; ++u) {
     const int e = (i0 + u) * kGemmThreads + threadIdx.x;
     const int r = e % ROWS, kg = e / ROWS;
-    uint4 o;
     if (TF32) {
-      o = make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
-                     __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
+      const uint4 o = make_uint4(__float_as_uint(to_tf32(v[u][0])), __float_as_uint(to_tf32(v[u][1])),
+                                 __float_as_uint(to_tf32(v[u][2])), __float_as_uint(to_tf32(v[u][3])));
+      *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = o;
     } else {
-      const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]);
-      const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4 % EPG], v[u][5 % EPG]);
-      const __nv_bfloat162 h3 = __floats2bfloat162_rn(v[u][6 % EPG], v[u][7 % EPG]);
-      o = make_uint4(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1),
-                     *reinterpret_cast<const uint32_t*>(&h2), *reinterpret_cast<const uint32_t*>(&h3));
+      float hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        hi[q] = __bfloat162float(__float2bfloat16_rn(v[u][q % EPG]));
+        lo[q] = v[u][q % EPG] - hi[q];  // exact in float32
+      }
+      const uint4 oh = make_uint4(bf16x2_bits(hi[0], hi[1]), bf16x2_bits(hi[2], hi[3]), bf16x2_bits(hi[4], hi[5]),
+                                  bf16x2_bits(hi[6], hi[7]));
+      const uint4 ol = make_uint4(bf16x2_bits(lo[0], lo[1]), bf16x2_bits(lo[2], lo[3]), bf16x2_bits(lo[4], lo[5]),
+                                  bf16x2_bits(lo[6], lo[7]));
+      *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = oh;
+      *reinterpret_cast<uint4*>(dst + lo_off + (kg * ROWS + r) * 16) = ol;
     }
-    *reinterpret_cast<uint4*>(dst + (kg * ROWS + r) * 16) = o;
   }
 }
 
@@ -119,13 +133,13 @@ __device__ __forceinline__ void gemm_tile_store(int i0, const float (&v)[StageSh
 // converting and storing any of them, so that many loads are in flight.
 template <bool TF32, int ROWS>
 __device__ __forceinline__ void gemm_stage_tile(const float* __restrict__ src, long long sr, long long sk, int r0,
-                                                int rlim, int k0, int kn, bool vec, unsigned char* dst) {
+                                                int rlim, int k0, int kn, bool vec, unsigned char* dst, int lo_off) {
   using Sh = StageShape<TF32, ROWS>;
 #pragma unroll 1
   for (int i0 = 0; i0 < Sh::ITEMS; i0 += Sh::BATCH) {
     float v[Sh::BATCH][Sh::EPG];
     gemm_tile_load<TF32, ROWS>(src, sr, sk, r0, rlim, k0, kn, vec, i0, v);
-    gemm_tile_store<TF32, ROWS>(i0, v, dst);
+    gemm_tile_store<TF32, ROWS>(i0, v, dst, lo_off);
   }
 }
 
@@ -135,7 +149,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
   constexpr int ES = TF32 ? 4 : 2;
   constexpr int KB = kGemmKc * ES;                  // bytes per row per stage
   constexpr int A_BYTES = 128 * KB, B_BYTES = NT * KB;
-  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int LO = A_BYTES + B_BYTES;              // BF16: the lo tiles follow the hi tiles
+  constexpr int STAGE = TF32 ? A_BYTES + B_BYTES : 2 * (A_BYTES + B_BYTES);
   constexpr uint32_t TCOLS = NT < 32 ? 32 : NT;      // TMEM columns (power of two >= 32)
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t never_bar;  // nothing arrives here (test limit only)
@@ -186,8 +201,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
     const bool to = c >= 2 && !mbar_wait(&mbar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), lim);
     const int kn = min(kGemmKc, kend - k0);
     if constexpr (kPipe) {
-      gemm_tile_store<TF32, 128>(0, va, st);
-      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES);
+      gemm_tile_store<TF32, 128>(0, va, st, LO);
+      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES, LO);
       const int k1 = k0 + kGemmKc;
       if (k1 < kend) {
         const int kn1 = min(kGemmKc, kend - k1);
@@ -197,11 +212,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
     } else if constexpr (kCombine) {
       gemm_tile_load<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, 0, va);
       gemm_tile_load<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, 0, vb);
-      gemm_tile_store<TF32, 128>(0, va, st);
-      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES);
+      gemm_tile_store<TF32, 128>(0, va, st, LO);
+      gemm_tile_store<TF32, NT>(0, vb, st + A_BYTES, LO);
     } else {
-      gemm_stage_tile<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, st);
-      gemm_stage_tile<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, st + A_BYTES);
+      gemm_stage_tile<TF32, 128>(A, g.sAi, g.sAk, i0, g.Mr, k0, kn, vecA, st, LO);
+      gemm_stage_tile<TF32, NT>(B, g.sBj, g.sBk, j0, g.Nc, k0, kn, vecB, st + A_BYTES, LO);
     }
     fence_async_smem();
     tc_fence_before();
@@ -214,8 +229,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       for (int q = 0; q < KB / 32; ++q) {  // 32 bytes of K per MMA (16 BF16 or 8 TF32)
         const uint64_t da = umma_desc(sa + q * 2 * ALBO, ALBO, 128);
         const uint64_t db = umma_desc(sb + q * 2 * BLBO, BLBO, 128);
-        if (TF32) umma_tf32(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);
-        else umma_f16(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);
+        if (TF32) {
+          umma_tf32(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);
+        } else {
+          const uint64_t dal = umma_desc(sa + LO + q * 2 * ALBO, ALBO, 128);
+          const uint64_t dbl = umma_desc(sb + LO + q * 2 * BLBO, BLBO, 128);
+          umma_f16(tacc, da, db, idesc, (c > 0 || q > 0) ? 1u : 0u);  // hi * hi
+          umma_f16(tacc, da, dbl, idesc, 1u);                          // hi * lo
+          umma_f16(tacc, dal, db, idesc, 1u);                          // lo * hi
+        }
       }
       umma_commit(&mbar[c & 1]);
     }

@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(float* __restrict__ fac, con
 
 template <int NT, bool TF32>
 static cudaError_t gemm_launch(const GemmArgs& g, dim3 grid, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)gemm_stage_bytes(NT, TF32);
+  // two pipeline stages when a split has more than one K chunk, else one (more CTAs per SM)
+  const size_t smem = (g.kspan > kGemmKc ? 2 : 1) * (size_t)gemm_stage_bytes(NT, TF32);
   k_gemm_tc<NT, TF32><<<grid, kGemmThreads, smem, st>>>(g);
   return cudaGetLastError();
 }

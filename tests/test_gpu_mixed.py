@@ -22,19 +22,18 @@ from tests._parity import rel, elem_rel, image_scale, state_errors, ll_rel, as64
 pytestmark = pytest.mark.gpu
 
 TOL_MIXED = 1e-3
-# BF16 with single-BF16 operands in the lambda and W/H GEMMs: per tensor within 1e-3, but
-# the largest per-element W / H error reaches 2.1e-3 (each BF16 rounding of W, H and of the
-# P, R operands moves a W entry by about 5e-4 in one update, emulated in float64, and the
-# W, H and g~ blocks compound); asserted at its measured level here, and the BF16 form is
-# not the form that meets the 1e-3 per-element bar (TF32 is: at most 2e-4 per element).
-TOL_BF16_EL = 3e-3
+# The BF16 form splits every tensor-core operand into BF16 hi and lo parts (three MMAs per
+# product), so it meets the per-element bar with room (measured up to 2e-5 for W, H, g~,
+# Q after one iteration); the TF32 form's single-TF32 GEMM operands reach 2e-4 (W, H) and
+# 5.7e-4 (Q at M = 8).
+TOL_BF16_EL = TOL_MIXED
 TAU_Q = 1.0     # element floor of Q: tau x (norm of the entry's row)
 TAU_IMG = 1.0   # element floor of the images: tau x |x_ft|
 KEYS = ("W", "H", "G", "Q", "LL", "separated", "W_el", "H_el", "G_el", "Q_el", "separated_el")
 
 
 def _check(err, precision):
-    """Per tensor within 1e-3 in both forms; per element within 1e-3 (TF32) or TOL_BF16_EL."""
+    """Per tensor and per element within 1e-3 in both forms."""
     el_tol = TOL_BF16_EL if precision == "bf16" else TOL_MIXED
     assert max(err[k] for k in KEYS if not k.endswith("_el")) < TOL_MIXED, err
     assert max(err[k] for k in KEYS if k.endswith("_el") and k in err) < el_tol, err
