@@ -505,7 +505,8 @@ def c3_instances(n=64, seed=0):
 def run_batched(args):
     """One step = every instance restarted from its seeded state and iterated 50 times, all
     members of one batch (one graph launch per step).  Also times the same step with the
-    instances run one after another (sequential), for comparison."""
+    instances run one after another (sequential: each mixture's iterations finish before the
+    next mixture's start), for comparison."""
     import torch
     from paper_1903_03237_gb300.build import build
     build()
@@ -526,10 +527,11 @@ def run_batched(args):
             c.restart()
         batch.iterate(iters)
 
-    def step_sequential():
+    def step_sequential():  # one mixture at a time: each finishes before the next starts
         for c in ctxs:
             c.restart()
             c.iterate(iters)
+            c.sync()
 
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
