@@ -112,7 +112,8 @@ fmnmf_status fmnmf_default_opts(fmnmf_opts* opts);
 /*
  * Creates a context for one mixture and sets the initial state.
  *  X           complex64 [F][T][M], host (x_on_device = 0) or device (x_on_device = 1).
- *              Must be finite (checked; FMNMF_ENONFINITE otherwise).
+ *              Must be finite (checked on the device after the copy; FMNMF_ENONFINITE
+ *              otherwise, with the index of the first non-finite float in the message).
  *  F, T        >= 1 bins and frames; M in [1, 8] channels; N >= 1 sources; K >= 1 bases.
  *  seed        initial state (the paper fixes none for FastMNMF; Sec. IV-A only gives
  *              one for its DP experiments):  with u_i the i-th output of the counter-based
@@ -133,7 +134,9 @@ fmnmf_status fmnmf_init(fmnmf_ctx** out, const void* X, int x_on_device, int F, 
 fmnmf_status fmnmf_footprint(int F, int T, int M, int N, int K, const fmnmf_opts* opts, size_t* bytes);
 
 /* Replaces the mixture of an existing context (same F, T, M) and re-initialises the state
- * from `seed` as fmnmf_init does, reusing the context's device memory. */
+ * from `seed` as fmnmf_init does, reusing the context's device memory.  A non-finite X
+ * returns FMNMF_ENONFINITE after it has replaced the mixture: reset again with a finite X
+ * before iterating. */
 fmnmf_status fmnmf_reset(fmnmf_ctx* ctx, const void* X, int x_on_device, uint64_t seed);
 
 /* Restores the state the context had right after its last fmnmf_init, fmnmf_reset or

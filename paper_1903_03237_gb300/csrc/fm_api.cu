@@ -896,23 +896,31 @@ inline uint64_t sm64(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+// The first non-finite float of x[0..n) (atomicMin of its index; *first starts at all ones).
+__global__ void k_check_finite(const float* __restrict__ x, size_t n, unsigned long long* first) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) atomicMin(first, (unsigned long long)i);
+}
+
+// Copies X into the context (host -> device or device -> device) and checks it on the
+// device: the first non-finite float, if any, is reported as FMNMF_ENONFINITE (the copy has
+// then replaced the context's mixture).  Synchronises.
 fmnmf_status load_x(fmnmf_ctx* ctx, const void* X, int x_on_device) {
   const size_t nfl = (size_t)ctx->F * ctx->T * ctx->M * 2;
   if (!X) return set_err(ctx, FMNMF_EINVAL, "X is NULL");
-  if (x_on_device) {
-    CK(cudaMemcpyAsync((void*)ctx->p.X, X, nfl * 4, cudaMemcpyDeviceToDevice, ctx->st));
-    // finiteness check on the device copy: reuse the host path on a staged copy
-    std::vector<float> h(nfl);
-    CK(cudaMemcpyAsync(h.data(), ctx->p.X, nfl * 4, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    for (size_t i = 0; i < nfl; ++i)
-      if (!std::isfinite(h[i])) return set_err(ctx, FMNMF_ENONFINITE, "X has a non-finite value at float %zu", i);
-  } else {
-    const float* h = (const float*)X;
-    for (size_t i = 0; i < nfl; ++i)
-      if (!std::isfinite(h[i])) return set_err(ctx, FMNMF_ENONFINITE, "X has a non-finite value at float %zu", i);
-    CK(cudaMemcpyAsync((void*)ctx->p.X, X, nfl * 4, cudaMemcpyHostToDevice, ctx->st));
-  }
+  CK(cudaMemcpyAsync((void*)ctx->p.X, X, nfl * 4, x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->st));
+  // the per-CTA log-likelihood partials are scratch between launches: their first 8 bytes
+  // hold the index
+  unsigned long long* first = reinterpret_cast<unsigned long long*>(ctx->p.llpart);
+  CK(cudaMemsetAsync(first, 0xFF, sizeof(unsigned long long), ctx->st));
+  const unsigned blocks = (unsigned)std::min<size_t>((size_t)4 * std::max(1, ctx->sms), (nfl + 255) / 256);
+  k_check_finite<<<blocks, 256, 0, ctx->st>>>((const float*)ctx->p.X, nfl, first);
+  CK(cudaGetLastError());
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, first, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h != ~0ULL) return set_err(ctx, FMNMF_ENONFINITE, "X has a non-finite value at float %llu", h);
   return FMNMF_OK;
 }
 

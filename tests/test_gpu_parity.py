@@ -258,6 +258,16 @@ def test_errors(fm):
     with pytest.raises(fm.FastMNMFError) as e:
         fm.Context(X, 2, 2)
     assert e.value.status == fm.ENONFINITE
+    assert "float 258" in str(e.value)          # ((3 * 20 + 4) * 2 + 1) * 2: the real part
+    # the device-input path of reset, and recovery with a finite mixture
+    import torch
+    ctx2 = fm.Context(make_mixture(10, 20, 2, 2, 2, 1).X, 2, 2)
+    with pytest.raises(fm.FastMNMFError) as e:
+        ctx2.reset(torch.from_numpy(X).cuda(), seed=3)
+    assert e.value.status == fm.ENONFINITE and "float 258" in str(e.value)
+    ctx2.reset(make_mixture(10, 20, 2, 2, 2, 2).X, seed=3)
+    ctx2.iterate(2)
+    assert np.isfinite(ctx2.loglik())
     with pytest.raises(fm.FastMNMFError) as e:
         fm.Context(make_mixture(10, 20, 2, 2, 2, 1).X, 2, 2, hbm_budget=1000)
     assert e.value.status == fm.ENOMEM
