@@ -160,10 +160,11 @@ fmnmf_status fmnmf_restart(fmnmf_ctx* ctx);
  * With the unconstrained source model (FastFCA, Sec. III-C-1) the W and H updates are
  * replaced by  lambda_ftn <- lambda_ftn * sqrt(num/den)  (Eq. 22, every point) and the nu
  * normalisation scales lambda_ftn instead of w_nkf (update_mask bit W selects the lambda
- * update, bit H is ignored).  With the fused schedule the mu normalisation is applied once
- * at the end of each call, and of each run of at most 100 iterations within it (it commutes
- * with every update, so the state is that of the per-iteration normalisation up to rounding;
- * results therefore depend on how iterations are split into calls, by rounding only).
+ * update, bit H is ignored).  In every form the mu normalisation is applied once at the end
+ * of each call, and of each run of at most 100 iterations within it (it commutes with every
+ * update, so the state is that of the per-iteration normalisation up to rounding; results
+ * therefore depend on how iterations are split into calls, by rounding only), and the
+ * log-likelihood is summed for the last iteration only.
  * Asynchronous: enqueued on the context stream; device errors surface at the next
  * synchronising call.
  */

@@ -615,14 +615,19 @@ struct Recorder {  // brackets launches with events when timing is on (works und
   }
 };
 
-cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec);
+cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec, bool last);
 
 // The end of an iteration.  With a Q update or normalisation and up to kFuseXtFrames
 // frames, the IP kernel also forms x~ and the log-likelihood of each bin right after the
 // bin's update (one launch instead of two: the short mixtures are launch-latency bound),
 // then the mu normalisation runs.  Longer mixtures keep the separate x~ / log-likelihood
 // kernel, whose many small CTAs keep more loads in flight than one CTA per bin.
-cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int norm) {
+// The end of an iteration: the IP update and x~ (with the bins' log-likelihood terms), and,
+// at the end of a chunk (last), the mu normalisation and the log-likelihood sum: mu rescales
+// w_nk and h_nk reciprocally, which leaves lambda, every ratio of the W and H rules and the
+// log-likelihood unchanged, so it commutes with the updates and is applied once per chunk,
+// as in the fused schedule; only the last iteration's log-likelihood is summed.
+cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int norm, bool last) {
   cudaError_t e;
   if (yflags && c->T > kFuseXtFrames) {
     LaunchArgs a;
@@ -634,9 +639,9 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
     x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
     x.n_pt_blocks = c->n_pt_blocks;
     x.apply_phi = 1;
-    x.do_mu = norm ? 1 : 0;
+    x.do_mu = (norm && last) ? 1 : 0;
     x.pr = c->fusedPR ? c->PR : nullptr;
-    x.grid = dim3(c->n_pt_blocks + (norm ? c->n_mu_blocks : 0));
+    x.grid = dim3(c->n_pt_blocks + (x.do_mu ? c->n_mu_blocks : 0));
     return rec.run(KK_XT, x);
   }
   if (yflags) {
@@ -646,11 +651,12 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
     a.xt_mode = 1; a.ctr = c->ctrLL;
     a.smem = c->ipSmem;
     a.pr = c->fusedPR ? c->PR : nullptr;
-    // with the mu normalisation to follow, its kernel adds up the log-likelihood (a last
-    // block beside the mu blocks) and the IP kernel skips its serial tail
-    a.ll_tail = norm ? 0 : 1;
+    // with the mu normalisation to follow (end of a chunk), its kernel adds up the
+    // log-likelihood (a last block beside the mu blocks) and the IP kernel skips its serial
+    // tail; inside a chunk the bins' terms are left for the last iteration's sum
+    a.ll_tail = (!norm && last) ? 1 : 0;
     if ((e = rec.run(KK_IP, a)) != cudaSuccess) return e;
-    if (!norm) return cudaSuccess;
+    if (!norm || !last) return cudaSuccess;
     LaunchArgs x;
     x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
     x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = 1; x.ll_bins = 1;
@@ -667,8 +673,8 @@ cudaError_t enqueue_tail(fmnmf_ctx* c, Recorder& rec, int yflags, int ipS, int n
   return rec.run(KK_XT, x);
 }
 
-cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
-  if (c->mixed) return enqueue_mixed_iteration(c, rec);
+cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec, bool last) {
+  if (c->mixed) return enqueue_mixed_iteration(c, rec, last);
   const unsigned mask = c->opts.update_mask;
   const int norm = c->opts.normalise ? FLAG_NORMALISE : 0;
   cudaError_t e;
@@ -680,11 +686,11 @@ cudaError_t enqueue_iteration(fmnmf_ctx* c, Recorder& rec) {
     if ((e = rec.run(KK_G, tile_args(c, c->gG, c->smG, FLAG_UPDATE, c->ctrG))) != cudaSuccess) return e;
   const int yflags = norm | ((mask & FMNMF_UPDATE_Q) ? FLAG_DO_V : 0);
   if ((e = rec.run(KK_Y, tile_args(c, c->gY, c->smY, yflags, c->ctrY))) != cudaSuccess) return e;
-  return enqueue_tail(c, rec, yflags, c->gY.S, norm);
+  return enqueue_tail(c, rec, yflags, c->gY.S, norm, last);
 }
 
 // The mixed-precision iteration: tensor-core GEMMs for lambda and the W / H sums.
-cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
+cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec, bool last) {
   const unsigned mask = c->opts.update_mask;
   const int norm = c->opts.normalise ? FLAG_NORMALISE : 0;
   cudaError_t e;
@@ -747,7 +753,7 @@ cudaError_t enqueue_mixed_iteration(fmnmf_ctx* c, Recorder& rec) {
     a.p.lam = c->lam;
     if ((e = rec.run(KK_Y, a)) != cudaSuccess) return e;
   }
-  return enqueue_tail(c, rec, yflags, ipS, norm);
+  return enqueue_tail(c, rec, yflags, ipS, norm, last);
 }
 
 LaunchArgs hgemm_args(fmnmf_ctx* c) {
@@ -806,7 +812,7 @@ cudaError_t enqueue_fused_chunk(fmnmf_ctx* c, Recorder& rec, int n) {
 cudaError_t enqueue_chunk(fmnmf_ctx* c, Recorder& rec, int n) {
   if (c->fused) return enqueue_fused_chunk(c, rec, n);
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_iteration(c, rec);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_iteration(c, rec, i == n - 1);
   return e;
 }
 
