@@ -99,7 +99,7 @@ enum { FMNMF_SOURCE_NMF = 0, FMNMF_SOURCE_FREE = 1 };
 typedef struct {
   int precision;          /* FMNMF_PREC_*                                      (default FP32) */
   unsigned update_mask;   /* FMNMF_UPDATE_* bits applied by fmnmf_iterate      (default ALL)  */
-  int normalise;          /* 1: scale normalisation after each iteration       (default 1)    */
+  int normalise;          /* 1: scale normalisation (see fmnmf_iterate)       (default 1)    */
   void* stream;           /* cudaStream_t for all device work; NULL = a private stream        */
   size_t hbm_budget;      /* 0 = unlimited; else init fails with ENOMEM above it              */
   int schedule;           /* FMNMF_SCHED_*                                     (default AUTO) */
