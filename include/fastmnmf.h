@@ -80,7 +80,8 @@ enum { FMNMF_UPDATE_W = 1, FMNMF_UPDATE_H = 2, FMNMF_UPDATE_G = 4, FMNMF_UPDATE_
 enum { FMNMF_PREC_FP32 = 0, FMNMF_PREC_BF16 = 1, FMNMF_PREC_TF32 = 2 };
 
 /* Launch schedule of the FP32 form.
- *  SWEEP: one tiled launch per block of the iteration (W, H, g~, V_fm, IP, x~): six launches.
+ *  SWEEP: one tiled launch per block of the iteration (W, H, g~, V_fm, the IP with x~; x~ in a
+ *         launch of its own beyond 1024 frames): five or six launches.
  *  FUSED: two launches per iteration.  Every block but the H update (Eq. 24, a sum over bins)
  *         is independent per frequency bin, so one kernel runs, per bin, the g~ update, V_fm
  *         and the IP update, the normalisation, x~, the bin's log-likelihood terms and the W
