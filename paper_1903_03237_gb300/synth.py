@@ -75,6 +75,40 @@ def make_state(F: int, T: int, M: int, N: int, K: int, seed: int):
     return W, H, G, Q
 
 
+def make_decoder(F: int, D: int, Hd: int, seed: int):
+    """Seeded random weights of the deep-prior decoder r = exp(W2 tanh(W1 z + b1) + b2)
+    (trained weights are not available): W1 ~ N(0, 1/D) [Hd, D], b1 ~ N(0, 0.01) [Hd],
+    W2 ~ N(0, 1/Hd) [F, Hd], b2 ~ N(0, 0.25) [F]; float32."""
+    rng = np.random.default_rng(seed + 104729)
+    W1 = rng.standard_normal((Hd, D)) / np.sqrt(D)
+    b1 = 0.1 * rng.standard_normal(Hd)
+    W2 = rng.standard_normal((F, Hd)) / np.sqrt(Hd)
+    b2 = 0.5 * rng.standard_normal(F)
+    return tuple(a.astype(np.float32) for a in (W1, b1, W2, b2))
+
+
+def make_dp_state(F: int, T: int, M: int, N: int, K: int, D: int, seed: int):
+    """A random starting state of the deep-prior model (speech source 0, NMF noise sources
+    1..N-1): Z ~ N(0, I) [T, D], u ~ U(0.5, 1.5) [F], v ~ K U(0.2, 1.2) [T], and W, H, g~, Q
+    as ``make_state`` draws them for the N-1 noise sources and N sources.  float32 /
+    complex64."""
+    W, H, G, Q = make_state(F, T, M, N, K, seed)
+    rng = np.random.default_rng(seed + 15485863)
+    Z = rng.standard_normal((T, D)).astype(np.float32)
+    u = rng.uniform(0.5, 1.5, size=F).astype(np.float32)
+    v = (K * rng.uniform(0.2, 1.2, size=T)).astype(np.float32)
+    return Z, u, v, W[1:].copy(), H[1:].copy(), G, Q
+
+
+def make_dp_draws(n_iter: int, S: int, T: int, D: int, seed: int):
+    """The Metropolis draws of n_iter iterations with S proposals per frame:
+    xi ~ N(0, I) [n_iter, S, T, D] and log u, u ~ U(0, 1) [n_iter, S, T]; float32."""
+    rng = np.random.default_rng(seed + 32452843)
+    xi = rng.standard_normal((n_iter, S, T, D)).astype(np.float32)
+    logu = np.log(rng.uniform(np.finfo(np.float64).tiny, 1.0, size=(n_iter, S, T))).astype(np.float32)
+    return xi, logu
+
+
 def make_signals(M: int, S: int, n_src: int, seed: int, taps: int = 64) -> np.ndarray:
     """Seeded time-domain multichannel recordings for the front end (STFT, its inverse and
     the spectral initialisation), float32 [M, S]: n_src sources, each white Gaussian noise
