@@ -377,6 +377,77 @@ fmnmf_status fmnmf_loglik_noalloc(const void* X, const float* W, const float* H,
                                   const void* Q, int F, int T, int M, int N, int K, double* ll,
                                   void* stream);
 
+/* ---- FastMNMF-DP (Sec. III-B-3, Sec. III-C-3) --------------------------------------------
+ * Source 0 (the paper's speech source n = 1) has the deep-prior PSD of Sec. II-B-3,
+ *     lambda_ft0 = u_f v_t [sigma^2_theta(z_t)]_f,   sigma^2_theta(z) = exp(W2 tanh(W1 z + b1) + b2),
+ * a two-layer decoder whose weights the caller supplies (fmnmf_dp_set_decoder; trained weights
+ * are the caller's, the method does not train them).  Sources 1..N-1 (noise) have the NMF PSD
+ * of Eq. 9 with K bases.  The spatial model and its updates are those of FastMNMF (Eqs. 16-21).
+ * One iteration, in this order, each block from the current parameters:
+ *   Z   n_proposals Metropolis proposals per frame: z' = z + sqrt(eps) xi, accepted where
+ *       log u < log gamma_t, log gamma_t being the change of Eq. 17 when lambda_ft0 alone
+ *       changes, with y~ of the other sources, g~ and x~ of the iteration's start;
+ *   u, v the multiplicative rules of Sec. III-B-3;  W, H of the noise sources: Eqs. 23-24;
+ *   g~  Eq. 21;  Q  Eqs. 18-20;  normalisation (opts.normalise): phi_f = tr(Q_f Q_f^H)/M,
+ *       nu_nf = sum_m g~_nfm (into u and W), mu_0 = sum_f u_f (into v), mu_nk = sum_f w_nkf
+ *       (into H); lambda g~ and the log-likelihood are unchanged by it.
+ * The random draws are inputs: xi ~ N(0, I) and log u, u ~ U(0, 1), from the caller.
+ * All arithmetic is FP32 on the CUDA cores; the per-bin g~ / IP kernel is that of the fused
+ * FP32 schedule (float-float IP).  Layouts (row-major, float32 unless stated):
+ *   X [F][T][M] complex64;  Z [T][D];  u [F];  v [T];  W [N-1][K][F];  H [N-1][K][T];
+ *   G [N][F][M];  Q [F][M][M] complex64;  W1 [Hd][D];  b1 [Hd];  W2 [F][Hd];  b2 [F];
+ *   xi [n_iter][n_proposals][T][D];  logu [n_iter][n_proposals][T];  images [N][F][T][M] complex64.
+ * Host pointers are read or written before the call returns (copies); device pointers (with
+ * the *_on_device flags) must stay valid until the work on the context's stream is done.
+ * Errors: FMNMF_EINVAL for bad shapes or arguments (message via fmnmf_dp_last_error(dp), or
+ * fmnmf_dp_last_error(NULL) when there is no context yet); device faults of the method
+ * (singular IP system, non-finite value) are reported by the next synchronising call, as for
+ * FastMNMF.  Not thread-safe per context. */
+typedef struct fmnmf_dp fmnmf_dp;
+typedef struct {
+  int D;               /* latent dimension of z_t                      (default 16, Sec. IV-A)   */
+  int Hd;              /* decoder hidden width, multiple of 4, <= 1024  (default 128)            */
+  int n_proposals;     /* Metropolis proposals per frame per iteration  (default 30, Sec. IV-A)  */
+  float eps;           /* proposal variance                             (default 1e-4, Sec. IV-A)*/
+  int normalise;       /* 1: scale normalisation                        (default 1)              */
+  void* stream;        /* cudaStream_t for all device work; NULL = a private stream               */
+} fmnmf_dp_opts;
+
+fmnmf_status fmnmf_dp_default_opts(fmnmf_dp_opts* opts);
+/* Needs 1 <= N <= 8, (N-1) K <= 256, N M small enough for the per-bin kernel of the fused
+ * schedule, and one frame's x~, y~ and decoder staging within the device's shared memory. */
+fmnmf_status fmnmf_dp_create(fmnmf_dp** out, const void* X, int x_on_device, int F, int T, int M, int N,
+                             int K, const fmnmf_dp_opts* opts);
+/* Host weights; finite.  Invalidates the state (r = sigma^2(z) changes): set it again. */
+fmnmf_status fmnmf_dp_set_decoder(fmnmf_dp* dp, const float* W1, const float* b1, const float* W2,
+                                  const float* b2);
+/* Host state; u, v, W, H finite and positive, G finite and nonnegative, Q finite.  Forms r and
+ * lambda of every source, x~, log|det Q|^2 and the log-likelihood; resets the accepted count.
+ * W and H may be NULL when N = 1. */
+fmnmf_status fmnmf_dp_set_state(fmnmf_dp* dp, const float* Z, const float* u, const float* v,
+                                const float* W, const float* H, const float* G, const void* Q);
+/* Host copies of the state; any pointer may be NULL.  Synchronises. */
+fmnmf_status fmnmf_dp_get_state(fmnmf_dp* dp, float* Z, float* u, float* v, float* W, float* H,
+                                float* G, void* Q);
+/* n_iter iterations, enqueued (asynchronous); the log-likelihood of the state after the last
+ * one is ready at the next fmnmf_dp_loglik.  Host draws are copied in chunks. */
+fmnmf_status fmnmf_dp_iterate(fmnmf_dp* dp, int n_iter, const float* xi, const float* logu,
+                              int draws_on_device);
+/* The Z block alone (one iteration's n_proposals proposals per frame) with the current u, v,
+ * W, H, g~, Q and x~; writes log gamma of every proposal to loggamma [n_proposals][T] (host,
+ * may be NULL) and the number accepted to *accepted (may be NULL).  The log-likelihood is not
+ * refreshed.  Synchronises. */
+fmnmf_status fmnmf_dp_metropolis(fmnmf_dp* dp, const float* xi, const float* logu, int draws_on_device,
+                                 float* loggamma, long long* accepted);
+fmnmf_status fmnmf_dp_sync(fmnmf_dp* dp);
+fmnmf_status fmnmf_dp_loglik(fmnmf_dp* dp, double* ll);
+/* Proposals accepted since the last fmnmf_dp_set_state. */
+fmnmf_status fmnmf_dp_accepted(fmnmf_dp* dp, long long* n);
+/* Multichannel Wiener filter (Eq. 3 with Eq. 16) of every source, as fmnmf_separate. */
+fmnmf_status fmnmf_dp_separate(fmnmf_dp* dp, void* out, int out_on_device);
+fmnmf_status fmnmf_dp_destroy(fmnmf_dp* dp);
+const char* fmnmf_dp_last_error(const fmnmf_dp* dp);
+
 #ifdef __cplusplus
 }
 #endif

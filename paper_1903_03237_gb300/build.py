@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfastmnmf.so")
 
-SOURCES = ["fm_api.cu", "fm_kernels_m2.cu", "fm_kernels_m4.cu", "fm_kernels_m8.cu", "fm_noalloc.cu", "fm_mixed.cu", "fm_server.cu", "fm_frontend.cu"]
+SOURCES = ["fm_api.cu", "fm_dp.cu", "fm_kernels_m2.cu", "fm_kernels_m4.cu", "fm_kernels_m8.cu", "fm_noalloc.cu", "fm_mixed.cu", "fm_server.cu", "fm_frontend.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -1658,3 +1658,349 @@ fmnmf_status fmnmf_batch_destroy(fmnmf_batch* b) {
 }
 
 }  // extern "C"
+
+// ===========================================================================================
+// FastMNMF-DP (Sec. III-B-3, Sec. III-C-3): the deep-prior speech source (source 0) and NMF
+// noise sources around a context of the unconstrained source model, whose lambda, g~, Q, x~
+// and per-bin kernel (g~, V_fm + IP, normalisation, x~, terms of Eq. 17) it shares.
+// ===========================================================================================
+struct fmnmf_dp {
+  fmnmf_ctx* ctx = nullptr;
+  fmnmf_dp_opts o{};
+  int F = 0, T = 0, M = 0, N = 0, K = 0;
+  void* buf = nullptr;  // u, v, Z, R, noise W and H, decoder, nu, draws, log gamma, counter
+  float *u = nullptr, *v = nullptr, *Z = nullptr, *R = nullptr, *Wn = nullptr, *Hn = nullptr;
+  float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *nu = nullptr;
+  float *xi = nullptr, *logu = nullptr, *lg = nullptr;
+  unsigned long long* acc = nullptr;
+  int draw_iters = 0;  // iterations of host draws the device buffers hold
+  size_t mh_smem = 0;
+  int tb = 0;
+  bool have_decoder = false, have_state = false;
+};
+
+namespace {
+
+constexpr int kDpDrawIters = 4;  // host draws are copied in chunks of this many iterations
+
+DpArgs dp_args(fmnmf_dp* d) {
+  DpArgs a;
+  a.p = d->ctx->p;
+  a.lam = d->ctx->lam;
+  a.u = d->u; a.v = d->v; a.Z = d->Z; a.R = d->R; a.Wn = d->Wn; a.Hn = d->Hn;
+  a.W1 = d->W1; a.b1 = d->b1; a.W2 = d->W2; a.b2 = d->b2;
+  a.D = d->o.D; a.Hd = d->o.Hd; a.K = d->K;
+  a.S = d->o.n_proposals;
+  a.sqrt_eps = (float)std::sqrt((double)d->o.eps);
+  a.n_acc = d->acc;
+  a.nu = d->nu;
+  a.maxm = d->ctx->maxm;
+  a.tb = d->tb;
+  return a;
+}
+
+// One iteration: Z (S proposals per frame), u, v, the noise W, H, then the per-bin kernel
+// (g~, Q, phi / nu normalisation with nu exported, x~, terms of Eq. 17), then nu / mu into
+// u, v, W, H; with `last`, the sum of Eq. 17.
+cudaError_t enqueue_dp_iteration(fmnmf_dp* d, const float* xi, const float* logu, bool last) {
+  fmnmf_ctx* c = d->ctx;
+  DpArgs a = dp_args(d);
+  a.xi = xi;
+  a.logu = logu;
+  const bool norm = d->o.normalise != 0;
+  cudaError_t e;
+  if (a.S > 0) {
+    c->launches++;
+    if ((e = dp_launch_mh(a, d->mh_smem, c->st)) != cudaSuccess) return e;
+  }
+  c->launches += 2;
+  if ((e = dp_launch_fsweep(a, 0, c->st)) != cudaSuccess) return e;
+  if ((e = dp_launch_tsweep(a, 0, c->st)) != cudaSuccess) return e;
+  if (d->N > 1) {
+    c->launches += 2;
+    if ((e = dp_launch_fsweep(a, 1, c->st)) != cudaSuccess) return e;
+    if ((e = dp_launch_tsweep(a, 1, c->st)) != cudaSuccess) return e;
+  }
+  LaunchArgs b;
+  b.p = c->p;
+  b.p.nu_out = d->nu;
+  b.st = c->st;
+  b.grid = dim3(c->F);
+  b.smem = c->binSm;
+  b.flags = FU_G | FU_Q | FU_FREE | (norm ? (FU_NORM | FU_LAMWB) : 0);
+  b.lam = c->lam;
+  b.pr = c->PR;
+  if ((e = launch(c, KK_BIN, b)) != cudaSuccess) return e;
+  if (norm) {
+    c->launches++;
+    if ((e = dp_launch_norm(a, c->st)) != cudaSuccess) return e;
+  }
+  if (!last) return cudaSuccess;
+  LaunchArgs x;
+  x.p = c->p; x.st = c->st; x.ctr = c->ctrLL;
+  x.n_pt_blocks = 0; x.apply_phi = 0; x.do_mu = 0; x.ll_bins = 1;
+  x.grid = dim3(1);
+  return launch(c, KK_XT, x);
+}
+
+fmnmf_status dp_err(fmnmf_dp* d, fmnmf_status s, const char* msg) {
+  return set_err(d ? d->ctx : nullptr, s, "%s", msg);
+}
+
+}  // namespace
+
+extern "C" {
+
+fmnmf_status fmnmf_dp_default_opts(fmnmf_dp_opts* o) {
+  if (!o) return set_err(nullptr, FMNMF_EINVAL, "opts is NULL");
+  o->D = 16;
+  o->Hd = 128;
+  o->n_proposals = 30;
+  o->eps = 1e-4f;
+  o->normalise = 1;
+  o->stream = nullptr;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_dp_create(fmnmf_dp** out, const void* X, int x_on_device, int F, int T, int M, int N, int K,
+                             const fmnmf_dp_opts* opts) {
+  if (!out) return set_err(nullptr, FMNMF_EINVAL, "out is NULL");
+  *out = nullptr;
+  fmnmf_dp_opts o;
+  fmnmf_dp_default_opts(&o);
+  if (opts) o = *opts;
+  if (N < 1 || N > 8 || K < 1 || (N - 1) * K > 256)
+    return set_err(nullptr, FMNMF_EINVAL, "FastMNMF-DP needs 1 <= N <= 8 and (N-1)*K <= 256 (N=%d K=%d)", N, K);
+  if (o.D < 1 || o.D > 256 || o.Hd < 4 || o.Hd > 1024 || o.Hd % 4 != 0)
+    return set_err(nullptr, FMNMF_EINVAL, "decoder shape D=%d Hd=%d (need 1 <= D <= 256, Hd a multiple of 4 in [4, 1024])", o.D, o.Hd);
+  if (o.n_proposals < 0 || !(o.eps >= 0.f) || !std::isfinite(o.eps))
+    return set_err(nullptr, FMNMF_EINVAL, "n_proposals must be >= 0 and eps finite and >= 0");
+  fmnmf_opts co;
+  fmnmf_default_opts(&co);
+  co.source_model = FMNMF_SOURCE_FREE;
+  co.normalise = o.normalise;
+  co.stream = o.stream;
+  fmnmf_ctx* ctx = nullptr;
+  fmnmf_status s = fmnmf_init(&ctx, X, x_on_device, F, T, M, N, 1, 0, &co);
+  if (s != FMNMF_OK) return s;
+  auto fail = [&](fmnmf_status st, const char* fmt, auto... args) {
+    set_err(nullptr, st, fmt, args...);
+    fmnmf_destroy(ctx);
+    return st;
+  };
+  if (!ctx->fused) return fail(FMNMF_EINVAL, "FastMNMF-DP: N*M=%d is too large for the per-bin kernel", N * M);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return fail(FMNMF_ECUDA, "FastMNMF-DP: device query failed");
+  fmnmf_dp* d = new fmnmf_dp;
+  d->ctx = ctx;
+  d->o = o;
+  d->F = F; d->T = T; d->M = M; d->N = N; d->K = K;
+  d->tb = dp_mh_frames(F, M, o.D, o.Hd, (size_t)optin - 1024, &d->mh_smem);
+  if (d->tb == 0) {
+    delete d;
+    return fail(FMNMF_EINVAL, "FastMNMF-DP: F*M=%d too large to stage one frame in shared memory", F * M);
+  }
+  if (dp_prepare(ctx->maxm, d->mh_smem) != cudaSuccess) {
+    delete d;
+    return fail(FMNMF_ECUDA, "FastMNMF-DP: shared-memory attribute failed");
+  }
+  const size_t Fs = F, Ts = T, Ds = o.D, Hs = o.Hd, Ss = o.n_proposals, nK = (size_t)(N - 1) * K;
+  d->draw_iters = kDpDrawIters;
+  const size_t counts[] = {Fs, Ts, Ts * Ds, Fs * Ts, nK * Fs, nK * Ts, Hs * Ds, Hs, Fs * Hs, Fs, (size_t)N * Fs,
+                           kDpDrawIters * Ss * Ts * Ds, kDpDrawIters * Ss * Ts, Ss * Ts};
+  float** dst[] = {&d->u, &d->v, &d->Z, &d->R, &d->Wn, &d->Hn, &d->W1, &d->b1, &d->W2, &d->b2, &d->nu,
+                   &d->xi, &d->logu, &d->lg};
+  size_t off[15], total = 0;
+  for (int i = 0; i < 14; ++i) {
+    off[i] = total;
+    total += ((counts[i] * 4 + 255) / 256) * 256;
+  }
+  off[14] = total;
+  total += 256;
+  if (cudaMalloc(&d->buf, total) != cudaSuccess) {
+    delete d;
+    return fail(FMNMF_ENOMEM, "FastMNMF-DP: cudaMalloc of %zu bytes failed", total);
+  }
+  for (int i = 0; i < 14; ++i) *dst[i] = (float*)((char*)d->buf + off[i]);
+  d->acc = (unsigned long long*)((char*)d->buf + off[14]);
+  if (cudaMemsetAsync(d->acc, 0, 8, ctx->st) != cudaSuccess || cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+    cudaFree(d->buf);
+    delete d;
+    return fail(FMNMF_ECUDA, "FastMNMF-DP: counter reset failed");
+  }
+  *out = d;
+  return FMNMF_OK;
+}
+
+const char* fmnmf_dp_last_error(const fmnmf_dp* d) { return d ? d->ctx->err.c_str() : g_thread_err.c_str(); }
+
+fmnmf_status fmnmf_dp_set_decoder(fmnmf_dp* d, const float* W1, const float* b1, const float* W2, const float* b2) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  if (!W1 || !b1 || !W2 || !b2) return dp_err(d, FMNMF_EINVAL, "set_decoder needs W1, b1, W2 and b2");
+  fmnmf_ctx* ctx = d->ctx;
+  const size_t D = d->o.D, Hd = d->o.Hd, F = d->F;
+  const struct { const float* src; float* dst; size_t n; } c[4] = {
+      {W1, d->W1, Hd * D}, {b1, d->b1, Hd}, {W2, d->W2, F * Hd}, {b2, d->b2, F}};
+  for (auto& e : c)
+    for (size_t i = 0; i < e.n; ++i)
+      if (!std::isfinite(e.src[i])) return dp_err(d, FMNMF_EINVAL, "decoder weights must be finite");
+  CK(cudaStreamSynchronize(ctx->st));
+  for (auto& e : c) CK(cudaMemcpyAsync(e.dst, e.src, e.n * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  d->have_decoder = true;
+  d->have_state = false;  // r = sigma^2(z) changes with the decoder: the state must be set again
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_dp_set_state(fmnmf_dp* d, const float* Z, const float* u, const float* v, const float* W,
+                                const float* H, const float* G, const void* Q) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  fmnmf_ctx* ctx = d->ctx;
+  if (!d->have_decoder) return dp_err(d, FMNMF_EINVAL, "set_state: set the decoder first");
+  const size_t F = d->F, T = d->T, M = d->M, D = d->o.D, nK = (size_t)(d->N - 1) * d->K;
+  if (!Z || !u || !v || !G || !Q || (nK && (!W || !H))) return dp_err(d, FMNMF_EINVAL, "set_state: NULL argument");
+  for (size_t i = 0; i < T * D; ++i)
+    if (!std::isfinite(Z[i])) return dp_err(d, FMNMF_EINVAL, "z must be finite");
+  auto pos = [](const float* a, size_t n) {
+    for (size_t i = 0; i < n; ++i) if (!(a[i] > 0.f) || !std::isfinite(a[i])) return false;
+    return true;
+  };
+  if (!pos(u, F) || !pos(v, T) || (nK && (!pos(W, nK * F) || !pos(H, nK * T))))
+    return dp_err(d, FMNMF_EINVAL, "u, v, W and H must be finite and positive");
+  std::vector<float4> Qx;
+  fmnmf_status s = check_gq(ctx, G, Q, Qx);
+  if (s != FMNMF_OK) return s;
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpyAsync(d->Z, Z, T * D * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(d->u, u, F * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(d->v, v, T * 4, cudaMemcpyHostToDevice, ctx->st));
+  if (nK) {
+    CK(cudaMemcpyAsync(d->Wn, W, nK * F * 4, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(d->Hn, H, nK * T * 4, cudaMemcpyHostToDevice, ctx->st));
+  }
+  CK(cudaMemcpyAsync(ctx->p.G, G, (size_t)d->N * F * M * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->p.Qx, Qx.data(), Qx.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->p.status, 0, 4, ctx->st));
+  CK(cudaMemsetAsync(d->acc, 0, 8, ctx->st));
+  ctx->launches += d->N > 1 ? 2 : 1;
+  CK(dp_launch_init(dp_args(d), ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // the host vector Qx goes out of scope
+  if ((s = refresh_state(ctx)) != FMNMF_OK) return s;
+  if ((s = check_status(ctx)) != FMNMF_OK) return s;
+  d->have_state = true;
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_dp_get_state(fmnmf_dp* d, float* Z, float* u, float* v, float* W, float* H, float* G, void* Q) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  fmnmf_ctx* ctx = d->ctx;
+  const size_t F = d->F, T = d->T, M = d->M, D = d->o.D, nK = (size_t)(d->N - 1) * d->K;
+  CK(cudaStreamSynchronize(ctx->st));
+  if (Z) CK(cudaMemcpyAsync(Z, d->Z, T * D * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (u) CK(cudaMemcpyAsync(u, d->u, F * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (v) CK(cudaMemcpyAsync(v, d->v, T * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (W && nK) CK(cudaMemcpyAsync(W, d->Wn, nK * F * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (H && nK) CK(cudaMemcpyAsync(H, d->Hn, nK * T * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (G) CK(cudaMemcpyAsync(G, ctx->p.G, (size_t)d->N * F * M * 4, cudaMemcpyDeviceToHost, ctx->st));
+  if (Q) CK(cudaMemcpyAsync(Q, ctx->p.Qf, F * M * M * sizeof(float2), cudaMemcpyDeviceToHost, ctx->st));
+  return check_status(ctx);
+}
+
+fmnmf_status fmnmf_dp_iterate(fmnmf_dp* d, int n_iter, const float* xi, const float* logu, int draws_on_device) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  fmnmf_ctx* ctx = d->ctx;
+  if (n_iter < 0) return dp_err(d, FMNMF_EINVAL, "n_iter < 0");
+  if (!d->have_state) return dp_err(d, FMNMF_EINVAL, "iterate: set the decoder and the state first");
+  const size_t S = d->o.n_proposals, T = d->T, D = d->o.D;
+  if (S && n_iter && (!xi || !logu)) return dp_err(d, FMNMF_EINVAL, "iterate: the Metropolis draws are NULL");
+  sync_wait_limit(ctx);
+  const size_t xs = S * T * D, ls = S * T;
+  for (int i0 = 0; i0 < n_iter; i0 += d->draw_iters) {
+    const int n = std::min(d->draw_iters, n_iter - i0);
+    const float* xb = nullptr;
+    const float* lb = nullptr;
+    if (S) {
+      if (draws_on_device) {
+        xb = xi + i0 * xs;
+        lb = logu + i0 * ls;
+      } else {
+        CK(cudaMemcpyAsync(d->xi, xi + i0 * xs, n * xs * 4, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(d->logu, logu + i0 * ls, n * ls * 4, cudaMemcpyHostToDevice, ctx->st));
+        xb = d->xi;
+        lb = d->logu;
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      CK(enqueue_dp_iteration(d, S ? xb + i * xs : nullptr, S ? lb + i * ls : nullptr, i0 + i == n_iter - 1));
+  }
+  return FMNMF_OK;
+}
+
+fmnmf_status fmnmf_dp_metropolis(fmnmf_dp* d, const float* xi, const float* logu, int draws_on_device,
+                                 float* loggamma, long long* accepted) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  fmnmf_ctx* ctx = d->ctx;
+  if (!d->have_state) return dp_err(d, FMNMF_EINVAL, "metropolis: set the decoder and the state first");
+  const size_t S = d->o.n_proposals, T = d->T, D = d->o.D;
+  if (!S) return FMNMF_OK;
+  if (!xi || !logu) return dp_err(d, FMNMF_EINVAL, "metropolis: the draws are NULL");
+  CK(cudaStreamSynchronize(ctx->st));
+  DpArgs a = dp_args(d);
+  if (draws_on_device) {
+    a.xi = xi;
+    a.logu = logu;
+  } else {
+    CK(cudaMemcpyAsync(d->xi, xi, S * T * D * 4, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(d->logu, logu, S * T * 4, cudaMemcpyHostToDevice, ctx->st));
+    a.xi = d->xi;
+    a.logu = d->logu;
+  }
+  a.loggamma = d->lg;
+  unsigned long long before = 0, after = 0;
+  CK(cudaMemcpyAsync(&before, d->acc, 8, cudaMemcpyDeviceToHost, ctx->st));
+  ctx->launches++;
+  CK(dp_launch_mh(a, d->mh_smem, ctx->st));
+  CK(cudaMemcpyAsync(&after, d->acc, 8, cudaMemcpyDeviceToHost, ctx->st));
+  if (loggamma) CK(cudaMemcpyAsync(loggamma, d->lg, S * T * 4, cudaMemcpyDeviceToHost, ctx->st));
+  fmnmf_status s = check_status(ctx);
+  if (accepted) *accepted = (long long)(after - before);
+  return s;
+}
+
+fmnmf_status fmnmf_dp_sync(fmnmf_dp* d) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  return check_status(d->ctx);
+}
+
+fmnmf_status fmnmf_dp_loglik(fmnmf_dp* d, double* ll) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  return fmnmf_loglik(d->ctx, ll);
+}
+
+fmnmf_status fmnmf_dp_accepted(fmnmf_dp* d, long long* n) {
+  if (!d || !n) return set_err(d ? d->ctx : nullptr, FMNMF_EINVAL, "NULL argument");
+  fmnmf_ctx* ctx = d->ctx;
+  unsigned long long a = 0;
+  CK(cudaMemcpyAsync(&a, d->acc, 8, cudaMemcpyDeviceToHost, ctx->st));
+  fmnmf_status s = check_status(ctx);
+  *n = (long long)a;
+  return s;
+}
+
+fmnmf_status fmnmf_dp_separate(fmnmf_dp* d, void* out, int out_on_device) {
+  if (!d) return set_err(nullptr, FMNMF_EINVAL, "dp is NULL");
+  return fmnmf_separate(d->ctx, out, out_on_device);
+}
+
+fmnmf_status fmnmf_dp_destroy(fmnmf_dp* d) {
+  if (!d) return FMNMF_OK;
+  if (d->ctx && d->ctx->st) cudaStreamSynchronize(d->ctx->st);
+  if (d->buf) cudaFree(d->buf);
+  fmnmf_status s = fmnmf_destroy(d->ctx);
+  delete d;
+  return s;
+}
+
+}  // extern "C"

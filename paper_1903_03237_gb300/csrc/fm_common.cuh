@@ -36,6 +36,7 @@ struct Prob {
   double* llpart;      // [ll_blocks] per-CTA log-likelihood partials
   unsigned* counters;  // arrival counters of the split reductions (zero between launches)
   const float* lam;    // [N][F][T] lambda formed by the tensor-core GEMM (mixed form), or null
+  float* nu_out;       // [N][F] nu_nf of the normalisation written by k_bin, or null
   unsigned wait_limit; // 0: the normal bound of the tensor-core kernels' waits; else a test
                        // limit for their consumer waits, with one wait on an mbarrier nothing
                        // arrives at (makes the timeout path run; drains keep the full bound)

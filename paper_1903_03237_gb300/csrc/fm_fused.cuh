@@ -530,6 +530,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bin(Prob p, float* __restrict__
         for (int m = 0; m < MAXM; ++m)
           if (m < M) gs[n * MAXM + m] = gv[m] / nu;
         nus[n] = nu;
+        if (p.nu_out) p.nu_out[(size_t)n * F + f] = nu;
         if (!(nu > 0.f) || !isfinite(nu)) flag(p.status, ST_NONFINITE);
       }
       __syncthreads();

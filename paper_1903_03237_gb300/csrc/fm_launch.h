@@ -93,6 +93,42 @@ int gtc_frames_per_stage();
 cudaError_t launch_apply(float* fac, const float* C, int S, int N, int K, int own, unsigned* status,
                          cudaStream_t st);
 
+// FastMNMF-DP (fm_dp.cu): the deep-prior speech source (source 0) and NMF noise sources
+// (1..N-1) around the unconstrained-model context's lambda, g~, Q and x~.
+struct DpArgs {
+  Prob p;                        // the inner context's problem (X, G, Qf, xt, status, ...)
+  float* lam = nullptr;          // [N][F][T]
+  float* u = nullptr;            // [F]
+  float* v = nullptr;            // [T]
+  float* Z = nullptr;            // [T][D]
+  float* R = nullptr;            // [F][T] decoder output of Z
+  float* Wn = nullptr;           // [N-1][K][F]
+  float* Hn = nullptr;           // [N-1][K][T]
+  const float* W1 = nullptr;     // [Hd][D]
+  const float* b1 = nullptr;     // [Hd]
+  const float* W2 = nullptr;     // [F][Hd]
+  const float* b2 = nullptr;     // [F]
+  int D = 0, Hd = 0, K = 0;
+  const float* xi = nullptr;     // [S][T][D] draws of this iteration
+  const float* logu = nullptr;   // [S][T]
+  int S = 0;
+  float sqrt_eps = 0.f;
+  unsigned long long* n_acc = nullptr;  // accepted proposals (accumulated)
+  float* loggamma = nullptr;     // [S][T] log gamma of every proposal, or null
+  const float* nu = nullptr;     // [N][F] nu of the last normalisation (k_bin)
+  int maxm = 8;
+  int tb = 4;                    // frames per Metropolis CTA (1, 2 or 4)
+};
+// Frames per Metropolis CTA and its dynamic shared memory: the largest of 4, 2, 1 whose
+// staging fits in `limit` bytes (0 if none fits).
+int dp_mh_frames(int F, int M, int D, int Hd, size_t limit, size_t* smem);
+cudaError_t dp_prepare(int maxm, size_t mh_smem);
+cudaError_t dp_launch_init(const DpArgs& a, cudaStream_t st);     // R from Z, lambda of every source
+cudaError_t dp_launch_mh(const DpArgs& a, size_t smem, cudaStream_t st);  // S proposals per frame
+cudaError_t dp_launch_fsweep(const DpArgs& a, int mode, cudaStream_t st);  // per bin: u (0) or noise W (1)
+cudaError_t dp_launch_tsweep(const DpArgs& a, int mode, cudaStream_t st);  // per frame: v (0) or noise H (1)
+cudaError_t dp_launch_norm(const DpArgs& a, cudaStream_t st);     // nu into u, W; mu into v, H
+
 // Largest dynamic shared memory of the IP kernel's prefetch (X and y~ rows, g~, W of a bin):
 // small enough that four or more IP CTAs stay resident per SM.
 constexpr int kIpPrefetchMax = 40 * 1024;

@@ -41,13 +41,22 @@ EXPORTS = ["fmnmf_default_opts", "fmnmf_init", "fmnmf_reset", "fmnmf_restart", "
            "fmnmf_autotune", "fmnmf_batch_autotune", "fmnmf_get_tuning", "fmnmf_set_tuning",
            "fmnmf_footprint", "fmnmf_server_create", "fmnmf_server_submit", "fmnmf_server_poll",
            "fmnmf_server_wait", "fmnmf_server_result", "fmnmf_server_stats", "fmnmf_server_destroy",
-           "fmnmf_init_spectral", "fmnmf_stft_frames", "fmnmf_stft", "fmnmf_istft"]
+           "fmnmf_init_spectral", "fmnmf_stft_frames", "fmnmf_stft", "fmnmf_istft",
+           "fmnmf_dp_default_opts", "fmnmf_dp_create", "fmnmf_dp_set_decoder", "fmnmf_dp_set_state",
+           "fmnmf_dp_get_state", "fmnmf_dp_iterate", "fmnmf_dp_metropolis", "fmnmf_dp_sync",
+           "fmnmf_dp_loglik", "fmnmf_dp_accepted", "fmnmf_dp_separate", "fmnmf_dp_destroy",
+           "fmnmf_dp_last_error"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("update_mask", ctypes.c_uint), ("normalise", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("hbm_budget", ctypes.c_size_t), ("schedule", ctypes.c_int),
                 ("source_model", ctypes.c_int)]
+
+
+class DPOpts(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("Hd", ctypes.c_int), ("n_proposals", ctypes.c_int), ("eps", ctypes.c_float),
+                ("normalise", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -95,6 +104,19 @@ _sig = {
     "fmnmf_stft_frames": (_S, [_I, _I, _I, ctypes.POINTER(_I)]),
     "fmnmf_stft": (_S, [_P, _I, _I, _I, _I, _P, _P]),
     "fmnmf_istft": (_S, [_P, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "fmnmf_dp_default_opts": (_S, [ctypes.POINTER(DPOpts)]),
+    "fmnmf_dp_create": (_S, [ctypes.POINTER(_P), _P, _I, _I, _I, _I, _I, _I, ctypes.POINTER(DPOpts)]),
+    "fmnmf_dp_set_decoder": (_S, [_P, _P, _P, _P, _P]),
+    "fmnmf_dp_set_state": (_S, [_P] + [_P] * 7),
+    "fmnmf_dp_get_state": (_S, [_P] + [_P] * 7),
+    "fmnmf_dp_iterate": (_S, [_P, _I, _P, _P, _I]),
+    "fmnmf_dp_metropolis": (_S, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_longlong)]),
+    "fmnmf_dp_sync": (_S, [_P]),
+    "fmnmf_dp_loglik": (_S, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "fmnmf_dp_accepted": (_S, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "fmnmf_dp_separate": (_S, [_P, _P, _I]),
+    "fmnmf_dp_destroy": (_S, [_P]),
+    "fmnmf_dp_last_error": (ctypes.c_char_p, [_P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -347,6 +369,121 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _check_dp(st: int, dp=None):
+    if st != OK:
+        msg = _lib.fmnmf_dp_last_error(dp)
+        raise FastMNMFError(st, msg.decode() if msg else "")
+
+
+class DPContext:
+    """FastMNMF-DP (Sec. III-B-3, III-C-3): a deep-prior speech source (source 0) and NMF noise
+    sources (1..N-1) for one mixture (wraps fmnmf_dp).  Host arrays are NumPy; the Metropolis
+    draws may be torch CUDA tensors (kept resident on the device)."""
+
+    def __init__(self, X, N: int, K: int, *, D: int = 16, Hd: int = 128, n_proposals: int = 30,
+                 eps: float = 1e-4, normalise: bool = True, stream=None):
+        o = DPOpts()
+        _check_dp(_lib.fmnmf_dp_default_opts(ctypes.byref(o)))
+        o.D, o.Hd, o.n_proposals, o.eps = D, Hd, n_proposals, eps
+        o.normalise = 1 if normalise else 0
+        o.stream = stream
+        self._dp = _P()
+        if torch is not None and isinstance(X, torch.Tensor) and X.is_cuda:
+            assert X.dtype == torch.complex64 and X.dim() == 3 and X.is_contiguous()
+            F, T, M = X.shape
+            torch.cuda.synchronize(X.device)
+            st = _lib.fmnmf_dp_create(ctypes.byref(self._dp), X.data_ptr(), 1, F, T, M, N, K, ctypes.byref(o))
+        else:
+            Xh, ptr = _host_ptr(X, np.complex64)
+            F, T, M = Xh.shape
+            st = _lib.fmnmf_dp_create(ctypes.byref(self._dp), ptr, 0, F, T, M, N, K, ctypes.byref(o))
+        _check_dp(st, None)
+        self.F, self.T, self.M, self.N, self.K = F, T, M, N, K
+        self.D, self.Hd, self.S = D, Hd, n_proposals
+
+    def close(self):
+        if self._dp:
+            _lib.fmnmf_dp_destroy(self._dp)
+            self._dp = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_decoder(self, W1, b1, W2, b2):
+        a = [_host_ptr(x, np.float32) for x in (W1, b1, W2, b2)]
+        assert a[0][0].shape == (self.Hd, self.D) and a[2][0].shape == (self.F, self.Hd)
+        _check_dp(_lib.fmnmf_dp_set_decoder(self._dp, *[p for _, p in a]), self._dp)
+
+    def set_state(self, Z, u, v, W, H, G, Q):
+        a = [_host_ptr(x, np.float32) for x in (Z, u, v, W, H, G)]
+        q = _host_ptr(Q, np.complex64)
+        assert a[0][0].shape == (self.T, self.D)
+        _check_dp(_lib.fmnmf_dp_set_state(self._dp, *[p for _, p in a], q[1]), self._dp)
+
+    def get_state(self):
+        F, T, M, N, K, D = self.F, self.T, self.M, self.N, self.K, self.D
+        Z = np.empty((T, D), np.float32)
+        u = np.empty(F, np.float32)
+        v = np.empty(T, np.float32)
+        W = np.empty((N - 1, K, F), np.float32)
+        H = np.empty((N - 1, K, T), np.float32)
+        G = np.empty((N, F, M), np.float32)
+        Q = np.empty((F, M, M), np.complex64)
+        _check_dp(_lib.fmnmf_dp_get_state(self._dp, *[x.ctypes.data for x in (Z, u, v, W, H, G, Q)]), self._dp)
+        return Z, u, v, W, H, G, Q
+
+    def _draws(self, xi, logu):
+        if torch is not None and isinstance(xi, torch.Tensor) and xi.is_cuda:
+            assert xi.dtype == torch.float32 and logu.dtype == torch.float32
+            assert xi.is_contiguous() and logu.is_contiguous()
+            return xi.data_ptr(), logu.data_ptr(), 1, None
+        xh, xp = _host_ptr(xi, np.float32)
+        lh, lp = _host_ptr(logu, np.float32)
+        return xp, lp, 0, (xh, lh)
+
+    def iterate(self, n: int, xi, logu):
+        """n iterations; xi [n][S][T][D], logu [n][S][T] (NumPy, or CUDA tensors on the device)."""
+        xp, lp, dev, keep = self._draws(xi, logu)
+        if not dev:
+            assert keep[0].shape == (n, self.S, self.T, self.D) and keep[1].shape == (n, self.S, self.T)
+        _check_dp(_lib.fmnmf_dp_iterate(self._dp, n, xp, lp, dev), self._dp)
+
+    def metropolis(self, xi, logu):
+        """The Z block alone: xi [S][T][D], logu [S][T]; returns (log gamma [S][T], accepted)."""
+        xp, lp, dev, keep = self._draws(xi, logu)
+        lg = np.empty((self.S, self.T), np.float32)
+        n = ctypes.c_longlong(0)
+        _check_dp(_lib.fmnmf_dp_metropolis(self._dp, xp, lp, dev, lg.ctypes.data, ctypes.byref(n)), self._dp)
+        return lg, n.value
+
+    def sync(self):
+        _check_dp(_lib.fmnmf_dp_sync(self._dp), self._dp)
+
+    def loglik(self) -> float:
+        v = ctypes.c_double(0.0)
+        _check_dp(_lib.fmnmf_dp_loglik(self._dp, ctypes.byref(v)), self._dp)
+        return v.value
+
+    def accepted(self) -> int:
+        n = ctypes.c_longlong(0)
+        _check_dp(_lib.fmnmf_dp_accepted(self._dp, ctypes.byref(n)), self._dp)
+        return n.value
+
+    def separate(self) -> np.ndarray:
+        out = np.empty((self.N, self.F, self.T, self.M), np.complex64)
+        _check_dp(_lib.fmnmf_dp_separate(self._dp, out.ctypes.data, 0), self._dp)
+        return out
 
 
 def stft_frames(S: int, L: int = 1024, hop: int = 256) -> int:
