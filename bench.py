@@ -454,6 +454,12 @@ def run_ours(args):
                    "burst_200_at_once": {"requests": 200, "continuous_batching": {k: cb2[k] for k in keep},
                                          "one_at_a_time": {k: fifo2[k] for k in keep}}}
 
+    dp = None
+    if rank == 0 and not args.no_dp:
+        dp = dp_measure(fm, torch, 20, 3)
+        if not args.no_cpu_baseline:
+            dp["oracle_s_per_iteration"] = dp_oracle_seconds()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         # a bounded sample: all bins of c1 (2 iterations), the first 96 bins of larger mixtures
@@ -482,6 +488,8 @@ def run_ours(args):
             line[name] = o
         if serving is not None:
             line["serving"] = serving
+        if dp is not None:
+            line["fastmnmf_dp"] = dp
         if "plain_fp32" in others:
             line["speedup_vs_plain_fp32"] = res["value"] / others["plain_fp32"]["value"]
         # the whole iteration against HBM by the minimum traffic of one iteration with lambda,
@@ -495,6 +503,106 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# FastMNMF-DP at the paper's setting (Sec. IV-A): 8 s at 16 kHz with a 1024-point window and
+# a 256-point shift (F = 513, T = 500), M = 5, speech + one noise source (N = 2) with K = 16
+# noise bases, D = 16, 30 proposals per frame, eps = 1e-4; decoder width 128 (random weights).
+DP_SETTING = dict(F=513, T=500, M=5, N=2, K=16, D=16, Hd=128, S=30, eps=1e-4)
+DP_PAPER_GPU_MS = 98.0   # Table I (GPU, GTX 1080 Ti): FastMNMF-DP, N = 2, K = 16, 0.98 decisec per iteration
+
+
+def dp_flops_mh(F, T, M, D, Hd, S):
+    """Algorithmic flops of one Metropolis launch: per proposal and frame the decoder (hidden
+    layer 2 D Hd, output layer 2 Hd F) and the log gamma terms (about 8 flops per (f, m) besides
+    one exponential per f and one division pair and one logarithm per (f, m))."""
+    return float(S) * T * (2.0 * D * Hd + 2.0 * Hd * F + 8.0 * F * M)
+
+
+def dp_measure(fm, torch, steps, warmup):
+    """ms per FastMNMF-DP iteration at the paper's setting, device-resident draws (timed with
+    events on the context's stream over `steps` consecutive iterations), the Metropolis launch
+    alone, and end to end with the draws copied from pinned host memory inside the timed region
+    and the log-likelihood read back."""
+    from paper_1903_03237_gb300.synth import make_mixture, make_dp_state, make_decoder, make_dp_draws
+    c = DP_SETTING
+    F, T, M, N, K, Dd, Hd, S = c["F"], c["T"], c["M"], c["N"], c["K"], c["D"], c["Hd"], c["S"]
+    X = make_mixture(F, T, M, N, K, 0).X
+    state = make_dp_state(F, T, M, N, K, Dd, 0)
+    theta = make_decoder(F, Dd, Hd, 0)
+    n = warmup + steps
+    xi, logu = make_dp_draws(n, S, T, Dd, 0)
+    xid, lud = torch.from_numpy(xi).cuda(), torch.from_numpy(logu).cuda()
+    xih, luh = torch.from_numpy(xi).pin_memory(), torch.from_numpy(logu).pin_memory()
+    st = torch.cuda.Stream()
+    out = {"workload": "FastMNMF-DP, F513 T500 M5 N2 K16, D16, decoder width 128 (seeded random weights), "
+                       "30 proposals per frame, eps 1e-4; consecutive iterations (state L2-resident, as in a run)",
+           "unit": "ms per iteration", "paper_gtx1080ti_ms": DP_PAPER_GPU_MS}
+    with fm.DPContext(X, N, K, D=Dd, Hd=Hd, n_proposals=S, eps=c["eps"], stream=st.cuda_stream) as dp:
+        dp.set_decoder(*theta)
+        dp.set_state(*state)
+        dp.iterate(warmup, xid[:warmup], lud[:warmup])
+        dp.sync()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dp.iterate(steps, xid[warmup:], lud[warmup:])
+        e1.record(st)
+        dp.sync()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # the Metropolis launch alone (one iteration's proposals), bracketed by events on the
+        # context's stream; the call also reads two 8-byte counters
+        dp.set_state(*state)
+        torch.cuda.synchronize()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(st)
+        fm.lib().fmnmf_dp_metropolis(dp._dp, xid[0].data_ptr(), lud[0].data_ptr(), 1, None, None)
+        e3.record(st)
+        dp.sync()
+        torch.cuda.synchronize()
+        mh_ms = e2.elapsed_time(e3)
+        # end to end: draws from pinned host memory, copied inside the timed region, and the
+        # log-likelihood read back
+        dp.set_state(*state)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs = torch.empty_like(xid[:steps])
+        ls = torch.empty_like(lud[:steps])
+        with torch.cuda.stream(st):
+            xs.copy_(xih[warmup:], non_blocking=True)
+            ls.copy_(luh[warmup:], non_blocking=True)
+        dp.iterate(steps, xs, ls)
+        ll = dp.loglik()
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / steps
+        acc = dp.accepted()
+    fl = dp_flops_mh(F, T, M, Dd, Hd, S)
+    ach = fl / (mh_ms * 1e-3) / 1e12
+    out.update({"ms_per_iteration": ms, "iterations_per_s": 1e3 / ms, "e2e_ms_per_iteration": e2e_ms,
+                "h2d_bytes_per_iteration": S * T * (Dd + 1) * 4, "d2h_bytes_per_call": 8,
+                "vs_paper_gpu": DP_PAPER_GPU_MS / ms, "loglik_final": ll, "accepted_last_run": acc,
+                "steps": steps, "warmup": warmup, "metropolis_ms": mh_ms, "metropolis_share": mh_ms / ms,
+                "metropolis_roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": ach / FP32_PEAK_TFLOPS, "flops_per_launch": fl,
+                                        "kernel": "k_dp_mh"}})
+    return out
+
+
+def dp_oracle_seconds():
+    """Seconds of the float64 oracle (as it stands) for one FastMNMF-DP iteration at the same
+    setting, timed on the host."""
+    from oracle import fastmnmf_dp_oracle as DPO
+    from paper_1903_03237_gb300.synth import make_mixture, make_dp_state, make_decoder, make_dp_draws
+    c = DP_SETTING
+    F, T, M, N, K, Dd, Hd, S = c["F"], c["T"], c["M"], c["N"], c["K"], c["D"], c["Hd"], c["S"]
+    X = make_mixture(F, T, M, N, K, 0).X.astype(np.complex128)
+    state = [a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+             for a in make_dp_state(F, T, M, N, K, Dd, 0)]
+    theta = tuple(a.astype(np.float64) for a in make_decoder(F, Dd, Hd, 0))
+    xi, logu = make_dp_draws(1, S, T, Dd, 0)
+    t0 = time.perf_counter()
+    DPO.iterate_dp(X, *state, theta, xi.astype(np.float64), logu.astype(np.float64), c["eps"], n_iter=1)
+    return time.perf_counter() - t0
 
 
 def c3_instances(n=64, seed=0):
@@ -689,6 +797,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planned launch shapes (no tuner run)")
     ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving replay of the default run")
+    ap.add_argument("--no-dp", action="store_true", help="skip the FastMNMF-DP measurement of the default run")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])

@@ -1789,15 +1789,16 @@ fmnmf_status fmnmf_dp_create(fmnmf_dp** out, const void* X, int x_on_device, int
     return st;
   };
   if (!ctx->fused) return fail(FMNMF_EINVAL, "FastMNMF-DP: N*M=%d is too large for the per-bin kernel", N * M);
-  int dev = 0, optin = 0;
+  int dev = 0, optin = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(FMNMF_ECUDA, "FastMNMF-DP: device query failed");
   fmnmf_dp* d = new fmnmf_dp;
   d->ctx = ctx;
   d->o = o;
   d->F = F; d->T = T; d->M = M; d->N = N; d->K = K;
-  d->tb = dp_mh_frames(F, M, o.D, o.Hd, (size_t)optin - 1024, &d->mh_smem);
+  d->tb = dp_mh_frames(F, T, M, o.D, o.Hd, sms, (size_t)optin - 1024, &d->mh_smem);
   if (d->tb == 0) {
     delete d;
     return fail(FMNMF_EINVAL, "FastMNMF-DP: F*M=%d too large to stage one frame in shared memory", F * M);

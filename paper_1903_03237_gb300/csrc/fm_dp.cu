@@ -23,10 +23,11 @@
 namespace fm {
 namespace {
 
-constexpr int kDpTT = 8;                  // frames per CTA of the per-frame sweeps
-constexpr int kDpFC = kThreads / kDpTT;   // bins per chunk of the per-frame sweeps (32)
+constexpr int kDpTT = 2;                  // frames per CTA of the per-frame sweeps
+constexpr int kDpFC = kThreads / kDpTT;   // bins per chunk of the per-frame sweeps (128)
 constexpr int kDpMaxPairs = 256;          // (N-1) K noise bases per sweep CTA
-constexpr int kDpItems = kDpMaxPairs * kDpTT / kThreads;  // H-sweep items per thread (8)
+constexpr int kDpItems = kDpMaxPairs * kDpTT / kThreads;  // H-sweep items per thread (2)
+constexpr int kMhMaxThreads = 576;       // Metropolis CTA: one bin per thread up to F = 576
 
 
 // Shared-memory layout (floats) of the Metropolis kernel for TB frames.
@@ -47,7 +48,7 @@ __host__ __device__ inline MhLayout mh_layout(int F, int M, int TB, int D, int H
   L.zs = take(TB * D);         // z [tb][d]
   L.zn = take(TB * D);         // proposal
   L.vs = take(TB);             // v_t
-  L.red = take((kThreads / 32) * TB);
+  L.red = take((kMhMaxThreads / 32) * TB);
   L.total = o;
   return L;
 }
@@ -69,7 +70,7 @@ __device__ __forceinline__ void bin_y(const float* __restrict__ lam, const float
 // The hidden layer of nt frames: h[tb][j] = tanh(b1_j + sum_d W1[j][d] z[tb][d]).
 __device__ __forceinline__ void hidden_layer(const float* __restrict__ W1, const float* __restrict__ b1,
                                              const float* z, float* h, int nt, int D, int Hd) {
-  for (int e = threadIdx.x; e < nt * Hd; e += kThreads) {
+  for (int e = threadIdx.x; e < nt * Hd; e += blockDim.x) {
     const int tb = e / Hd, j = e - tb * Hd;
     float a = b1[j];
     const float* w = W1 + (size_t)j * D;
@@ -85,6 +86,7 @@ __device__ __forceinline__ void decode_bin(const float* __restrict__ W2, const f
   const float4* w = reinterpret_cast<const float4*>(W2 + (size_t)f * Hd);
 #pragma unroll
   for (int i = 0; i < TB; ++i) s[i] = 0.f;
+#pragma unroll 4
   for (int j4 = 0; j4 < (Hd >> 2); ++j4) {
     const float4 wv = __ldg(w + j4);
 #pragma unroll
@@ -156,12 +158,12 @@ __global__ void __launch_bounds__(kThreads) k_dp_lam_noise(DpArgs a) {
 // so nothing cancels between two large sums).  Accepted where log u < log gamma_t.
 // ---------------------------------------------------------------------------------------
 template <int MAXM, int TB>
-__global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
+__global__ void __launch_bounds__(kMhMaxThreads) k_dp_mh(DpArgs a) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ int acc_s[TB];
   const int F = a.p.F, T = a.p.T, M = a.p.M, N = a.p.N, D = a.D, Hd = a.Hd;
   const size_t FT = (size_t)F * T;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nthr = blockDim.x;
   const int t0 = blockIdx.x * TB, nt = min(TB, T - t0);
   const MhLayout L = mh_layout(F, M, TB, D, Hd);
   float* xs = dsm + L.xs;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
 
   // ---- stage the frames' x~, y~^{-0}, r and z, and the bins' g~_0 and u
   const int run = nt * M;  // x~ of the tile's frames is contiguous per bin
-  for (int e = tid; e < F * run; e += kThreads) {
+  for (int e = tid; e < F * run; e += nthr) {
     const int f = e / run, r = e - f * run, tb = r / M, m = r - tb * M;
     const size_t ft = (size_t)f * T + t0 + tb;
     xs[(tb * M + m) * F + f] = a.p.xt[ft * M + m];
@@ -186,16 +188,16 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
     for (int n = 1; n < N; ++n) y = fmaf(a.lam[n * FT + ft], a.p.G[((size_t)n * F + f) * M + m], y);
     yr[(tb * M + m) * F + f] = y;
   }
-  for (int e = tid; e < F * M; e += kThreads) {
+  for (int e = tid; e < F * M; e += nthr) {
     const int f = e / M, m = e - f * M;
     g0[m * F + f] = a.p.G[(size_t)f * M + m];
   }
-  for (int f = tid; f < F; f += kThreads) {
+  for (int f = tid; f < F; f += nthr) {
     uf[f] = a.u[f];
     for (int tb = 0; tb < nt; ++tb) rold[tb * F + f] = a.R[(size_t)f * T + t0 + tb];
   }
-  for (int e = tid; e < TB * Hd; e += kThreads) h[e] = 0.f;  // rows of absent frames stay 0
-  for (int e = tid; e < nt * D; e += kThreads) zs[e] = a.Z[(size_t)t0 * D + e];
+  for (int e = tid; e < TB * Hd; e += nthr) h[e] = 0.f;  // rows of absent frames stay 0
+  for (int e = tid; e < nt * D; e += nthr) zs[e] = a.Z[(size_t)t0 * D + e];
   if (tid < nt) vs[tid] = a.v[t0 + tid];
   unsigned n_acc = 0;
   __syncthreads();
@@ -203,14 +205,14 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
   for (int s = 0; s < a.S; ++s) {
     // proposal z' = z + sqrt(eps) xi
     const float* xi = a.xi + ((size_t)s * T + t0) * D;
-    for (int e = tid; e < nt * D; e += kThreads) zn[e] = fmaf(a.sqrt_eps, xi[e], zs[e]);
+    for (int e = tid; e < nt * D; e += nthr) zn[e] = fmaf(a.sqrt_eps, xi[e], zs[e]);
     __syncthreads();
     hidden_layer(a.W1, a.b1, zn, h, nt, D, Hd);
     __syncthreads();
     float part[TB];
 #pragma unroll
     for (int tb = 0; tb < TB; ++tb) part[tb] = 0.f;
-    for (int f = tid; f < F; f += kThreads) {
+    for (int f = tid; f < F; f += nthr) {
       float sv[TB];
       decode_bin<TB>(a.W2, a.b2, h, Hd, f, sv);
       const float u = uf[f];
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
     __syncthreads();
     if (tid < nt) {
       float lg = 0.f;
-      for (int w = 0; w < kThreads / 32; ++w) lg += red[w * TB + tid];
+      for (int w = 0; w < (nthr >> 5); ++w) lg += red[w * TB + tid];
       const int acc = a.logu[(size_t)s * T + t0 + tid] < lg;
       acc_s[tid] = acc;
       n_acc += acc;
@@ -253,9 +255,9 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
     }
     __syncthreads();
     // accepted frames take the proposal (each thread copies what it wrote or will read)
-    for (int e = tid; e < nt * D; e += kThreads)
+    for (int e = tid; e < nt * D; e += nthr)
       if (acc_s[e / D]) zs[e] = zn[e];
-    for (int f = tid; f < F; f += kThreads)
+    for (int f = tid; f < F; f += nthr)
 #pragma unroll
       for (int tb = 0; tb < TB; ++tb)
         if (tb < nt && acc_s[tb]) rold[tb * F + f] = rnew[tb * F + f];
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(kThreads) k_dp_mh(DpArgs a) {
   }
 
   // ---- the sampled z, its r and lambda_ft0 of the tile's frames
-  for (int e = tid; e < nt * D; e += kThreads) a.Z[(size_t)t0 * D + e] = zs[e];
-  for (int f = tid; f < F; f += kThreads)
+  for (int e = tid; e < nt * D; e += nthr) a.Z[(size_t)t0 * D + e] = zs[e];
+  for (int f = tid; f < F; f += nthr)
     for (int tb = 0; tb < nt; ++tb) {
       const size_t i = (size_t)f * T + t0 + tb;
       const float r = rold[tb * F + f];
@@ -428,13 +430,17 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
   for (int f0 = 0; f0 < F; f0 += kDpFC) {
     const int f = f0 + fl;
     if (valid && f < F) {
-      float gv[8 * MAXM];
-      for (int e = 0; e < N * MAXM; ++e) {
-        const int n = e / MAXM, m = e - n * MAXM;
-        gv[e] = (m < M) ? a.p.G[((size_t)n * F + f) * M + m] : 0.f;
-      }
+      const float* gf = a.p.G + (size_t)f * M;  // g~_nfm at gf[n F M + m]
+      const size_t gn = (size_t)F * M;
       float y[MAXM], A[MAXM], B[MAXM];
-      bin_y<MAXM>(a.lam, gv, N, M, FT, (size_t)f * T + t, y);
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) y[m] = 0.f;
+      for (int n = 0; n < N; ++n) {
+        const float l = a.lam[n * FT + (size_t)f * T + t];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) y[m] = fmaf(l, gf[n * gn + m], y[m]);
+      }
       const float* xp = a.p.xt + ((size_t)f * T + t) * M;
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
@@ -444,10 +450,11 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
       if (mode == 0) {
         float P = 0.f, Rr = 0.f;
 #pragma unroll
-        for (int m = 0; m < MAXM; ++m) {
-          P = fmaf(gv[m], A[m], P);
-          Rr = fmaf(gv[m], B[m], Rr);
-        }
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) {
+            P = fmaf(gf[m], A[m], P);
+            Rr = fmaf(gf[m], B[m], Rr);
+          }
         const float w = a.u[f] * a.R[(size_t)f * T + t];
         num = fmaf(w, P, num);
         den = fmaf(w, Rr, den);
@@ -455,10 +462,11 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
         for (int n = 1; n < N; ++n) {
           float P = 0.f, Rr = 0.f;
 #pragma unroll
-          for (int m = 0; m < MAXM; ++m) {
-            P = fmaf(gv[n * MAXM + m], A[m], P);
-            Rr = fmaf(gv[n * MAXM + m], B[m], Rr);
-          }
+          for (int m = 0; m < MAXM; ++m)
+            if (m < M) {
+              P = fmaf(gf[n * gn + m], A[m], P);
+              Rr = fmaf(gf[n * gn + m], B[m], Rr);
+            }
           Ps[n - 1][fl][tl] = P;
           Rs[n - 1][fl][tl] = Rr;
         }
@@ -551,13 +559,15 @@ __global__ void __launch_bounds__(kThreads) k_dp_norm(DpArgs a) {
 
 }  // namespace
 
-int dp_mh_frames(int F, int M, int D, int Hd, size_t limit, size_t* smem) {
+int dp_mh_frames(int F, int T, int M, int D, int Hd, int sms, size_t limit, size_t* smem) {
+  // the most frames per CTA (each row of W2 read once serves them all) that still gives every
+  // SM about 1.5 CTAs and fits the staging in shared memory
   for (int tb = 4; tb >= 1; tb >>= 1) {
     const size_t b = (size_t)mh_layout(F, M, tb, D, Hd).total * sizeof(float);
-    if (b <= limit) {
-      if (smem) *smem = b;
-      return tb;
-    }
+    if (b > limit) continue;
+    if (tb > 1 && 2 * ((T + tb - 1) / tb) < 3 * sms) continue;
+    if (smem) *smem = b;
+    return tb;
   }
   return 0;
 }
@@ -570,13 +580,21 @@ cudaError_t mh_prepare(size_t smem) {
   if ((e = cudaFuncSetAttribute(k_dp_mh<MAXM, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_dp_mh<MAXM, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
+// Threads of a Metropolis CTA: whole warps, one bin per thread where F allows, the bins
+// spread evenly over the rounds otherwise (no round for a few tail bins).
+int mh_threads(int F) {
+  const int rounds = (F + kMhMaxThreads - 1) / kMhMaxThreads;
+  const int per = (F + rounds - 1) / rounds;
+  return ((per + 31) / 32) * 32;
+}
 template <int MAXM>
 cudaError_t mh_launch(const DpArgs& a, size_t smem, cudaStream_t st) {
   const dim3 grid((a.p.T + a.tb - 1) / a.tb);
+  const int nthr = mh_threads(a.p.F);
   switch (a.tb) {
-    case 4: k_dp_mh<MAXM, 4><<<grid, kThreads, smem, st>>>(a); break;
-    case 2: k_dp_mh<MAXM, 2><<<grid, kThreads, smem, st>>>(a); break;
-    default: k_dp_mh<MAXM, 1><<<grid, kThreads, smem, st>>>(a); break;
+    case 4: k_dp_mh<MAXM, 4><<<grid, nthr, smem, st>>>(a); break;
+    case 2: k_dp_mh<MAXM, 2><<<grid, nthr, smem, st>>>(a); break;
+    default: k_dp_mh<MAXM, 1><<<grid, nthr, smem, st>>>(a); break;
   }
   return cudaGetLastError();
 }

@@ -120,8 +120,8 @@ struct DpArgs {
   int tb = 4;                    // frames per Metropolis CTA (1, 2 or 4)
 };
 // Frames per Metropolis CTA and its dynamic shared memory: the largest of 4, 2, 1 whose
-// staging fits in `limit` bytes (0 if none fits).
-int dp_mh_frames(int F, int M, int D, int Hd, size_t limit, size_t* smem);
+// staging fits in `limit` bytes and that leaves about 1.5 CTAs per SM (0 if none fits).
+int dp_mh_frames(int F, int T, int M, int D, int Hd, int sms, size_t limit, size_t* smem);
 cudaError_t dp_prepare(int maxm, size_t mh_smem);
 cudaError_t dp_launch_init(const DpArgs& a, cudaStream_t st);     // R from Z, lambda of every source
 cudaError_t dp_launch_mh(const DpArgs& a, size_t smem, cudaStream_t st);  // S proposals per frame
