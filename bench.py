@@ -765,6 +765,18 @@ def profile_run(args):
     build()
     from paper_1903_03237_gb300 import fastmnmf as fm
     from paper_1903_03237_gb300.synth import make_mixture
+    if args.workload == "dp":
+        # FastMNMF-DP at the paper's setting: 4 iterations with device-resident draws
+        from paper_1903_03237_gb300.synth import make_dp_state, make_decoder, make_dp_draws
+        c = DP_SETTING
+        F, T, M, N, K, Dd, Hd, S = c["F"], c["T"], c["M"], c["N"], c["K"], c["D"], c["Hd"], c["S"]
+        xi, logu = make_dp_draws(4, S, T, Dd, 0)
+        with fm.DPContext(make_mixture(F, T, M, N, K, 0).X, N, K, D=Dd, Hd=Hd, n_proposals=S, eps=c["eps"]) as dp:
+            dp.set_decoder(*make_decoder(F, Dd, Hd, 0))
+            dp.set_state(*make_dp_state(F, T, M, N, K, Dd, 0))
+            dp.iterate(4, torch.from_numpy(xi).cuda(), torch.from_numpy(logu).cuda())
+            print("profile run ok, log-likelihood", dp.loglik(), "accepted", dp.accepted())
+        return
     w = WORKLOAD
     F = args.bins or w["F"]
     mix = make_mixture(F, w["T"], w["M"], w["N"], w["K"], 0, diffuse_frac=w["diffuse"])
@@ -784,8 +796,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu captures, no JSON line")
     ap.add_argument("--bins", type=int, default=0, help="--profile-run: number of frequency bins (default: the workload's)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c3", "c4"], default="c1",
-                    help="c1 (default, the headline line), c2 (large mixture), c3 (batched mixtures), c4 (serving)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c3", "c4", "dp"], default="c1",
+                    help="c1 (default, the headline line), c2 (large mixture), c3 (batched mixtures), c4 (serving), "
+                         "dp (FastMNMF-DP at the paper's setting; with --profile-run only)")
     ap.add_argument("--requests", type=int, default=2000, help="c4: number of requests")
     ap.add_argument("--max-active", type=int, default=16, help="c4: resident requests")
     ap.add_argument("--rate", type=float, default=20.0,
@@ -801,6 +814,8 @@ def main():
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c1"])
+    if args.workload == "dp" and not args.profile_run:
+        ap.error("--workload dp is a --profile-run workload; the default line measures FastMNMF-DP under fastmnmf_dp")
     if args.profile_run:
         profile_run(args)
     elif args.workload == "c3":
