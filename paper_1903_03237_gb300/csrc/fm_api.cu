@@ -1674,8 +1674,7 @@ struct fmnmf_dp {
   float *xi = nullptr, *logu = nullptr, *lg = nullptr;
   unsigned long long* acc = nullptr;
   int draw_iters = 0;  // iterations of host draws the device buffers hold
-  size_t mh_smem = 0;
-  int tb = 0;
+  DpMhPlan mh;  // launch shape of the Metropolis kernel
   bool have_decoder = false, have_state = false;
 };
 
@@ -1695,7 +1694,7 @@ DpArgs dp_args(fmnmf_dp* d) {
   a.n_acc = d->acc;
   a.nu = d->nu;
   a.maxm = d->ctx->maxm;
-  a.tb = d->tb;
+  a.tb = d->mh.TB;
   return a;
 }
 
@@ -1711,7 +1710,7 @@ cudaError_t enqueue_dp_iteration(fmnmf_dp* d, const float* xi, const float* logu
   cudaError_t e;
   if (a.S > 0) {
     c->launches++;
-    if ((e = dp_launch_mh(a, d->mh_smem, c->st)) != cudaSuccess) return e;
+    if ((e = dp_launch_mh(a, d->mh, c->st)) != cudaSuccess) return e;
   }
   c->launches += 2;
   if ((e = dp_launch_fsweep(a, 0, c->st)) != cudaSuccess) return e;
@@ -1798,12 +1797,12 @@ fmnmf_status fmnmf_dp_create(fmnmf_dp** out, const void* X, int x_on_device, int
   d->ctx = ctx;
   d->o = o;
   d->F = F; d->T = T; d->M = M; d->N = N; d->K = K;
-  d->tb = dp_mh_frames(F, T, M, o.D, o.Hd, sms, (size_t)optin - 1024, &d->mh_smem);
-  if (d->tb == 0) {
+  d->mh = dp_mh_plan(F, T, M, o.D, o.Hd, sms, (size_t)optin - 1024);
+  if (d->mh.C == 0) {
     delete d;
     return fail(FMNMF_EINVAL, "FastMNMF-DP: F*M=%d too large to stage one frame in shared memory", F * M);
   }
-  if (dp_prepare(ctx->maxm, d->mh_smem) != cudaSuccess) {
+  if (dp_prepare(ctx->maxm, d->mh) != cudaSuccess) {
     delete d;
     return fail(FMNMF_ECUDA, "FastMNMF-DP: shared-memory attribute failed");
   }
@@ -1962,7 +1961,7 @@ fmnmf_status fmnmf_dp_metropolis(fmnmf_dp* d, const float* xi, const float* logu
   unsigned long long before = 0, after = 0;
   CK(cudaMemcpyAsync(&before, d->acc, 8, cudaMemcpyDeviceToHost, ctx->st));
   ctx->launches++;
-  CK(dp_launch_mh(a, d->mh_smem, ctx->st));
+  CK(dp_launch_mh(a, d->mh, ctx->st));
   CK(cudaMemcpyAsync(&after, d->acc, 8, cudaMemcpyDeviceToHost, ctx->st));
   if (loggamma) CK(cudaMemcpyAsync(loggamma, d->lg, S * T * 4, cudaMemcpyDeviceToHost, ctx->st));
   fmnmf_status s = check_status(ctx);

@@ -16,9 +16,14 @@
 //
 // All FP32 on the CUDA cores; sums in a fixed order (no atomics on values), so results are
 // reproducible bit for bit.
+#include <algorithm>
+
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fm_launch.h"
+
+namespace cg = cooperative_groups;
 
 namespace fm {
 namespace {
@@ -27,28 +32,35 @@ constexpr int kDpTT = 2;                  // frames per CTA of the per-frame swe
 constexpr int kDpFC = kThreads / kDpTT;   // bins per chunk of the per-frame sweeps (128)
 constexpr int kDpMaxPairs = 256;          // (N-1) K noise bases per sweep CTA
 constexpr int kDpItems = kDpMaxPairs * kDpTT / kThreads;  // H-sweep items per thread (2)
-constexpr int kMhMaxThreads = 576;       // Metropolis CTA: one bin per thread up to F = 576
+constexpr int kMhMaxThreads = 320;       // threads of a Metropolis CTA (at most; two CTAs per SM)
+constexpr int kMhMaxTB = 16;             // frames of a Metropolis cluster (at most)
+constexpr int kMhMaxC = 8;               // CTAs of a Metropolis cluster (the portable limit)
 
 
-// Shared-memory layout (floats) of the Metropolis kernel for TB frames.
+// Shared-memory layout (floats) of one Metropolis CTA: FC bins of the cluster's split, TB
+// frames, a cluster of C CTAs.  W2 rows are padded by 4 floats so that the float4 reads of
+// consecutive bins fall on distinct banks.
 struct MhLayout {
-  int xs, yr, g0, uf, rold, rnew, h, zs, zn, vs, red, total;
+  int w2, b2, xs, yr, g0, uf, rold, rnew, h, zs, zn, vs, pl, pg, total;
 };
-__host__ __device__ inline MhLayout mh_layout(int F, int M, int TB, int D, int Hd) {
+__host__ __device__ inline MhLayout mh_layout(int FC, int M, int TB, int D, int Hd, int C) {
   MhLayout L;
   int o = 0;
   auto take = [&](int n) { const int at = o; o += (n + 3) & ~3; return at; };
-  L.xs = take(TB * M * F);     // x~ [tb*M + m][f]
-  L.yr = take(TB * M * F);     // y~^{-0} [tb*M + m][f]
-  L.g0 = take(M * F);          // g~_0 [m][f]
-  L.uf = take(F);              // u_f
-  L.rold = take(TB * F);       // r of the current z [tb][f]
-  L.rnew = take(TB * F);       // r of the proposal
-  L.h = take(TB * Hd);         // hidden layer [tb][j] (16-byte rows: Hd % 4 == 0)
+  L.w2 = take(FC * (Hd + 4));  // W2 rows of the CTA's bins
+  L.b2 = take(FC);
+  L.xs = take(TB * M * FC);    // x~ [tb*M + m][fl]
+  L.yr = take(TB * M * FC);    // y~^{-0} [tb*M + m][fl]
+  L.g0 = take(M * FC);         // g~_0 [m][fl]
+  L.uf = take(FC);             // u_f
+  L.rold = take(TB * FC);      // r of the current z [tb][fl]
+  L.rnew = take(TB * FC);      // r of the proposal
+  L.h = take(TB * Hd);         // hidden layer [tb][j]
   L.zs = take(TB * D);         // z [tb][d]
   L.zn = take(TB * D);         // proposal
   L.vs = take(TB);             // v_t
-  L.red = take((kMhMaxThreads / 32) * TB);
+  L.pl = take(TB * FC);        // log gamma terms summed per bin [tb][fl]
+  L.pg = take(2 * C * TB);     // the cluster's partial sums [proposal parity][rank][tb]
   L.total = o;
   return L;
 }
@@ -150,22 +162,38 @@ __global__ void __launch_bounds__(kThreads) k_dp_lam_noise(DpArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// k_dp_mh: S Metropolis proposals for each of the CTA's TB frames (Sec. III-B-3).  With
+// k_dp_mh: S Metropolis proposals for each of a cluster's TB frames (Sec. III-B-3).  With
 // y~^{-0}_ftm = sum_{n>=1} lambda_ftn g~_nfm fixed, the log acceptance ratio of frame t is
 //   log gamma_t = sum_{f,m} [ x~ (y_new - y_old) / (y_new y_old) - log(y_new / y_old) ],
 //   y_old = lambda_old g~_0 + y~^{-0},  y_new = y_old + (lambda_new - lambda_old) g~_0,
 // the change of Eq. 17 when lambda_ft0 alone changes (each term formed from the difference,
 // so nothing cancels between two large sums).  Accepted where log u < log gamma_t.
+//
+// The C CTAs of a cluster split the bins (FC each) and keep their rows of the decoder's
+// output layer W2 in shared memory for the whole launch, so W2 is read from L2 once per CTA
+// rather than once per proposal.  Per proposal, each CTA computes 1/C of the hidden units of
+// every frame and stores them into every CTA of the cluster (distributed shared memory);
+// after a cluster barrier each thread decodes FG frames of one bin and forms their terms.
+// Every CTA then sums its bins' terms per frame (a warp per frame, fixed order) and stores the
+// sum into every CTA of the cluster (buffers alternating with the proposal's parity); after a
+// second cluster barrier all CTAs add the C partial sums in rank order, so they all take the
+// same decisions, and each updates its own bins.
 // ---------------------------------------------------------------------------------------
-template <int MAXM, int TB>
-__global__ void __launch_bounds__(kMhMaxThreads) k_dp_mh(DpArgs a) {
+template <int MAXM, int FG>
+__global__ void __launch_bounds__(kMhMaxThreads, 2) k_dp_mh(DpArgs a) {
   extern __shared__ __align__(16) float dsm[];
-  __shared__ int acc_s[TB];
-  const int F = a.p.F, T = a.p.T, M = a.p.M, N = a.p.N, D = a.D, Hd = a.Hd;
+  __shared__ int acc_s[kMhMaxTB];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int F = a.p.F, T = a.p.T, M = a.p.M, N = a.p.N, D = a.D, Hd = a.Hd, TB = a.tb;
+  const int HdP = Hd + 4;
   const size_t FT = (size_t)F * T;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nthr = blockDim.x;
-  const int t0 = blockIdx.x * TB, nt = min(TB, T - t0);
-  const MhLayout L = mh_layout(F, M, TB, D, Hd);
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  const int FC = (F + C - 1) / C, f0 = rank * FC, nfc = max(0, min(FC, F - f0));
+  const int t0 = (blockIdx.x / C) * TB, nt = min(TB, T - t0);
+  const MhLayout L = mh_layout(FC, M, TB, D, Hd, C);
+  float* w2 = dsm + L.w2;
+  float* b2 = dsm + L.b2;
   float* xs = dsm + L.xs;
   float* yr = dsm + L.yr;
   float* g0 = dsm + L.g0;
@@ -176,104 +204,147 @@ __global__ void __launch_bounds__(kMhMaxThreads) k_dp_mh(DpArgs a) {
   float* zs = dsm + L.zs;
   float* zn = dsm + L.zn;
   float* vs = dsm + L.vs;
-  float* red = dsm + L.red;
+  float* pl = dsm + L.pl;
+  float* pg = dsm + L.pg;
 
-  // ---- stage the frames' x~, y~^{-0}, r and z, and the bins' g~_0 and u
+  // ---- stage the CTA's bins (W2 rows, b2, g~_0, u) and the frames' x~, y~^{-0}, r, z
+  for (int e = tid; e < nfc * (Hd >> 2); e += nthr) {
+    const int fl = e / (Hd >> 2), j4 = e - fl * (Hd >> 2);
+    reinterpret_cast<float4*>(w2 + fl * HdP)[j4] =
+        __ldg(reinterpret_cast<const float4*>(a.W2 + (size_t)(f0 + fl) * Hd) + j4);
+  }
   const int run = nt * M;  // x~ of the tile's frames is contiguous per bin
-  for (int e = tid; e < F * run; e += nthr) {
-    const int f = e / run, r = e - f * run, tb = r / M, m = r - tb * M;
-    const size_t ft = (size_t)f * T + t0 + tb;
-    xs[(tb * M + m) * F + f] = a.p.xt[ft * M + m];
+  for (int e = tid; e < nfc * run; e += nthr) {
+    const int fl = e / run, r = e - fl * run, tb = r / M, m = r - tb * M;
+    const size_t ft = (size_t)(f0 + fl) * T + t0 + tb;
+    xs[(tb * M + m) * FC + fl] = a.p.xt[ft * M + m];
     float y = 0.f;
-    for (int n = 1; n < N; ++n) y = fmaf(a.lam[n * FT + ft], a.p.G[((size_t)n * F + f) * M + m], y);
-    yr[(tb * M + m) * F + f] = y;
+    for (int n = 1; n < N; ++n) y = fmaf(a.lam[n * FT + ft], a.p.G[((size_t)n * F + f0 + fl) * M + m], y);
+    yr[(tb * M + m) * FC + fl] = y;
   }
-  for (int e = tid; e < F * M; e += nthr) {
-    const int f = e / M, m = e - f * M;
-    g0[m * F + f] = a.p.G[(size_t)f * M + m];
+  for (int e = tid; e < nfc * M; e += nthr) {
+    const int fl = e / M, m = e - fl * M;
+    g0[m * FC + fl] = a.p.G[(size_t)(f0 + fl) * M + m];
   }
-  for (int f = tid; f < F; f += nthr) {
-    uf[f] = a.u[f];
-    for (int tb = 0; tb < nt; ++tb) rold[tb * F + f] = a.R[(size_t)f * T + t0 + tb];
+  for (int fl = tid; fl < nfc; fl += nthr) {
+    b2[fl] = a.b2[f0 + fl];
+    uf[fl] = a.u[f0 + fl];
+    for (int tb = 0; tb < nt; ++tb) rold[tb * FC + fl] = a.R[(size_t)(f0 + fl) * T + t0 + tb];
   }
   for (int e = tid; e < TB * Hd; e += nthr) h[e] = 0.f;  // rows of absent frames stay 0
   for (int e = tid; e < nt * D; e += nthr) zs[e] = a.Z[(size_t)t0 * D + e];
   if (tid < nt) vs[tid] = a.v[t0 + tid];
   unsigned n_acc = 0;
-  __syncthreads();
+  // every CTA of the cluster has started and initialised its shared memory before any CTA
+  // stores into another's
+  cluster.sync();
 
+  // this thread's bin and frames: item = g FC + fl, frames g FG .. g FG + FG - 1
+  const int NG = TB / FG;
+  const int g = tid / FC, fl = tid - g * FC;
+  const bool own = g < NG && fl < nfc;
+  const int JC = (Hd + C - 1) / C, j0 = rank * JC, nj = max(0, min(JC, Hd - j0));
   for (int s = 0; s < a.S; ++s) {
-    // proposal z' = z + sqrt(eps) xi
+    // proposal z' = z + sqrt(eps) xi (every CTA of the cluster forms the same)
     const float* xi = a.xi + ((size_t)s * T + t0) * D;
     for (int e = tid; e < nt * D; e += nthr) zn[e] = fmaf(a.sqrt_eps, xi[e], zs[e]);
     __syncthreads();
-    hidden_layer(a.W1, a.b1, zn, h, nt, D, Hd);
-    __syncthreads();
-    float part[TB];
+    // this CTA's share of the hidden units, into every CTA of the cluster
+    for (int e = tid; e < nt * nj; e += nthr) {
+      const int tb = e / nj, j = j0 + (e - tb * nj);
+      float v = a.b1[j];
+      const float* w = a.W1 + (size_t)j * D;
+      for (int d = 0; d < D; ++d) v = fmaf(w[d], zn[tb * D + d], v);
+      v = tanhf(v);
+      for (int c = 0; c < C; ++c) cluster.map_shared_rank(h, c)[tb * Hd + j] = v;
+    }
+    cluster.sync();
+    if (own) {
+      float sv[FG];
 #pragma unroll
-    for (int tb = 0; tb < TB; ++tb) part[tb] = 0.f;
-    for (int f = tid; f < F; f += nthr) {
-      float sv[TB];
-      decode_bin<TB>(a.W2, a.b2, h, Hd, f, sv);
-      const float u = uf[f];
+      for (int i = 0; i < FG; ++i) sv[i] = 0.f;
+      const float4* w = reinterpret_cast<const float4*>(w2 + fl * HdP);
+      const float* hg = h + g * FG * Hd;
+#pragma unroll 2
+      for (int j4 = 0; j4 < (Hd >> 2); ++j4) {
+        const float4 wv = w[j4];
 #pragma unroll
-      for (int tb = 0; tb < TB; ++tb)
+        for (int i = 0; i < FG; ++i) {
+          const float4 hv = *reinterpret_cast<const float4*>(hg + i * Hd + 4 * j4);
+          sv[i] = fmaf(wv.x, hv.x, sv[i]);
+          sv[i] = fmaf(wv.y, hv.y, sv[i]);
+          sv[i] = fmaf(wv.z, hv.z, sv[i]);
+          sv[i] = fmaf(wv.w, hv.w, sv[i]);
+        }
+      }
+      const float u = uf[fl], bias = b2[fl];
+#pragma unroll
+      for (int i = 0; i < FG; ++i) {
+        const int tb = g * FG + i;
         if (tb < nt) {
-          const float rn = expf(sv[tb]);
-          rnew[tb * F + f] = rn;
-          const float lo = u * vs[tb] * rold[tb * F + f];
+          const float rn = expf(sv[i] + bias);
+          rnew[tb * FC + fl] = rn;
+          const float lo = u * vs[tb] * rold[tb * FC + fl];
           const float dl = u * vs[tb] * rn - lo;
           float acc = 0.f;
 #pragma unroll
           for (int m = 0; m < MAXM; ++m)
             if (m < M) {
-              const float g = g0[m * F + f];
-              const float yo = fmaf(lo, g, yr[(tb * M + m) * F + f]);
-              const float d = dl * g;
+              const float gm = g0[m * FC + fl];
+              const float yo = fmaf(lo, gm, yr[(tb * M + m) * FC + fl]);
+              const float d = dl * gm;
               const float yn = yo + d;
-              acc += xs[(tb * M + m) * F + f] * d / (yn * yo) - log1pf(d / yo);
+              acc += xs[(tb * M + m) * FC + fl] * d / (yn * yo) - log1pf(d / yo);
             }
-          part[tb] += acc;
+          pl[tb * FC + fl] = acc;
         }
-    }
-    // log gamma per frame: warp sums, then the warps in order
-#pragma unroll
-    for (int tb = 0; tb < TB; ++tb) {
-      float v = part[tb];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp * TB + tb] = v;
+      }
     }
     __syncthreads();
+    // this CTA's sum per frame (a warp per frame, bins in a fixed order), into every CTA
+    float* buf = pg + (s & 1) * C * TB;
+    for (int tb = warp; tb < nt; tb += nw) {
+      float cp = 0.f;
+      for (int b = lane; b < nfc; b += 32) cp += pl[tb * FC + b];
+      for (int o = 16; o > 0; o >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, o);
+      if (lane < C) cluster.map_shared_rank(buf, lane)[rank * TB + tb] = cp;
+    }
+    cluster.sync();
     if (tid < nt) {
       float lg = 0.f;
-      for (int w = 0; w < (nthr >> 5); ++w) lg += red[w * TB + tid];
+      for (int c = 0; c < C; ++c) lg += buf[c * TB + tid];
       const int acc = a.logu[(size_t)s * T + t0 + tid] < lg;
       acc_s[tid] = acc;
-      n_acc += acc;
-      if (a.loggamma) a.loggamma[(size_t)s * T + t0 + tid] = lg;
-      if (isnan(lg)) flag(a.p.status, ST_NONFINITE);
+      if (rank == 0) {
+        n_acc += acc;
+        if (a.loggamma) a.loggamma[(size_t)s * T + t0 + tid] = lg;
+        if (isnan(lg)) flag(a.p.status, ST_NONFINITE);
+      }
     }
     __syncthreads();
     // accepted frames take the proposal (each thread copies what it wrote or will read)
     for (int e = tid; e < nt * D; e += nthr)
       if (acc_s[e / D]) zs[e] = zn[e];
-    for (int f = tid; f < F; f += nthr)
+    if (own)
 #pragma unroll
-      for (int tb = 0; tb < TB; ++tb)
-        if (tb < nt && acc_s[tb]) rold[tb * F + f] = rnew[tb * F + f];
-    __syncthreads();
+      for (int i = 0; i < FG; ++i) {
+        const int tb = g * FG + i;
+        if (tb < nt && acc_s[tb]) rold[tb * FC + fl] = rnew[tb * FC + fl];
+      }
   }
+  __syncthreads();
 
-  // ---- the sampled z, its r and lambda_ft0 of the tile's frames
-  for (int e = tid; e < nt * D; e += nthr) a.Z[(size_t)t0 * D + e] = zs[e];
-  for (int f = tid; f < F; f += nthr)
-    for (int tb = 0; tb < nt; ++tb) {
-      const size_t i = (size_t)f * T + t0 + tb;
-      const float r = rold[tb * F + f];
-      a.R[i] = r;
-      a.lam[i] = uf[f] * vs[tb] * r;
-    }
-  if (tid < nt && n_acc) atomicAdd(a.n_acc, (unsigned long long)n_acc);
+  // ---- the sampled z (rank 0), r and lambda_ft0 of the CTA's bins
+  if (rank == 0)
+    for (int e = tid; e < nt * D; e += nthr) a.Z[(size_t)t0 * D + e] = zs[e];
+  for (int e = tid; e < nfc * nt; e += nthr) {
+    const int b = e / nt, tb = e - b * nt;
+    const size_t i = (size_t)(f0 + b) * T + t0 + tb;
+    const float r = rold[tb * FC + b];
+    a.R[i] = r;
+    a.lam[i] = uf[b] * vs[tb] * r;
+  }
+  if (rank == 0 && tid < nt && n_acc) atomicAdd(a.n_acc, (unsigned long long)n_acc);
 }
 
 // Block sum of two values in a fixed order (warp shuffles, then the warps in order); the
@@ -559,52 +630,61 @@ __global__ void __launch_bounds__(kThreads) k_dp_norm(DpArgs a) {
 
 }  // namespace
 
-int dp_mh_frames(int F, int T, int M, int D, int Hd, int sms, size_t limit, size_t* smem) {
-  // the most frames per CTA (each row of W2 read once serves them all) that still gives every
-  // SM about 1.5 CTAs and fits the staging in shared memory
-  for (int tb = 4; tb >= 1; tb >>= 1) {
-    const size_t b = (size_t)mh_layout(F, M, tb, D, Hd).total * sizeof(float);
+DpMhPlan dp_mh_plan(int F, int T, int M, int D, int Hd, int sms, size_t limit) {
+  // about 64 bins per CTA; then the most frames per cluster (every W2 row read from shared
+  // memory serves them all) that still puts a CTA on every SM and fits the staging
+  DpMhPlan pl;
+  const int C = std::min(kMhMaxC, std::max(1, (F + 63) / 64));
+  const int FC = (F + C - 1) / C;
+  for (int TB = kMhMaxTB; TB >= 1; TB >>= 1) {
+    const size_t b = (size_t)mh_layout(FC, M, TB, D, Hd, C).total * sizeof(float);
     if (b > limit) continue;
-    if (tb > 1 && 2 * ((T + tb - 1) / tb) < 3 * sms) continue;
-    if (smem) *smem = b;
-    return tb;
+    if (TB > 1 && ((T + TB - 1) / TB) * C < sms) continue;
+    const int FG = std::min(TB, 4);
+    const int thr = std::max(64, ((TB / FG * FC + 31) / 32) * 32);
+    if (thr > kMhMaxThreads) continue;
+    pl.C = C; pl.TB = TB; pl.FG = FG; pl.threads = thr; pl.smem = b;
+    return pl;
   }
-  return 0;
+  return pl;
 }
 
 namespace {
 template <int MAXM>
 cudaError_t mh_prepare(size_t smem) {
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_dp_mh<MAXM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_dp_mh<MAXM, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_dp_mh<MAXM, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-// Threads of a Metropolis CTA: whole warps, one bin per thread where F allows, the bins
-// spread evenly over the rounds otherwise (no round for a few tail bins).
-int mh_threads(int F) {
-  const int rounds = (F + kMhMaxThreads - 1) / kMhMaxThreads;
-  const int per = (F + rounds - 1) / rounds;
-  return ((per + 31) / 32) * 32;
+  if ((e = cudaFuncSetAttribute(k_dp_mh<MAXM, 1>, A, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_dp_mh<MAXM, 2>, A, (int)smem)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_dp_mh<MAXM, 4>, A, (int)smem);
 }
 template <int MAXM>
-cudaError_t mh_launch(const DpArgs& a, size_t smem, cudaStream_t st) {
-  const dim3 grid((a.p.T + a.tb - 1) / a.tb);
-  const int nthr = mh_threads(a.p.F);
-  switch (a.tb) {
-    case 4: k_dp_mh<MAXM, 4><<<grid, nthr, smem, st>>>(a); break;
-    case 2: k_dp_mh<MAXM, 2><<<grid, nthr, smem, st>>>(a); break;
-    default: k_dp_mh<MAXM, 1><<<grid, nthr, smem, st>>>(a); break;
+cudaError_t mh_launch(const DpArgs& a, const DpMhPlan& pl, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(((a.p.T + pl.TB - 1) / pl.TB) * pl.C);
+  cfg.blockDim = dim3(pl.threads);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)pl.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  switch (pl.FG) {
+    case 4: return cudaLaunchKernelEx(&cfg, k_dp_mh<MAXM, 4>, a);
+    case 2: return cudaLaunchKernelEx(&cfg, k_dp_mh<MAXM, 2>, a);
+    default: return cudaLaunchKernelEx(&cfg, k_dp_mh<MAXM, 1>, a);
   }
-  return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t dp_prepare(int maxm, size_t mh_smem) {
+cudaError_t dp_prepare(int maxm, const DpMhPlan& pl) {
   switch (maxm) {
-    case 2: return mh_prepare<2>(mh_smem);
-    case 4: return mh_prepare<4>(mh_smem);
-    default: return mh_prepare<8>(mh_smem);
+    case 2: return mh_prepare<2>(pl.smem);
+    case 4: return mh_prepare<4>(pl.smem);
+    default: return mh_prepare<8>(pl.smem);
   }
 }
 
@@ -619,11 +699,11 @@ cudaError_t dp_launch_init(const DpArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t dp_launch_mh(const DpArgs& a, size_t smem, cudaStream_t st) {
+cudaError_t dp_launch_mh(const DpArgs& a, const DpMhPlan& pl, cudaStream_t st) {
   switch (a.maxm) {
-    case 2: return mh_launch<2>(a, smem, st);
-    case 4: return mh_launch<4>(a, smem, st);
-    default: return mh_launch<8>(a, smem, st);
+    case 2: return mh_launch<2>(a, pl, st);
+    case 4: return mh_launch<4>(a, pl, st);
+    default: return mh_launch<8>(a, pl, st);
   }
 }
 

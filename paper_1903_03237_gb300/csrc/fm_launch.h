@@ -117,14 +117,18 @@ struct DpArgs {
   float* loggamma = nullptr;     // [S][T] log gamma of every proposal, or null
   const float* nu = nullptr;     // [N][F] nu of the last normalisation (k_bin)
   int maxm = 8;
-  int tb = 4;                    // frames per Metropolis CTA (1, 2 or 4)
+  int tb = 1;                    // frames per Metropolis cluster
 };
-// Frames per Metropolis CTA and its dynamic shared memory: the largest of 4, 2, 1 whose
-// staging fits in `limit` bytes and that leaves about 1.5 CTAs per SM (0 if none fits).
-int dp_mh_frames(int F, int T, int M, int D, int Hd, int sms, size_t limit, size_t* smem);
-cudaError_t dp_prepare(int maxm, size_t mh_smem);
+// Launch shape of the Metropolis kernel: clusters of C CTAs (the bins split C ways), TB frames
+// per cluster, FG frames per thread; C = 0 when nothing fits in `limit` bytes of shared memory.
+struct DpMhPlan {
+  int C = 0, TB = 0, FG = 0, threads = 0;
+  size_t smem = 0;
+};
+DpMhPlan dp_mh_plan(int F, int T, int M, int D, int Hd, int sms, size_t limit);
+cudaError_t dp_prepare(int maxm, const DpMhPlan& plan);
 cudaError_t dp_launch_init(const DpArgs& a, cudaStream_t st);     // R from Z, lambda of every source
-cudaError_t dp_launch_mh(const DpArgs& a, size_t smem, cudaStream_t st);  // S proposals per frame
+cudaError_t dp_launch_mh(const DpArgs& a, const DpMhPlan& plan, cudaStream_t st);  // S proposals per frame
 cudaError_t dp_launch_fsweep(const DpArgs& a, int mode, cudaStream_t st);  // per bin: u (0) or noise W (1)
 cudaError_t dp_launch_tsweep(const DpArgs& a, int mode, cudaStream_t st);  // per frame: v (0) or noise H (1)
 cudaError_t dp_launch_norm(const DpArgs& a, cudaStream_t st);     // nu into u, W; mu into v, H

@@ -164,6 +164,7 @@ SHAPES = [
     (20, 30, 8, 3, 2, 4, 12, 3, 4),
     (50, 23, 4, 1, 1, 16, 32, 5, 5),
     (40, 1000, 2, 2, 2, 8, 16, 3, 6),     # enough frames for 4 frames per Metropolis CTA
+    (40, 600, 3, 2, 2, 8, 16, 3, 7),      # 2 frames per Metropolis CTA
 ]
 IDS = [f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}D{s[5]}H{s[6]}S{s[7]}" for s in SHAPES]
 
