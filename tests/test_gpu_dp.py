@@ -155,16 +155,17 @@ def _ctx(fm, X, state, theta, N, K, S, eps=1e-4, normalise=True):
 
 
 # F, T, M, N, K, D, Hd, S, seed: ragged T (not a multiple of 4 or 8), F beyond one CTA's 256
-# threads, every channel bucket, speech alone (N = 1), several noise sources; 1, 2 (the
-# paper-scale case) and 4 frames per Metropolis CTA
+# threads, every channel bucket, speech alone (N = 1), several noise sources; Metropolis launches
+# with clusters of 1 CTA (1, 2 and 4 frames), 5 CTAs (F300) and 8 CTAs with 16 frames (the
+# paper-scale case)
 SHAPES = [
     (33, 41, 2, 2, 3, 16, 128, 5, 1),
     (300, 37, 3, 3, 4, 8, 64, 4, 2),
     (64, 75, 5, 2, 16, 16, 128, 6, 3),
     (20, 30, 8, 3, 2, 4, 12, 3, 4),
     (50, 23, 4, 1, 1, 16, 32, 5, 5),
-    (40, 1000, 2, 2, 2, 8, 16, 3, 6),     # enough frames for 4 frames per Metropolis CTA
-    (40, 600, 3, 2, 2, 8, 16, 3, 7),      # 2 frames per Metropolis CTA
+    (40, 1000, 2, 2, 2, 8, 16, 3, 6),     # 4 frames per Metropolis cluster
+    (40, 600, 3, 2, 2, 8, 16, 3, 7),      # 2 frames per Metropolis cluster
 ]
 IDS = [f"F{s[0]}T{s[1]}M{s[2]}N{s[3]}K{s[4]}D{s[5]}H{s[6]}S{s[7]}" for s in SHAPES]
 
