@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_fsweep(DpArgs a, int mode) {
   __shared__ float red[2 * (kThreads / 32)];
   __shared__ float ws[kDpMaxPairs];
   __shared__ float Ps[7][kThreads], Rs[7][kThreads];
+  __shared__ float sn_s[kThreads], sd_s[kThreads];  // slice sums of the noise W rule
   __shared__ float uf_s;
   const int F = a.p.F, T = a.p.T, M = a.p.M, N = a.p.N, K = a.K;
   const size_t FT = (size_t)F * T;
@@ -421,8 +422,11 @@ __global__ void __launch_bounds__(kThreads) k_dp_fsweep(DpArgs a, int mode) {
     for (int t = tid; t < T; t += kThreads) a.lam[(size_t)f * T + t] = u * a.v[t] * a.R[(size_t)f * T + t];
     return;
   }
-  // mode 1: the noise bases of the bin, one (n, k) pair per thread
+  // mode 1: the noise bases of the bin; each (n, k) pair summed by nsl threads, each over every
+  // nsl-th frame of a chunk, the slices added in order at the end
   const int np = (N - 1) * K;
+  const int nsl = max(1, kThreads / np);
+  const int pair = tid % np, sl = tid / np;
   float an = 0.f, ad = 0.f;
   for (int t0 = 0; t0 < T; t0 += kThreads) {
     const int t = t0 + tid;
@@ -447,17 +451,29 @@ __global__ void __launch_bounds__(kThreads) k_dp_fsweep(DpArgs a, int mode) {
       }
     }
     __syncthreads();
-    if (tid < np) {
-      const int n1 = tid / K;
-      const float* hr = a.Hn + (size_t)tid * T + t0;
+    if (sl < nsl) {
+      const int n1 = pair / K;
+      const float* hr = a.Hn + (size_t)pair * T + t0;
       const int tc = min(kThreads, T - t0);
-      for (int j = 0; j < tc; ++j) {
+      for (int j = sl; j < tc; j += nsl) {
         const float hv = hr[j];
         an = fmaf(hv, Ps[n1][j], an);
         ad = fmaf(hv, Rs[n1][j], ad);
       }
     }
     __syncthreads();
+  }
+  if (nsl > 1) {
+    sn_s[tid] = an;
+    sd_s[tid] = ad;
+    __syncthreads();
+    if (tid < np) {
+      an = ad = 0.f;
+      for (int q = 0; q < nsl; ++q) {
+        an += sn_s[q * np + tid];
+        ad += sd_s[q * np + tid];
+      }
+    }
   }
   if (tid < np) {
     const size_t wi = (size_t)tid * F + f;
@@ -487,6 +503,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
   __shared__ float Ps[7][kDpFC][kDpTT], Rs[7][kDpFC][kDpTT];
   __shared__ float rn[kDpFC][kDpTT], rd[kDpFC][kDpTT];
   __shared__ float hs[kDpMaxPairs * kDpTT];
+  __shared__ float sn_s[kThreads], sd_s[kThreads];  // slice sums of the noise H rule
   __shared__ float vs[kDpTT];
   const int F = a.p.F, T = a.p.T, M = a.p.M, N = a.p.N, K = a.K;
   const size_t FT = (size_t)F * T;
@@ -494,6 +511,8 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
   const int t0 = blockIdx.x * kDpTT, t = t0 + tl;
   const bool valid = t < T;
   const int np = (N - 1) * K;
+  const int nitems = np * kDpTT;                        // (pair, frame) items of the H rule
+  const int nsl = (nitems > 0 && nitems < kThreads) ? kThreads / nitems : 1;  // threads per item
   float an[kDpItems], ad[kDpItems];
 #pragma unroll
   for (int i = 0; i < kDpItems; ++i) an[i] = ad[i] = 0.f;
@@ -548,6 +567,19 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
     if (mode == 1) {
       __syncthreads();
       const int fc = min(kDpFC, F - f0);
+      if (nsl > 1) {
+        // each (pair, frame) item summed by nsl threads over every nsl-th bin of the chunk
+        if (tid < nsl * nitems) {
+          const int item = tid % nitems, sl = tid / nitems;
+          const int pair = item / kDpTT, tl2 = item - pair * kDpTT, n1 = pair / K;
+          const float* wr = a.Wn + (size_t)pair * F + f0;
+          for (int j = sl; j < fc; j += nsl) {
+            const float w = wr[j];
+            an[0] = fmaf(w, Ps[n1][j][tl2], an[0]);
+            ad[0] = fmaf(w, Rs[n1][j][tl2], ad[0]);
+          }
+        }
+      } else
 #pragma unroll
       for (int i = 0; i < kDpItems; ++i) {
         const int item = tid + i * kThreads;
@@ -584,10 +616,23 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
       for (int f = fl; f < F; f += kDpFC) a.lam[(size_t)f * T + t] = a.u[f] * vs[tl] * a.R[(size_t)f * T + t];
     return;
   }
+  if (nsl > 1) {
+    // the slices of each item added in order
+    sn_s[tid] = an[0];
+    sd_s[tid] = ad[0];
+    __syncthreads();
+    if (tid < nitems) {
+      an[0] = ad[0] = 0.f;
+      for (int q = 0; q < nsl; ++q) {
+        an[0] += sn_s[q * nitems + tid];
+        ad[0] += sd_s[q * nitems + tid];
+      }
+    }
+  }
 #pragma unroll
   for (int i = 0; i < kDpItems; ++i) {
     const int item = tid + i * kThreads;
-    if (item < np * kDpTT) {
+    if (item < nitems) {
       const int pair = item / kDpTT, tl2 = item - pair * kDpTT;
       if (t0 + tl2 < T) {
         const size_t hi = (size_t)pair * T + t0 + tl2;
