@@ -72,3 +72,32 @@ def test_front_end_host_side():
     assert b"F" in lib.fmnmf_last_error(None)
     assert lib.fmnmf_istft(None, 1, 33, 4, 2, 200, 64, 16, None, None) == fm.EINVAL  # frames too short
     assert lib.fmnmf_init_spectral(None) == fm.EINVAL
+
+
+def test_dp_host_side():
+    # FastMNMF-DP defaults (the paper's D = 16, 30 proposals, eps = 1e-4) and the argument errors
+    # the C ABI reports before it touches a device
+    from paper_1903_03237_gb300.build import build
+    build()
+    from paper_1903_03237_gb300 import fastmnmf as fm
+    lib = fm.lib()
+    o = fm.DPOpts()
+    assert lib.fmnmf_dp_default_opts(ctypes.byref(o)) == fm.OK
+    assert (o.D, o.Hd, o.n_proposals, o.normalise) == (16, 128, 30, 1) and o.eps == ctypes.c_float(1e-4).value
+    X = (ctypes.c_float * 64)()
+    dp = ctypes.c_void_p()
+    for field, value, word in (("Hd", 10, b"Hd"), ("D", 0, b"D"), ("n_proposals", -1, b"n_proposals"),
+                               ("eps", -1.0, b"eps")):
+        bad = fm.DPOpts()
+        lib.fmnmf_dp_default_opts(ctypes.byref(bad))
+        setattr(bad, field, value)
+        assert lib.fmnmf_dp_create(ctypes.byref(dp), ctypes.addressof(X), 0, 4, 4, 2, 2, 2, ctypes.byref(bad)) == fm.EINVAL
+        assert word in lib.fmnmf_dp_last_error(None)
+    assert lib.fmnmf_dp_create(ctypes.byref(dp), ctypes.addressof(X), 0, 4, 4, 2, 9, 2, None) == fm.EINVAL   # N > 8
+    assert lib.fmnmf_dp_create(ctypes.byref(dp), ctypes.addressof(X), 0, 4, 4, 2, 3, 200, None) == fm.EINVAL  # (N-1)K > 256
+    assert lib.fmnmf_dp_create(None, ctypes.addressof(X), 0, 4, 4, 2, 2, 2, None) == fm.EINVAL
+    for call in (lambda: lib.fmnmf_dp_set_decoder(None, None, None, None, None),
+                 lambda: lib.fmnmf_dp_iterate(None, 1, None, None, 0),
+                 lambda: lib.fmnmf_dp_sync(None)):
+        assert call() == fm.EINVAL
+    assert lib.fmnmf_dp_destroy(None) == fm.OK
