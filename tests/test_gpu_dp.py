@@ -333,3 +333,42 @@ def test_paper_scale_one_iteration(fm):
     assert na == acc[0]
     assert _ll_rel(ll, X64, ref, th) < 1e-5
     _assert_within(err, 1e-5, T, args, 1)
+
+
+def test_one_iteration_without_normalisation(fm):
+    F, T, M, N, K, Dd, Hd, S, seed = SHAPES[1]
+    X, state, theta = _problem(F, T, M, N, K, Dd, Hd, seed)
+    xi, logu = make_dp_draws(1, S, T, Dd, seed)
+    logu[:] = -np.inf        # every proposal accepted: no decision depends on rounding
+    X64 = X.astype(np.complex128)
+    th = tuple(a.astype(np.float64) for a in theta)
+    args = (X64, *_as64(state), th, xi.astype(np.float64), logu.astype(np.float64), float(np.float32(1e-4)))
+    *ref, tr = D.iterate_dp(*args, n_iter=1, do_normalise=False)
+    with _ctx(fm, X, state, theta, N, K, S, normalise=False) as dp:
+        dp.iterate(1, xi, logu)
+        ll = dp.loglik()
+        got = dp.get_state()
+    err = _state_errors(got, ref)
+    print("raw", {k: f"{v:.1e}" for k, v in err.items()})
+    assert _ll_rel(ll, X64, ref, th) < 1e-5
+    for k, v in err.items():
+        assert v < 1e-5, (k, v, err)
+
+
+def test_device_draws_equal_host_draws(fm):
+    import torch
+    F, T, M, N, K, Dd, Hd, S, seed = SHAPES[0]
+    X, state, theta = _problem(F, T, M, N, K, Dd, Hd, seed)
+    xi, logu = make_dp_draws(6, S, T, Dd, seed)   # more than one chunk of host draws
+    outs = []
+    for on_device in (False, True):
+        with _ctx(fm, X, state, theta, N, K, S) as dp:
+            if on_device:
+                dp.iterate(6, torch.from_numpy(xi).cuda(), torch.from_numpy(logu).cuda())
+            else:
+                dp.iterate(6, xi, logu)
+            outs.append((dp.get_state(), dp.loglik(), dp.accepted()))
+    (sa, la, na), (sb, lb, nb) = outs
+    assert na == nb and la == lb
+    for a, b in zip(sa, sb):
+        assert np.array_equal(a, b)
