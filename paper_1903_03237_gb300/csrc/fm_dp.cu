@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_fsweep(DpArgs a, int mode) {
       const int n1 = pair / K;
       const float* hr = a.Hn + (size_t)pair * T + t0;
       const int tc = min(kThreads, T - t0);
+#pragma unroll 8
       for (int j = sl; j < tc; j += nsl) {
         const float hv = hr[j];
         an = fmaf(hv, Ps[n1][j], an);
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(kThreads) k_dp_tsweep(DpArgs a, int mode) {
           const int item = tid % nitems, sl = tid / nitems;
           const int pair = item / kDpTT, tl2 = item - pair * kDpTT, n1 = pair / K;
           const float* wr = a.Wn + (size_t)pair * F + f0;
+#pragma unroll 8
           for (int j = sl; j < fc; j += nsl) {
             const float w = wr[j];
             an[0] = fmaf(w, Ps[n1][j][tl2], an[0]);
